@@ -1,0 +1,287 @@
+"""CPU oracle for sign(H_W(mu)) b by restarted LR-deflated multishift FOM.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import this package.  It shares no
+code with the CUDA library (``paper_0910_2927_gb300``) and never imports it.
+
+Two layers, both FP64:
+
+* O2, iterative (C, ``wilson.c`` / ``fomlr.c``): the Wilson kernel and
+  Algorithm 1 (restarted FOM-LR(m,k)) in the A^2 reading of eq. (6.2).
+* O1, dense (NumPy/SciPy, small lattices only): the dense matrix of H_W(mu),
+  its eigendecomposition (critical eigenpairs for LR deflation, Sec. 4), the
+  dense deflated rational target and the exact sign function.
+
+Every function names the passage of the paper it follows.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import numpy as np
+
+from . import build as _build
+
+_LIB = None
+
+
+class _Lattice(C.Structure):
+    _fields_ = [("dims", C.c_int * 4), ("antiperiodic", C.c_int * 4),
+                ("mu", C.c_double), ("mass", C.c_double)]
+
+
+class _Report(C.Structure):
+    _fields_ = [("cycles", C.c_int), ("matvecs", C.c_int), ("converged", C.c_int),
+                ("breakdown", C.c_int), ("res_est", C.c_double)]
+
+
+def lib():
+    """Load (building on first use) the C oracle."""
+    global _LIB
+    if _LIB is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        P = C.c_void_p
+        L.orc_hw.argtypes = [C.POINTER(_Lattice), P, P, P]
+        L.orc_hw.restype = None
+        L.orc_hw_sites.argtypes = [C.POINTER(_Lattice), P, P, P, P, C.c_int64]
+        L.orc_hw_sites.restype = None
+        L.orc_kenney_laub.argtypes = [C.c_int, C.c_double, P, P]
+        L.orc_kenney_laub.restype = C.c_int
+        L.orc_fom_lr.argtypes = [C.POINTER(_Lattice), P, C.c_int, P, P, C.c_int, C.c_double,
+                                 C.c_int, C.c_int, C.c_int, P, P, P, P, P, P,
+                                 C.POINTER(_Report)]
+        L.orc_fom_lr.restype = C.c_int
+        L.orc_num_threads.restype = C.c_int
+        _LIB = L
+    return _LIB
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def _lat(dims, mu, mass, antiperiodic):
+    lt = _Lattice()
+    for i in range(4):
+        lt.dims[i] = int(dims[i])
+        lt.antiperiodic[i] = int(antiperiodic[i])
+    lt.mu = float(mu)
+    lt.mass = float(mass)
+    return lt
+
+
+def _c128(a):
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    return a
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+# ---------------------------------------------------------------- operator --
+
+def hw(dims, links, psi, mu, mass=-1.6, antiperiodic=(0, 0, 0, 1)):
+    """H_W(mu) psi = gamma5 D_W(mu) psi (Sec. 1; D_W(mu) as read in wilson.c)."""
+    U = _c128(links)
+    x = _c128(psi).reshape(-1)
+    out = np.empty_like(x)
+    lt = _lat(dims, mu, mass, antiperiodic)
+    lib().orc_hw(C.byref(lt), _ptr(U), _ptr(x), _ptr(out))
+    return out
+
+
+def hw_sites(dims, links, psi, sites, mu, mass=-1.6, antiperiodic=(0, 0, 0, 1)):
+    """H_W(mu) psi evaluated only at the listed sites; returns shape (len(sites), 12)."""
+    U = _c128(links)
+    x = _c128(psi).reshape(-1)
+    out = np.zeros_like(x)
+    st = np.ascontiguousarray(sites, dtype=np.int64)
+    lt = _lat(dims, mu, mass, antiperiodic)
+    lib().orc_hw_sites(C.byref(lt), _ptr(U), _ptr(x), _ptr(out), _ptr(st), st.size)
+    return out.reshape(-1, 12)[st]
+
+
+def dense_hw(dims, links, mu, mass=-1.6, antiperiodic=(0, 0, 0, 1)):
+    """Dense n x n matrix of H_W(mu), column by column (small lattices only)."""
+    n = 12 * int(np.prod(dims))
+    A = np.empty((n, n), dtype=np.complex128)
+    e = np.zeros(n, dtype=np.complex128)
+    for j in range(n):
+        e[j] = 1.0
+        A[:, j] = hw(dims, links, e, mu, mass, antiperiodic)
+        e[j] = 0.0
+    return A
+
+
+# ------------------------------------------------- rational approximation --
+
+def kenney_laub(s, c=1.0):
+    """Shifts and weights of eq. (6.2) with the scale c of Sec. 6 folded in.
+
+    Returns (sigma', omega') with g_s(c t) = t sum omega'_i / (t^2 - sigma'_i).
+    """
+    sig = np.empty(s)
+    om = np.empty(s)
+    rc = lib().orc_kenney_laub(int(s), float(c), _ptr(sig), _ptr(om))
+    if rc:
+        raise ValueError("kenney_laub: need s >= 1 and c > 0")
+    return sig, om
+
+
+def kl_closed_form(t, s):
+    """g_s(t) = ((t+1)^{2s} - (t-1)^{2s}) / ((t+1)^{2s} + (t-1)^{2s}), eq. (6.1)."""
+    t = np.asarray(t, dtype=np.complex128)
+    a = (t + 1) ** (2 * s)
+    b = (t - 1) ** (2 * s)
+    return (a - b) / (a + b)
+
+
+def kl_partial_fractions(t, s, c=1.0):
+    """g_s(c t) from the partial fractions of eq. (6.2)."""
+    sig, om = kenney_laub(s, c)
+    t = np.asarray(t, dtype=np.complex128)
+    return t * sum(om[i] / (t * t - sig[i]) for i in range(s))
+
+
+# ------------------------------------------------------------ Algorithm 1 --
+
+def fom_lr(dims, links, b, mu, sigma, omega, k, tol, max_cycles=1000, project_each_cycle=True,
+           R=None, L=None, lam=None, mass=-1.6, antiperiodic=(0, 0, 0, 1), want_shifts=False):
+    """Restarted FOM-LR(m,k), Algorithm 1, in the A^2 reading of eq. (6.2).
+
+    Returns (x, report, x_shift) where x approximates
+    x_P + sum_i omega_i (A^2 - sigma_i)^{-1} A (I - P) b and x_shift[i] is the
+    iterate of shifted system i (None unless want_shifts).
+    """
+    U = _c128(links)
+    bb = _c128(b).reshape(-1)
+    n = bb.size
+    s = len(sigma)
+    sig = np.ascontiguousarray(sigma, dtype=np.float64)
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    if R is None:
+        m = 0
+        Rc = Lc = lc = np.zeros(1, dtype=np.complex128)
+    else:
+        R = np.asarray(R)
+        m = R.shape[1]
+        Rc = _c128(R.T)      # column-major n x m == row-major m x n
+        Lc = _c128(np.asarray(L).T)
+        lc = _c128(lam)
+    x = np.empty(n, dtype=np.complex128)
+    xs = np.empty((s, n), dtype=np.complex128) if want_shifts else None
+    rep = _Report()
+    lt = _lat(dims, mu, mass, antiperiodic)
+    rc = lib().orc_fom_lr(C.byref(lt), _ptr(U), s, _ptr(sig), _ptr(om), int(k), float(tol),
+                          int(max_cycles), int(bool(project_each_cycle)), m, _ptr(Rc), _ptr(Lc),
+                          _ptr(lc), _ptr(bb), _ptr(x), _ptr(xs) if xs is not None else None,
+                          C.byref(rep))
+    report = dict(status=rc, cycles=rep.cycles, matvecs=rep.matvecs, converged=bool(rep.converged),
+                  breakdown=bool(rep.breakdown), res_est=rep.res_est)
+    if rc not in (0, 3):
+        raise RuntimeError(f"orc_fom_lr failed with status {rc}")
+    return x, report, xs
+
+
+# ------------------------------------------------------------ dense (O1) --
+
+def eig(A):
+    """Dense eigendecomposition A = X diag(w) X^{-1}; returns (w, X, X^{-1})."""
+    w, X = np.linalg.eig(A)
+    return w, X, np.linalg.inv(X)
+
+
+def critical_eigenpairs(A, m, extra=0, decomposition=None):
+    """LR deflation data of Sec. 4: the m eigenvalues of smallest |lambda|.
+
+    Returns (R, L, lam, lam_next): right eigenvectors R (n x m), left
+    eigenvectors L (n x m) normalised so that L^dag R = I (the rows of X^{-1}),
+    the eigenvalues, and the next `extra` eigenvalues in the same order.
+    Order: |lambda|, then Re lambda, then Im lambda.
+    """
+    w, X, Xinv = decomposition if decomposition is not None else eig(A)
+    order = np.lexsort((w.imag, w.real, np.abs(w)))
+    w = w[order]
+    X = X[:, order]
+    Xinv = Xinv[order, :]
+    if m < len(w):
+        gap = abs(w[m]) - abs(w[m - 1]) if m > 0 else 1.0
+        if m > 0 and gap < 1e-8 * abs(w[m - 1]):
+            raise ValueError("critical eigenvalue selection is ambiguous: |lambda_m| ~ |lambda_m+1|")
+    R = X[:, :m].copy()
+    L = Xinv[:m, :].conj().T.copy()
+    return R, L, w[:m].copy(), w[m:m + extra].copy()
+
+
+def deflated_target(A, b, sigma, omega, R=None, L=None, lam=None):
+    """Dense x* = R sign(Re Lambda) L^dag b + sum_i omega_i (A^2 - sigma_i)^{-1} A (I - P) b.
+
+    The split of eq. (4.2) with x_P from eq. (4.3) and the partial fractions of
+    eq. (6.2) on the remainder; solved by dense LU, one solve per shift.
+    """
+    n = A.shape[0]
+    b = np.asarray(b, dtype=np.complex128).reshape(-1)
+    if R is None or R.shape[1] == 0:
+        xP = np.zeros(n, dtype=np.complex128)
+        r = b.copy()
+    else:
+        c = L.conj().T @ b
+        xP = R @ (np.where(np.real(lam) > 0, 1.0, -1.0) * c)
+        r = b - R @ c
+    A2 = A @ A
+    bt = A @ r
+    x = xP.copy()
+    eye = np.eye(n)
+    for sg, om in zip(sigma, omega):
+        x += om * np.linalg.solve(A2 - sg * eye, bt)
+    return x
+
+
+def sign_eig(A, decomposition=None):
+    """Exact sign(A) = X sign(Re Lambda) X^{-1} (spectral definition, Sec. 1 footnote)."""
+    w, X, Xinv = decomposition if decomposition is not None else eig(A)
+    return (X * np.where(w.real > 0, 1.0, -1.0)) @ Xinv
+
+
+def sign_schur(A):
+    """Exact sign(A) from the Schur form sorted right half-plane first.
+
+    With A = Q T Q^dag, T = [[T11, T12], [0, T22]], spec(T11) in Re > 0 and
+    spec(T22) in Re < 0: sign(T) = [[I, Z], [0, -I]] where T11 Z - Z T22 = 2 T12.
+    """
+    import scipy.linalg as sla
+    T, Q, sdim = sla.schur(A.astype(np.complex128), output="complex", sort="rhp")
+    n = A.shape[0]
+    T11, T12, T22 = T[:sdim, :sdim], T[:sdim, sdim:], T[sdim:, sdim:]
+    Z = sla.solve_sylvester(T11, -T22, 2 * T12)
+    S = np.zeros((n, n), dtype=np.complex128)
+    S[:sdim, :sdim] = np.eye(sdim)
+    S[sdim:, sdim:] = -np.eye(n - sdim)
+    S[:sdim, sdim:] = Z
+    return Q @ S @ Q.conj().T
+
+
+def rational_error_bound(lam_rest, s, c):
+    """max over the non-deflated eigenvalues of |sign(c lambda) - g_s(c lambda)|.
+
+    Closed form from eq. (6.1): for Re t > 0, g_s(t) = (1 - q^{2s}) / (1 + q^{2s})
+    with q = (t - 1)/(t + 1), so sign(t) - g_s(t) = 2 q^{2s} / (1 + q^{2s});
+    g_s is odd, which gives the Re t < 0 half.
+    """
+    t = c * np.asarray(lam_rest, dtype=np.complex128)
+    t = np.where(t.real > 0, t, -t)
+    q = (t - 1) / (t + 1)
+    q2s = q ** (2 * s)
+    return float(np.max(np.abs(2 * q2s / (1 + q2s)))) if t.size else 0.0
+
+
+def scale_from_bounds(a_min, b_max):
+    """c = ((m + r)(m - r))^{-1/2} of Sec. 6 for spectra in C(m,r) u C(-m,r).
+
+    With the circle fitted to |lambda| in [a_min, b_max] on the real axis,
+    m + r = b_max and m - r = a_min, so c = 1 / sqrt(a_min * b_max).
+    """
+    return 1.0 / math.sqrt(a_min * b_max)

@@ -1,0 +1,110 @@
+"""Pins for the oracle's Wilson kernel H_W(mu) = gamma5 D_W(mu) (Sec. 1).
+
+Checked against things other than itself: the free-field plane-wave closed
+form (fixes every sign, the e^{+-mu} placement and the boundary phase), the
+identity H_W(mu)^dag = H_W(-mu), Hermiticity at mu = 0, and gauge covariance
+(fixes U versus U^dag on forward and backward hops)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import seeded_inputs as si
+
+# gamma matrices written out from the chiral-basis definition
+_S = [np.array([[0, 1], [1, 0]]), np.array([[0, -1j], [1j, 0]]), np.array([[1, 0], [0, -1]])]
+_G = []
+for k in range(3):
+    g = np.zeros((4, 4), dtype=complex)
+    g[:2, 2:] = -1j * _S[k]
+    g[2:, :2] = 1j * _S[k]
+    _G.append(g)
+_gt = np.zeros((4, 4), dtype=complex)
+_gt[:2, 2:] = np.eye(2)
+_gt[2:, :2] = np.eye(2)
+_G.append(_gt)
+_G5 = _G[0] @ _G[1] @ _G[2] @ _G[3]
+
+
+def test_gamma_algebra():
+    for a in range(4):
+        for b in range(4):
+            ac = _G[a] @ _G[b] + _G[b] @ _G[a]
+            np.testing.assert_allclose(ac, 2 * np.eye(4) * (a == b), atol=1e-15)
+        np.testing.assert_allclose(_G[a], _G[a].conj().T, atol=0)
+    np.testing.assert_allclose(_G5, np.diag([1, 1, -1, -1]), atol=1e-15)
+
+
+def _coords(dims):
+    lx, ly, lz, lt = dims
+    t, z, y, x = np.meshgrid(range(lt), range(lz), range(ly), range(lx), indexing="ij")
+    return np.stack([x.ravel(), y.ravel(), z.ravel(), t.ravel()], axis=1)
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.3, 1.0])
+@pytest.mark.parametrize("dims,ap", [((4, 4, 4, 4), (0, 0, 0, 1)), ((3, 4, 5, 6), (0, 0, 0, 1)),
+                                     ((4, 3, 2, 5), (1, 0, 1, 0))])
+def test_free_field_plane_wave(mu, dims, ap):
+    """U = 1: H_W psi = gamma5 [(4+m) - sum cos q + i sum gamma sin q] psi, q_t = p_t - i mu."""
+    mass = -1.6
+    U = si.unit_links(dims)
+    X = _coords(dims)
+    rng = np.random.default_rng(5)
+    for trial in range(4):
+        nvec = [rng.integers(0, d) for d in dims]
+        p = np.array([(2 * np.pi * nvec[i] + (np.pi if ap[i] else 0.0)) / dims[i] for i in range(4)])
+        u = rng.standard_normal((4, 3)) + 1j * rng.standard_normal((4, 3))
+        phase = np.exp(1j * X @ p)
+        psi = (phase[:, None, None] * u[None]).reshape(-1)
+        q = p.astype(complex)
+        q[3] = p[3] - 1j * mu
+        Dp = (4 + mass - np.sum(np.cos(q))) * np.eye(4) + 1j * sum(_G[i] * np.sin(q[i]) for i in range(4))
+        expect = (phase[:, None, None] * (_G5 @ Dp @ u)[None]).reshape(-1)
+        got = O.hw(dims, U, psi, mu, mass, ap)
+        np.testing.assert_allclose(got, expect, atol=1e-12 * np.abs(expect).max())
+
+
+def test_gamma5_hermiticity_and_mu0_hermiticity():
+    dims = (3, 4, 3, 4)
+    U = si.random_su3_links(dims, 0.7, 42)
+    b = si.gaussian_field(dims, 1)
+    c = si.gaussian_field(dims, 2)
+    for mu in (0.3, 1.0):
+        lhs = np.vdot(c, O.hw(dims, U, b, mu))
+        rhs = np.vdot(O.hw(dims, U, c, -mu), b)
+        assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+        # and not Hermitian at mu != 0
+        assert abs(lhs - np.vdot(O.hw(dims, U, c, mu), b)) > 1e-3 * abs(lhs)
+    lhs = np.vdot(c, O.hw(dims, U, b, 0.0))
+    rhs = np.vdot(O.hw(dims, U, c, 0.0), b)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_gauge_covariance():
+    """U^G_nu(x) = G(x) U_nu(x) G(x+nu)^dag  =>  H[U^G] (G psi) = G H[U] psi."""
+    dims = (4, 3, 4, 5)
+    U = si.random_su3_links(dims, 0.7, 9)
+    G = si.random_gauge_transform(dims, 10)
+    X = _coords(dims)
+    vol = X.shape[0]
+    strides = np.array([1, dims[0], dims[0] * dims[1], dims[0] * dims[1] * dims[2]])
+    UG = np.empty_like(U)
+    for nu in range(4):
+        Y = X.copy()
+        Y[:, nu] = (Y[:, nu] + 1) % dims[nu]
+        fwd = Y @ strides
+        UG[:, nu] = G @ U[:, nu] @ np.conj(np.transpose(G[fwd], (0, 2, 1)))
+    psi = si.gaussian_field(dims, 3).reshape(vol, 4, 3)
+    Gpsi = np.einsum("sab,sxb->sxa", G, psi).reshape(-1)
+    for mu in (0.0, 0.4):
+        lhs = O.hw(dims, UG, Gpsi, mu)
+        rhs = np.einsum("sab,sxb->sxa", G, O.hw(dims, U, psi.reshape(-1), mu).reshape(vol, 4, 3)).reshape(-1)
+        np.testing.assert_allclose(lhs, rhs, atol=1e-12 * np.abs(rhs).max())
+
+
+def test_sites_subset_matches_full():
+    dims = (3, 4, 5, 2)
+    U = si.random_su3_links(dims, 0.7, 4)
+    psi = si.gaussian_field(dims, 5)
+    full = O.hw(dims, U, psi, 0.3).reshape(-1, 12)
+    sites = np.array([0, 7, 33, 119])
+    np.testing.assert_array_equal(O.hw_sites(dims, U, psi, sites, 0.3), full[sites])
