@@ -1,0 +1,192 @@
+/*
+ * sgn.h -- C ABI of the GB300 library for sign(H_W(mu)) b.
+ *
+ * Method: Bloch, Breu, Frommer, Heybrock, Schaefer, Wettig, "Krylov subspace
+ * methods and the sign function: multishifts and deflation in the
+ * non-Hermitian case" (Lattice 2009).  The library computes
+ *
+ *     x = R sign(Re Lambda) L^dag b + sum_i omega_i (A^2 - sigma_i)^{-1} A (I - P) b
+ *
+ * for A = H_W(mu) = gamma5 D_W(mu) (Sec. 1), P = R L^dag (Sec. 4, eqs. (4.1)-(4.3)),
+ * and the partial fractions of eq. (6.2), by restarted LR-deflated multishift
+ * FOM (Algorithm 1, "FOM-LR(m,k)") run on A^2 with right-hand side A (I - P) b.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  * Lattice dims = {Lx, Ly, Lz, Lt}; site = x + Lx*(y + Ly*(z + Lz*t)); V = Lx*Ly*Lz*Lt.
+ *  * Spinor field: V*12 complex numbers, [site][spin 4][colour 3], complex stored
+ *    as interleaved (re, im) pairs.  "nrhs fields" are nrhs such fields back to back.
+ *  * Gauge links: V*4*9 complex128, [site][dir x,y,z,t][row 3][col 3].
+ *  * D_W(mu) psi(x) = (4 + m_W) psi(x) - 1/2 sum_nu [(1 - gamma_nu) e^{+mu d_nu,t} U_nu(x) psi(x+nu)
+ *                    + (1 + gamma_nu) e^{-mu d_nu,t} U_nu(x-nu)^dag psi(x-nu)],
+ *    chiral Euclidean gamma matrices, gamma5 = diag(1, 1, -1, -1) in spin.
+ *  * Every call returns an sgn_status (0 = success); no C++ exception crosses
+ *    the ABI.  On failure sgn_last_error() returns a thread-local message.
+ *  * All device work runs on the stream given to sgn_create (or sgn_set_stream).
+ *    Calls that return results to the host synchronise that stream.
+ *  * Device memory is obtained through the caller's allocator callbacks when
+ *    given (e.g. a framework's caching allocator), else cudaMalloc/cudaFree.
+ *    The context owns everything it allocates and frees it in sgn_destroy.
+ *  * Not thread-safe per context: one host thread drives one context.
+ */
+#ifndef SGN_H
+#define SGN_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+#define SGN_EXTERN extern "C"
+#else
+#define SGN_EXTERN extern
+#endif
+#define SGN_API SGN_EXTERN __attribute__((visibility("default")))
+
+typedef struct sgn_ctx sgn_ctx;
+
+typedef enum {
+    SGN_OK = 0,
+    SGN_ERR_ARG = 1,            /* invalid argument (size, pointer, range) */
+    SGN_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    SGN_ERR_NOT_CONVERGED = 3,  /* max_cycles reached; x holds the last iterate */
+    SGN_ERR_BREAKDOWN = 4,      /* a shifted Hessenberg system was singular */
+    SGN_ERR_DEFLATION = 5,      /* deflation data missing, ambiguous or inaccurate */
+    SGN_ERR_NONFINITE = 6,      /* NaN or Inf met in the inputs or the iteration */
+    SGN_ERR_TIMEOUT = 7,        /* a bounded device-side wait gave up */
+    SGN_ERR_STATE = 8,          /* call order violated (e.g. apply before load_gauge) */
+    SGN_ERR_ALLOC = 9           /* device allocation failed */
+} sgn_status;
+
+/* Arithmetic of the solve.
+ *  SGN_PREC_FP64:  stencil, Krylov basis, coefficients and iterates in FP64.
+ *  SGN_PREC_MIXED: stencil and Krylov basis in FP32; inner products, norms,
+ *                  Hessenberg matrix, shifted solves, restart coefficients,
+ *                  deflation coefficients and iterates in FP64; followed by
+ *                  per-shift iterative refinement on the true FP64 residual. */
+typedef enum { SGN_PREC_FP64 = 0, SGN_PREC_MIXED = 1 } sgn_precision;
+
+/* Storage of the FP32 stencil's links (mixed form only). */
+typedef enum { SGN_LINKS_FP32 = 0, SGN_LINKS_BF16 = 1 } sgn_link_storage;
+
+/* Flags of sgn_apply. */
+#define SGN_APPLY_HOST_BUFFERS 1  /* b and x are host pointers (copied inside the call) */
+#define SGN_APPLY_ADJOINT 2       /* apply sign(H_W(-mu)) = sign(H_W(mu))^dag instead */
+
+typedef void* (*sgn_alloc_fn)(size_t bytes, void* user);
+typedef void (*sgn_free_fn)(void* ptr, size_t bytes, void* user);
+
+typedef struct {
+    int status;           /* sgn_status of the solve */
+    int cycles;           /* restart cycles of the multishift phase (max over columns) */
+    int matvecs;          /* applications of H_W per column (max over columns) */
+    int refine_rounds;    /* mixed form: refinement rounds */
+    int refine_cycles;    /* mixed form: restart cycles spent in refinement */
+    int breakdown;        /* 1 if some Arnoldi cycle met an invariant subspace */
+    double res_est;       /* max over columns and shifts of |rho_i| ||r|| / ||b~|| */
+    double err_est;       /* mixed form: estimated relative error of x after refinement */
+    double ms;            /* wall time of the call in milliseconds (device events) */
+} sgn_report;
+
+/* Create a context for a lattice of extent dims[4] = {Lx, Ly, Lz, Lt} (each >= 2).
+ * alloc/free may be NULL (then cudaMalloc/cudaFree); user is passed through.
+ * stream is a cudaStream_t (NULL = legacy default stream).
+ * Defaults: mu = 0, m_W = -1.6, antiperiodic in t only, no rational function,
+ * k = 40, tol = 1e-10, max_cycles = 1000, projection every cycle (Algorithm 1),
+ * FP64 form, no deflation.  Errors: SGN_ERR_ARG, SGN_ERR_CUDA. */
+SGN_API int sgn_create(sgn_ctx** out, const int dims[4], sgn_alloc_fn alloc, sgn_free_fn free_,
+                       void* user, void* stream);
+
+/* Release everything the context owns.  NULL is accepted. */
+SGN_API int sgn_destroy(sgn_ctx* ctx);
+
+/* Change the stream used by later calls. */
+SGN_API int sgn_set_stream(sgn_ctx* ctx, void* stream);
+
+/* Copy the gauge field (Sec. 1: the links of D_W) into the context: complex128,
+ * [site][dir][3][3]; on_device = 1 for a device pointer, 0 for host memory.
+ * The caller keeps ownership of `links`.  Non-finite entries: SGN_ERR_NONFINITE. */
+SGN_API int sgn_load_gauge(sgn_ctx* ctx, const double* links, int on_device);
+
+/* Quark chemical potential mu: forward time hops carry e^{+mu}, backward e^{-mu}
+ * (Sec. 1; non-Hermitian for mu != 0).  Drops any deflation data, which belongs
+ * to one operator (SGN_ERR_STATE on apply until it is set again). */
+SGN_API int sgn_set_mu(sgn_ctx* ctx, double mu);
+
+/* Wilson kernel mass m_W (the workloads use -1.6).  Drops deflation data. */
+SGN_API int sgn_set_kernel_mass(sgn_ctx* ctx, double m_w);
+
+/* Boundary conditions: antiperiodic[nu] = 1 flips the sign of hops that wrap
+ * direction nu.  Default {0, 0, 0, 1}.  Drops deflation data. */
+SGN_API int sgn_set_boundary(sgn_ctx* ctx, const int antiperiodic[4]);
+
+/* Kenney-Laub partial fractions, eq. (6.2), with the scale c of Sec. 6 folded in:
+ * sigma[i] = -tan^2(theta_i) / c^2, omega[i] = sec^2(theta_i) / (s c),
+ * theta_i = pi (i + 1/2) / (2 s), i = 0..s-1, so that
+ * g_s(c t) = t sum_i omega[i] / (t^2 - sigma[i]).  Host arrays of length s.
+ * Needs no context.  Errors: SGN_ERR_ARG (s < 1, c <= 0, NULL). */
+SGN_API int sgn_kenney_laub(int s, double c, double* sigma, double* omega);
+
+/* Shifts and weights of the rational function applied to A^2, eq. (2.1) read
+ * with t^2 (eq. (6.2)): x = A sum_i omega[i] (A^2 - sigma[i])^{-1} (I - P) b.
+ * Host arrays of length s, 1 <= s <= 32.  Copied. */
+SGN_API int sgn_set_rational(sgn_ctx* ctx, int s, const double* sigma, const double* omega);
+
+/* Restart length k (Algorithm 1's k = k_max, 1 <= k <= 64), stopping tolerance on
+ * max_i |rho_i| ||r|| / ||b~|| (eq. (3.1)), cycle cap, and whether the
+ * projection step r = (I - P) r runs after every cycle (Algorithm 1; 0 gives
+ * the variant without it compared in Fig. 2). */
+SGN_API int sgn_set_restart(sgn_ctx* ctx, int k, double tol, int max_cycles, int project_each_cycle);
+
+/* Arithmetic form (sgn_precision) and, for the mixed form, the relative error
+ * of x that refinement aims at (e.g. 1e-8).  link_storage selects FP32 or BF16
+ * links for the FP32 stencil. */
+SGN_API int sgn_set_precision(sgn_ctx* ctx, int precision, double target_rel_err, int link_storage);
+
+/* LR deflation data of Sec. 4 (eq. (4.1)): m right eigenvectors R and left
+ * eigenvectors L (each n x m, column j = one field of n = 12 V complex128,
+ * columns back to back), eigenvalues lambda (m complex128), normalised so that
+ * L^dag R = I_m.  on_device as in sgn_load_gauge.  Copied; m = 0 clears.
+ * Errors: SGN_ERR_ARG, SGN_ERR_NONFINITE. */
+SGN_API int sgn_set_deflation(sgn_ctx* ctx, int m, const double* R, const double* L,
+                              const double* lambda, int on_device);
+
+/* Compute LR deflation data on the GPU (the paper leaves the method open,
+ * Sec. 4): the m eigenpairs of H_W(mu) of smallest |lambda| (right vectors from
+ * H_W(mu), left vectors from H_W(-mu) = H_W(mu)^dag), biorthonormalised.
+ * `extra` further eigenvalues are computed to expose the gap.  eig_tol bounds
+ * the relative eigen-residual ||A r - lambda r|| / (|lambda| ||r||).
+ * lambda_out (host, 2*(m+extra) doubles, may be NULL) receives the eigenvalues.
+ * Errors: SGN_ERR_DEFLATION (no convergence or ambiguous selection). */
+SGN_API int sgn_build_deflation(sgn_ctx* ctx, int m, int extra, double eig_tol, double* lambda_out);
+
+/* Copy the current deflation data out: R, L (n x m each) and lambda (m), all
+ * complex128 host arrays sized by the caller (any may be NULL). */
+SGN_API int sgn_get_deflation(sgn_ctx* ctx, int* m, double* R, double* L, double* lambda);
+
+/* Apply the deflated rational sign approximation to nrhs fields (Algorithm 1):
+ * x = sign(H_W(mu)) b within the accuracy of eq. (6.2) and the tolerance.
+ * b, x: nrhs fields of complex128 each; device pointers unless flags has
+ * SGN_APPLY_HOST_BUFFERS.  Each column has its own Krylov space; the columns
+ * run in lockstep and share every link load of the stencil.  rep may be NULL.
+ * Returns SGN_ERR_NOT_CONVERGED (x holds the last iterate) if max_cycles is hit.
+ * Errors: SGN_ERR_STATE (no gauge / rational function), SGN_ERR_ARG, SGN_ERR_CUDA. */
+SGN_API int sgn_apply(sgn_ctx* ctx, const double* b, double* x, int nrhs, int flags, sgn_report* rep);
+
+/* As sgn_apply, and also return the iterate of every shifted system,
+ * x_shift[i] ~ (A^2 - sigma_i)^{-1} A (I - P) b (eq. (2.2) with the A^2 reading):
+ * s * nrhs fields, shift-major ([i][rhs]), device pointers. */
+SGN_API int sgn_apply_shifts(sgn_ctx* ctx, const double* b, double* x, double* x_shift, int nrhs,
+                             int flags, sgn_report* rep);
+
+/* The Wilson kernel alone: out = H_W(mu) in (or H_W(-mu) with adjoint = 1) for
+ * nrhs fields.  precision SGN_PREC_FP64: complex128 fields; SGN_PREC_MIXED:
+ * complex64 fields with the FP32 (or BF16, see sgn_set_precision) links.
+ * Device pointers; in and out must not overlap. */
+SGN_API int sgn_hw_apply(sgn_ctx* ctx, const void* in, void* out, int nrhs, int precision, int adjoint);
+
+/* Thread-local message for the last failing call of this thread. */
+SGN_API const char* sgn_last_error(void);
+
+/* Library version string. */
+SGN_API const char* sgn_version(void);
+
+#endif /* SGN_H */

@@ -1,0 +1,242 @@
+"""sign(H_W(mu)) b on GB300: restarted LR-deflated multishift FOM (Bloch et al., Lattice 2009).
+
+Python layer over the C ABI of ``include/sgn.h``.  It only marshals
+arguments: every step of the method runs in the CUDA kernels of libsgn.so.
+PyTorch provides device memory (through its caching allocator) and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _abi
+from ._abi import (APPLY_ADJOINT, APPLY_HOST_BUFFERS, LINKS_BF16, LINKS_FP32, PREC_FP64, PREC_MIXED, Report,
+                   SignError, check, lib)
+
+__all__ = ["SignContext", "kenney_laub", "SignError", "PREC_FP64", "PREC_MIXED", "LINKS_FP32", "LINKS_BF16",
+           "sign_apply", "SignApply"]
+
+
+def kenney_laub(s: int, c: float = 1.0):
+    """Shifts and weights of eq. (6.2) with the scale c folded in (sgn_kenney_laub)."""
+    sig = np.empty(s)
+    om = np.empty(s)
+    check(lib().sgn_kenney_laub(int(s), float(c), sig.ctypes.data, om.ctypes.data))
+    return sig, om
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class SignContext:
+    """One lattice, one operator H_W(mu), one GPU.  Wraps an ``sgn_ctx``."""
+
+    def __init__(self, dims, mu=0.0, mass=-1.6, antiperiodic=(0, 0, 0, 1), device=None, stream=None,
+                 torch_allocator=True):
+        torch = _torch()
+        self.dims = tuple(int(d) for d in dims)
+        self.vol = int(np.prod(self.dims))
+        self.n = 12 * self.vol
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        torch.cuda.set_device(self.device)
+        self._stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        if torch_allocator:
+            dev = self.device.index
+
+            def _alloc(nbytes, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, self._stream)
+                except Exception:
+                    return None
+
+            def _free(ptr, nbytes, user):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._alloc_cb = _abi.ALLOC_FN(_alloc)
+            self._free_cb = _abi.FREE_FN(_free)
+        else:
+            self._alloc_cb = _abi.ALLOC_FN()
+            self._free_cb = _abi.FREE_FN()
+        h = C.c_void_p()
+        dims_c = (C.c_int * 4)(*self.dims)
+        check(lib().sgn_create(C.byref(h), dims_c, self._alloc_cb, self._free_cb, None,
+                               C.c_void_p(self._stream.cuda_stream)))
+        self._h = h
+        self.s = 0
+        self.m = 0
+        self.set_mu(mu)
+        self.set_kernel_mass(mass)
+        self.set_boundary(antiperiodic)
+
+    # -- lifetime ----------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().sgn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- parameters ----------------------------------------------------------
+    def set_mu(self, mu):
+        self.mu = float(mu)
+        check(lib().sgn_set_mu(self._h, self.mu))
+
+    def set_kernel_mass(self, m_w):
+        self.mass = float(m_w)
+        check(lib().sgn_set_kernel_mass(self._h, self.mass))
+
+    def set_boundary(self, antiperiodic):
+        check(lib().sgn_set_boundary(self._h, (C.c_int * 4)(*[int(a) for a in antiperiodic])))
+
+    def set_rational(self, sigma, omega):
+        sig = np.ascontiguousarray(sigma, dtype=np.float64)
+        om = np.ascontiguousarray(omega, dtype=np.float64)
+        check(lib().sgn_set_rational(self._h, sig.size, sig.ctypes.data, om.ctypes.data))
+        self.s = sig.size
+
+    def set_restart(self, k=40, tol=1e-10, max_cycles=1000, project_each_cycle=True):
+        check(lib().sgn_set_restart(self._h, int(k), float(tol), int(max_cycles), int(bool(project_each_cycle))))
+
+    def set_precision(self, precision=PREC_FP64, target_rel_err=1e-8, link_storage=LINKS_FP32):
+        check(lib().sgn_set_precision(self._h, int(precision), float(target_rel_err), int(link_storage)))
+
+    # -- data ----------------------------------------------------------------
+    def _as_c128(self, a):
+        torch = _torch()
+        if isinstance(a, torch.Tensor):
+            t = a.to(torch.complex128).contiguous()
+            return t, int(t.data_ptr()), int(t.is_cuda)
+        arr = np.ascontiguousarray(a, dtype=np.complex128)
+        return arr, arr.ctypes.data, 0
+
+    def load_gauge(self, links):
+        """links: (V, 4, 3, 3) complex128, torch (CPU or CUDA) or numpy."""
+        keep, ptr, on_dev = self._as_c128(links)
+        size = keep.numel() if hasattr(keep, "numel") else keep.size
+        if size != self.vol * 36:
+            raise ValueError(f"links must hold V*36 = {self.vol * 36} complex entries, got {size}")
+        check(lib().sgn_load_gauge(self._h, C.c_void_p(ptr), on_dev))
+
+    def set_deflation(self, R, L, lam):
+        """R, L: (n, m) right / left eigenvectors with L^dag R = I; lam: (m,) eigenvalues."""
+        torch = _torch()
+        if R is None or (hasattr(R, "shape") and R.shape[1] == 0):
+            check(lib().sgn_set_deflation(self._h, 0, None, None, None, 0))
+            self.m = 0
+            return
+        m = R.shape[1]
+        if isinstance(R, torch.Tensor):
+            Rt = R.transpose(0, 1).to(torch.complex128).contiguous()
+            Lt = L.transpose(0, 1).to(torch.complex128).contiguous()
+            lt = torch.as_tensor(lam).to(device=Rt.device, dtype=torch.complex128).contiguous()
+            ptrs = (Rt.data_ptr(), Lt.data_ptr(), lt.data_ptr())
+            on_dev = int(Rt.is_cuda)
+            if on_dev != int(lt.is_cuda):
+                raise ValueError("R, L and lam must live on the same device")
+            keep = (Rt, Lt, lt)
+        else:
+            Rt = np.ascontiguousarray(np.asarray(R).T, dtype=np.complex128)
+            Lt = np.ascontiguousarray(np.asarray(L).T, dtype=np.complex128)
+            lt = np.ascontiguousarray(lam, dtype=np.complex128)
+            ptrs = (Rt.ctypes.data, Lt.ctypes.data, lt.ctypes.data)
+            on_dev = 0
+            keep = (Rt, Lt, lt)
+        check(lib().sgn_set_deflation(self._h, int(m), C.c_void_p(ptrs[0]), C.c_void_p(ptrs[1]),
+                                      C.c_void_p(ptrs[2]), on_dev))
+        del keep
+        self.m = m
+
+    def build_deflation(self, m, extra=4, eig_tol=1e-10):
+        lam = np.empty(m + extra, dtype=np.complex128)
+        check(lib().sgn_build_deflation(self._h, int(m), int(extra), float(eig_tol), lam.ctypes.data))
+        self.m = m
+        return lam
+
+    def get_deflation(self):
+        mm = C.c_int()
+        check(lib().sgn_get_deflation(self._h, C.byref(mm), None, None, None))
+        m = mm.value
+        if m == 0:
+            return None, None, np.zeros(0, dtype=np.complex128)
+        R = np.empty((m, self.n), dtype=np.complex128)
+        L = np.empty((m, self.n), dtype=np.complex128)
+        lam = np.empty(m, dtype=np.complex128)
+        check(lib().sgn_get_deflation(self._h, C.byref(mm), R.ctypes.data, L.ctypes.data, lam.ctypes.data))
+        return R.T, L.T, lam
+
+    # -- application ----------------------------------------------------------
+    def apply(self, b, adjoint=False, shifts=False):
+        """x = sign(H_W(+-mu)) b for b of shape (nrhs, n) or (n,).
+
+        CUDA tensors run in place on the device; numpy arrays use the host-buffer
+        mode of the ABI (copies inside the call).  Returns (x, report) or, with
+        shifts=True (device only), (x, x_shift, report) with x_shift of shape
+        (s, nrhs, n)."""
+        torch = _torch()
+        flags = APPLY_ADJOINT if adjoint else 0
+        rep = Report()
+        if isinstance(b, torch.Tensor) and b.is_cuda:
+            squeeze = b.dim() == 1
+            bb = b.reshape(-1, self.n).to(torch.complex128).contiguous()
+            nrhs = bb.shape[0]
+            x = torch.empty_like(bb)
+            if shifts:
+                xs = torch.empty((self.s, nrhs, self.n), dtype=torch.complex128, device=bb.device)
+                code = lib().sgn_apply_shifts(self._h, C.c_void_p(bb.data_ptr()), C.c_void_p(x.data_ptr()),
+                                              C.c_void_p(xs.data_ptr()), nrhs, flags, C.byref(rep))
+            else:
+                code = lib().sgn_apply(self._h, C.c_void_p(bb.data_ptr()), C.c_void_p(x.data_ptr()), nrhs, flags,
+                                       C.byref(rep))
+            if code not in (0, 3):
+                check(code)
+            out = x.reshape(-1) if squeeze else x
+            if shifts:
+                return out, xs, rep.as_dict()
+            return out, rep.as_dict()
+        if shifts:
+            raise ValueError("per-shift iterates need CUDA tensors")
+        arr = np.ascontiguousarray(b, dtype=np.complex128)
+        squeeze = arr.ndim == 1
+        arr2 = arr.reshape(-1, self.n)
+        x = np.empty_like(arr2)
+        code = lib().sgn_apply(self._h, C.c_void_p(arr2.ctypes.data), C.c_void_p(x.ctypes.data), arr2.shape[0],
+                               flags | APPLY_HOST_BUFFERS, C.byref(rep))
+        if code not in (0, 3):
+            check(code)
+        return (x.reshape(-1) if squeeze else x), rep.as_dict()
+
+    def hw(self, psi, precision=PREC_FP64, adjoint=False):
+        """H_W(mu) psi (or H_W(-mu) psi) for CUDA fields of shape (nrhs, n) or (n,)."""
+        torch = _torch()
+        dt = torch.complex128 if precision == PREC_FP64 else torch.complex64
+        x = psi.to(dt).contiguous()
+        out = torch.empty_like(x)
+        nrhs = x.numel() // self.n
+        check(lib().sgn_hw_apply(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()), nrhs,
+                                 int(precision), int(bool(adjoint))))
+        return out
+
+
+def sign_apply(ctx: SignContext, b, adjoint=False):
+    """x = sign(H_W(mu)) b through an existing context."""
+    return ctx.apply(b, adjoint=adjoint)[0]
+
+
+def __getattr__(name):
+    if name == "SignApply":
+        from .autograd import SignApply
+        return SignApply
+    raise AttributeError(name)

@@ -1,0 +1,346 @@
+// The C ABI declared in include/sgn.h: argument checks, context state, host
+// and device copies, stream ordering.  Numerical work lives in the kernels.
+#include "ctx.cuh"
+
+#include <cmath>
+#include <cstring>
+#include <new>
+
+namespace sgn {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+namespace {
+
+int fail(int code, const std::string& msg) {
+    set_error(msg);
+    return code;
+}
+
+bool finite_host(const double* p, size_t count) {
+    for (size_t i = 0; i < count; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+// Order the internal stream after the caller's stream (entry) and the caller's
+// stream after the internal one (exit).
+int enter(sgn_ctx* c) {
+    SGN_CUDA(cudaEventRecord(c->ev_in, c->user_stream));
+    SGN_CUDA(cudaStreamWaitEvent(c->work, c->ev_in, 0));
+    return SGN_OK;
+}
+int leave(sgn_ctx* c) {
+    SGN_CUDA(cudaEventRecord(c->ev_out, c->work));
+    SGN_CUDA(cudaStreamWaitEvent(c->user_stream, c->ev_out, 0));
+    return SGN_OK;
+}
+
+int drop_deflation(sgn_ctx* c) {
+    c->m = 0;
+    c->lam.clear();
+    return SGN_OK;
+}
+
+int copy_in(sgn_ctx* c, void* dst, const void* src, size_t bytes, int on_device) {
+    SGN_CUDA(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                             c->work));
+    return SGN_OK;
+}
+
+}  // namespace
+}  // namespace sgn
+
+using namespace sgn;
+
+SGN_API const char* sgn_last_error(void) { return g_last_error.c_str(); }
+
+SGN_API const char* sgn_version(void) { return "sgn 0.1 (sm_103a)"; }
+
+SGN_API int sgn_create(sgn_ctx** out, const int dims[4], sgn_alloc_fn alloc, sgn_free_fn free_, void* user,
+                       void* stream) {
+    if (!out || !dims) return fail(SGN_ERR_ARG, "sgn_create: NULL argument");
+    *out = nullptr;
+    for (int d = 0; d < 4; ++d)
+        if (dims[d] < 2) return fail(SGN_ERR_ARG, "sgn_create: every lattice extent must be >= 2");
+    if ((alloc == nullptr) != (free_ == nullptr))
+        return fail(SGN_ERR_ARG, "sgn_create: give both allocator callbacks or neither");
+    sgn_ctx* c = new (std::nothrow) sgn_ctx();
+    if (!c) return fail(SGN_ERR_ALLOC, "sgn_create: out of host memory");
+    for (int d = 0; d < 4; ++d) c->dims[d] = dims[d];
+    c->vol = (int64_t)dims[0] * dims[1] * dims[2] * dims[3];
+    c->n = 12 * c->vol;
+    c->alloc = alloc;
+    c->free_ = free_;
+    c->user = user;
+    c->user_stream = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->work, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev_t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev_t1);
+    if (e == cudaSuccess) e = prepare_small_kernels();
+    if (e != cudaSuccess) {
+        set_error(std::string("sgn_create: ") + cudaGetErrorString(e));
+        sgn_destroy(c);
+        return SGN_ERR_CUDA;
+    }
+    *out = c;
+    return SGN_OK;
+}
+
+SGN_API int sgn_destroy(sgn_ctx* c) {
+    if (!c) return SGN_OK;
+    if (c->work) cudaStreamSynchronize(c->work);
+    release_engines(c);
+    dev_free(c, c->U64);
+    dev_free(c, c->U32);
+    dev_free(c, c->U16);
+    dev_free(c, c->R64);
+    dev_free(c, c->L64);
+    dev_free(c, c->R32);
+    dev_free(c, c->L32);
+    dev_free(c, c->lam_dev);
+    dev_free(c, c->lamc_dev);
+    dev_free(c, c->io);
+    dev_free(c, c->stage);
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
+    if (c->ev_t0) cudaEventDestroy(c->ev_t0);
+    if (c->ev_t1) cudaEventDestroy(c->ev_t1);
+    if (c->work) cudaStreamDestroy(c->work);
+    delete c;
+    return SGN_OK;
+}
+
+SGN_API int sgn_set_stream(sgn_ctx* c, void* stream) {
+    if (!c) return fail(SGN_ERR_ARG, "sgn_set_stream: NULL context");
+    c->user_stream = reinterpret_cast<cudaStream_t>(stream);
+    return SGN_OK;
+}
+
+SGN_API int sgn_load_gauge(sgn_ctx* c, const double* links, int on_device) {
+    if (!c || !links) return fail(SGN_ERR_ARG, "sgn_load_gauge: NULL argument");
+    const size_t count = (size_t)c->vol * 36;  // complex entries
+    if (!on_device && !finite_host(links, 2 * count))
+        return fail(SGN_ERR_NONFINITE, "sgn_load_gauge: non-finite link entry");
+    SGN_CHECK(enter(c));
+    SGN_CHECK(dev_alloc(c, c->U64, count * sizeof(double2)));
+    SGN_CHECK(dev_alloc(c, c->U32, count * sizeof(float2)));
+    SGN_CHECK(dev_alloc(c, c->U16, count * sizeof(__nv_bfloat162)));
+    SGN_CHECK(copy_in(c, c->U64.p, links, count * sizeof(double2), on_device));
+    SGN_CUDA(convert_f64_to_f32(as<double2>(c->U64), as<float2>(c->U32), (int64_t)count, c->work));
+    SGN_CUDA(links_f64_to_bf16(as<double2>(c->U64), as<__nv_bfloat162>(c->U16), (int64_t)count, c->work));
+    SGN_CUDA(cudaStreamSynchronize(c->work));
+    SGN_CHECK(leave(c));
+    c->have_gauge = true;
+    drop_deflation(c);
+    return SGN_OK;
+}
+
+SGN_API int sgn_set_mu(sgn_ctx* c, double mu) {
+    if (!c || !std::isfinite(mu)) return fail(SGN_ERR_ARG, "sgn_set_mu: bad argument");
+    if (mu != c->mu) drop_deflation(c);
+    c->mu = mu;
+    return SGN_OK;
+}
+
+SGN_API int sgn_set_kernel_mass(sgn_ctx* c, double m_w) {
+    if (!c || !std::isfinite(m_w)) return fail(SGN_ERR_ARG, "sgn_set_kernel_mass: bad argument");
+    if (m_w != c->mass) drop_deflation(c);
+    c->mass = m_w;
+    return SGN_OK;
+}
+
+SGN_API int sgn_set_boundary(sgn_ctx* c, const int antiperiodic[4]) {
+    if (!c || !antiperiodic) return fail(SGN_ERR_ARG, "sgn_set_boundary: NULL argument");
+    bool changed = false;
+    for (int d = 0; d < 4; ++d) {
+        int v = antiperiodic[d] ? 1 : 0;
+        changed = changed || v != c->ap[d];
+        c->ap[d] = v;
+    }
+    if (changed) drop_deflation(c);
+    return SGN_OK;
+}
+
+SGN_API int sgn_kenney_laub(int s, double c, double* sigma, double* omega) {
+    if (s < 1 || !(c > 0) || !std::isfinite(c) || !sigma || !omega)
+        return fail(SGN_ERR_ARG, "sgn_kenney_laub: need s >= 1, finite c > 0 and output arrays");
+    // eq. (6.2): theta_i = (pi / 2s)(i - 1/2), i = 1..s
+    for (int i = 0; i < s; ++i) {
+        const double th = M_PI * (i + 0.5) / (2.0 * s);
+        const double t = std::tan(th), co = std::cos(th);
+        sigma[i] = -(t * t) / (c * c);
+        omega[i] = 1.0 / (s * co * co * c);
+    }
+    return SGN_OK;
+}
+
+SGN_API int sgn_set_rational(sgn_ctx* c, int s, const double* sigma, const double* omega) {
+    if (!c || !sigma || !omega || s < 1 || s > 32) return fail(SGN_ERR_ARG, "sgn_set_rational: need 1 <= s <= 32");
+    if (!finite_host(sigma, s) || !finite_host(omega, s))
+        return fail(SGN_ERR_ARG, "sgn_set_rational: non-finite shift or weight");
+    c->sigma.assign(sigma, sigma + s);
+    c->omega.assign(omega, omega + s);
+    return SGN_OK;
+}
+
+SGN_API int sgn_set_restart(sgn_ctx* c, int k, double tol, int max_cycles, int project_each_cycle) {
+    if (!c || k < 1 || k > 64 || !(tol > 0) || max_cycles < 1)
+        return fail(SGN_ERR_ARG, "sgn_set_restart: need 1 <= k <= 64, tol > 0, max_cycles >= 1");
+    c->k = k;
+    c->tol = tol;
+    c->max_cycles = max_cycles;
+    c->project = project_each_cycle ? 1 : 0;
+    return SGN_OK;
+}
+
+SGN_API int sgn_set_precision(sgn_ctx* c, int precision, double target_rel_err, int link_storage) {
+    if (!c || (precision != SGN_PREC_FP64 && precision != SGN_PREC_MIXED) || !(target_rel_err > 0) ||
+        (link_storage != SGN_LINKS_FP32 && link_storage != SGN_LINKS_BF16))
+        return fail(SGN_ERR_ARG, "sgn_set_precision: bad argument");
+    c->precision = precision;
+    c->target = target_rel_err;
+    c->link_storage = link_storage;
+    return SGN_OK;
+}
+
+SGN_API int sgn_set_deflation(sgn_ctx* c, int m, const double* R, const double* L, const double* lambda,
+                              int on_device) {
+    if (!c || m < 0 || m > 64) return fail(SGN_ERR_ARG, "sgn_set_deflation: need 0 <= m <= 64");
+    if (m == 0) return drop_deflation(c);
+    if (!R || !L || !lambda) return fail(SGN_ERR_ARG, "sgn_set_deflation: NULL argument");
+    const size_t cnt = (size_t)c->n * m;
+    std::vector<double> lam(2 * (size_t)m);
+    if (on_device) {
+        SGN_CUDA(cudaMemcpy(lam.data(), lambda, sizeof(double) * 2 * m, cudaMemcpyDeviceToHost));
+    } else {
+        std::memcpy(lam.data(), lambda, sizeof(double) * 2 * m);
+        if (!finite_host(R, 2 * cnt) || !finite_host(L, 2 * cnt))
+            return fail(SGN_ERR_NONFINITE, "sgn_set_deflation: non-finite vector entry");
+    }
+    if (!finite_host(lam.data(), 2 * (size_t)m)) return fail(SGN_ERR_NONFINITE, "sgn_set_deflation: bad lambda");
+    for (int j = 0; j < m; ++j)
+        if (lam[2 * j] == 0.0)
+            return fail(SGN_ERR_DEFLATION, "sgn_set_deflation: an eigenvalue on the imaginary axis has no sign");
+    SGN_CHECK(enter(c));
+    SGN_CHECK(dev_alloc(c, c->R64, cnt * sizeof(double2)));
+    SGN_CHECK(dev_alloc(c, c->L64, cnt * sizeof(double2)));
+    SGN_CHECK(dev_alloc(c, c->R32, cnt * sizeof(float2)));
+    SGN_CHECK(dev_alloc(c, c->L32, cnt * sizeof(float2)));
+    SGN_CHECK(dev_alloc(c, c->lam_dev, (size_t)m * sizeof(double2)));
+    SGN_CHECK(dev_alloc(c, c->lamc_dev, (size_t)m * sizeof(double2)));
+    SGN_CHECK(copy_in(c, c->R64.p, R, cnt * sizeof(double2), on_device));
+    SGN_CHECK(copy_in(c, c->L64.p, L, cnt * sizeof(double2), on_device));
+    SGN_CUDA(convert_f64_to_f32(as<double2>(c->R64), as<float2>(c->R32), (int64_t)cnt, c->work));
+    SGN_CUDA(convert_f64_to_f32(as<double2>(c->L64), as<float2>(c->L32), (int64_t)cnt, c->work));
+    std::vector<double> lamc(lam);
+    for (int j = 0; j < m; ++j) lamc[2 * j + 1] = -lamc[2 * j + 1];
+    SGN_CUDA(cudaMemcpyAsync(c->lam_dev.p, lam.data(), sizeof(double) * 2 * m, cudaMemcpyHostToDevice, c->work));
+    SGN_CUDA(cudaMemcpyAsync(c->lamc_dev.p, lamc.data(), sizeof(double) * 2 * m, cudaMemcpyHostToDevice, c->work));
+    SGN_CUDA(cudaStreamSynchronize(c->work));
+    SGN_CHECK(leave(c));
+    c->lam.resize(m);
+    for (int j = 0; j < m; ++j) c->lam[j] = {lam[2 * j], lam[2 * j + 1]};
+    c->m = m;
+    return SGN_OK;
+}
+
+SGN_API int sgn_get_deflation(sgn_ctx* c, int* m, double* R, double* L, double* lambda) {
+    if (!c) return fail(SGN_ERR_ARG, "sgn_get_deflation: NULL context");
+    if (m) *m = c->m;
+    if (c->m == 0) return SGN_OK;
+    const size_t cnt = (size_t)c->n * c->m;
+    SGN_CUDA(cudaStreamSynchronize(c->work));
+    if (R) SGN_CUDA(cudaMemcpy(R, c->R64.p, cnt * sizeof(double2), cudaMemcpyDeviceToHost));
+    if (L) SGN_CUDA(cudaMemcpy(L, c->L64.p, cnt * sizeof(double2), cudaMemcpyDeviceToHost));
+    if (lambda)
+        for (int j = 0; j < c->m; ++j) {
+            lambda[2 * j] = c->lam[j].real();
+            lambda[2 * j + 1] = c->lam[j].imag();
+        }
+    return SGN_OK;
+}
+
+SGN_API int sgn_build_deflation(sgn_ctx* c, int m, int extra, double eig_tol, double* lambda_out) {
+    if (!c || m < 1 || m > 64 || extra < 0 || m + extra > 64 || !(eig_tol > 0))
+        return fail(SGN_ERR_ARG, "sgn_build_deflation: need 1 <= m, m + extra <= 64, eig_tol > 0");
+    if (!c->have_gauge) return fail(SGN_ERR_STATE, "sgn_build_deflation: load the gauge field first");
+    SGN_CHECK(enter(c));
+    int st = build_deflation(c, m, extra, eig_tol, lambda_out);
+    SGN_CHECK(leave(c));
+    return st;
+}
+
+namespace {
+
+int apply_common(sgn_ctx* c, const double* b, double* x, double* x_shift, int nrhs, int flags, sgn_report* rep) {
+    if (!c || !b || !x || nrhs < 1) return fail(SGN_ERR_ARG, "sgn_apply: bad argument");
+    if (!c->have_gauge) return fail(SGN_ERR_STATE, "sgn_apply: load the gauge field first");
+    if (c->sigma.empty()) return fail(SGN_ERR_STATE, "sgn_apply: set the rational function first");
+    if (x_shift && (flags & SGN_APPLY_HOST_BUFFERS))
+        return fail(SGN_ERR_ARG, "sgn_apply_shifts: per-shift output needs device buffers");
+    const bool host = flags & SGN_APPLY_HOST_BUFFERS;
+    const bool adjoint = flags & SGN_APPLY_ADJOINT;
+    const size_t fbytes = (size_t)c->n * nrhs * sizeof(double2);
+    if (host && !finite_host(b, 2 * (size_t)c->n * nrhs))
+        return fail(SGN_ERR_NONFINITE, "sgn_apply: non-finite entry in b");
+    SGN_CHECK(enter(c));
+    SGN_CUDA(cudaEventRecord(c->ev_t0, c->work));
+    const double2* bd = reinterpret_cast<const double2*>(b);
+    double2* xd = reinterpret_cast<double2*>(x);
+    if (host) {
+        SGN_CHECK(dev_alloc(c, c->stage, 2 * fbytes));
+        double2* sb = as<double2>(c->stage);
+        SGN_CUDA(cudaMemcpyAsync(sb, b, fbytes, cudaMemcpyHostToDevice, c->work));
+        bd = sb;
+        xd = sb + (size_t)c->n * nrhs;
+    }
+    int status = solve(c, bd, xd, reinterpret_cast<double2*>(x_shift), nrhs, adjoint, rep);
+    if (host && (status == SGN_OK || status == SGN_ERR_NOT_CONVERGED))
+        SGN_CUDA(cudaMemcpyAsync(x, xd, fbytes, cudaMemcpyDeviceToHost, c->work));
+    SGN_CUDA(cudaEventRecord(c->ev_t1, c->work));
+    SGN_CUDA(cudaEventSynchronize(c->ev_t1));
+    if (rep) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, c->ev_t0, c->ev_t1);
+        rep->ms = ms;
+    }
+    SGN_CHECK(leave(c));
+    return status;
+}
+
+}  // namespace
+
+SGN_API int sgn_apply(sgn_ctx* c, const double* b, double* x, int nrhs, int flags, sgn_report* rep) {
+    return apply_common(c, b, x, nullptr, nrhs, flags, rep);
+}
+
+SGN_API int sgn_apply_shifts(sgn_ctx* c, const double* b, double* x, double* x_shift, int nrhs, int flags,
+                             sgn_report* rep) {
+    if (!x_shift) return fail(SGN_ERR_ARG, "sgn_apply_shifts: NULL x_shift");
+    return apply_common(c, b, x, x_shift, nrhs, flags, rep);
+}
+
+SGN_API int sgn_hw_apply(sgn_ctx* c, const void* in, void* out, int nrhs, int precision, int adjoint) {
+    if (!c || !in || !out || nrhs < 1) return fail(SGN_ERR_ARG, "sgn_hw_apply: bad argument");
+    if (in == out) return fail(SGN_ERR_ARG, "sgn_hw_apply: in and out must differ");
+    if (!c->have_gauge) return fail(SGN_ERR_STATE, "sgn_hw_apply: load the gauge field first");
+    SGN_CHECK(enter(c));
+    if (precision == SGN_PREC_FP64) {
+        SGN_CUDA(apply_hw64(c, reinterpret_cast<double2*>(out), reinterpret_cast<const double2*>(in), nrhs,
+                            adjoint != 0, nullptr, c->work));
+    } else if (precision == SGN_PREC_MIXED) {
+        SGN_CUDA(apply_hw32(c, reinterpret_cast<float2*>(out), reinterpret_cast<const float2*>(in), nrhs,
+                            adjoint != 0, nullptr, c->work));
+    } else {
+        return fail(SGN_ERR_ARG, "sgn_hw_apply: unknown precision");
+    }
+    SGN_CHECK(leave(c));
+    return SGN_OK;
+}

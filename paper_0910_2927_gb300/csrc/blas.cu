@@ -1,0 +1,628 @@
+// Tall-skinny vector kernels: multi-dot products with deterministic two-stage
+// FP64 reductions, the fused passes of classical Gram-Schmidt with
+// reorthogonalisation (CGS2) for the Arnoldi relation eq. (2.4), the basis
+// update of Algorithm 1 and the LR projection r -> (I - R L^dag) r (Sec. 4).
+//
+// Element granularity is a 16-byte "pack": one complex128 or two complex64.
+// A thread owns PK packs of one column; a CTA of NT threads owns NT*PK
+// consecutive packs.  Dot products: each thread forms its PK pack products
+// (in FP32 for complex64 storage, i.e. chunks of 8 complex products), promotes
+// them to FP64 and the rest of the reduction -- warp shuffles, the CTA sum and
+// the per-column sum over CTAs -- is FP64 in a fixed order (no atomics).
+#include "blas.cuh"
+
+namespace sgn {
+namespace {
+
+constexpr int NT = 256;
+constexpr int NWARP = NT / 32;
+constexpr int PK = 4;
+constexpr int MAXSLOT = 72;  // >= kmax + 2 and >= deflation size + 1
+
+template <class T>
+struct Ops;
+
+template <>
+struct Ops<double2> {
+    using P = double2;
+    using C = double2;  // coefficient type used in the arithmetic
+    static constexpr int CPX = 1;
+    static __device__ __forceinline__ P ld_ro(const double2* b, int64_t pk) { return __ldg(b + pk); }
+    static __device__ __forceinline__ P ld(const double2* b, int64_t pk) { return b[pk]; }
+    static __device__ __forceinline__ void st(double2* b, int64_t pk, P v) { b[pk] = v; }
+    static __device__ __forceinline__ P zero() { return make_double2(0, 0); }
+    static __device__ __forceinline__ C coef(double2 c) { return c; }
+    // conj(v) * w
+    static __device__ __forceinline__ double2 dot(P v, P w) { return cconjmul(v, w); }
+    static __device__ __forceinline__ double nrm2(P w) { return w.x * w.x + w.y * w.y; }
+    // w -= c v
+    static __device__ __forceinline__ void sub_cv(P& w, C c, P v) {
+        w.x = fma(-c.x, v.x, w.x);
+        w.x = fma(c.y, v.y, w.x);
+        w.y = fma(-c.x, v.y, w.y);
+        w.y = fma(-c.y, v.x, w.y);
+    }
+    // a += c v
+    static __device__ __forceinline__ void add_cv(P& a, C c, P v) {
+        a.x = fma(c.x, v.x, a.x);
+        a.x = fma(-c.y, v.y, a.x);
+        a.y = fma(c.x, v.y, a.y);
+        a.y = fma(c.y, v.x, a.y);
+    }
+    static __device__ __forceinline__ P scal(P v, double s) { return make_double2(v.x * s, v.y * s); }
+    // x (complex128 array, CPX entries per pack) += v
+    static __device__ __forceinline__ void add_to(double2* x, int64_t pk, P v) {
+        double2 a = x[pk];
+        x[pk] = make_double2(a.x + v.x, a.y + v.y);
+    }
+    // x += c v computed in FP64
+    static __device__ __forceinline__ void add_cv_f64(double2 acc[1], double2 c, P v) {
+        acc[0].x = fma(c.x, v.x, acc[0].x);
+        acc[0].x = fma(-c.y, v.y, acc[0].x);
+        acc[0].y = fma(c.x, v.y, acc[0].y);
+        acc[0].y = fma(c.y, v.x, acc[0].y);
+    }
+};
+
+template <>
+struct Ops<float2> {
+    using P = float4;
+    using C = float2;
+    static constexpr int CPX = 2;
+    static __device__ __forceinline__ P ld_ro(const float2* b, int64_t pk) {
+        return __ldg(reinterpret_cast<const float4*>(b) + pk);
+    }
+    static __device__ __forceinline__ P ld(const float2* b, int64_t pk) { return reinterpret_cast<const float4*>(b)[pk]; }
+    static __device__ __forceinline__ void st(float2* b, int64_t pk, P v) { reinterpret_cast<float4*>(b)[pk] = v; }
+    static __device__ __forceinline__ P zero() { return make_float4(0, 0, 0, 0); }
+    static __device__ __forceinline__ C coef(double2 c) { return make_float2((float)c.x, (float)c.y); }
+    static __device__ __forceinline__ double2 dot(P v, P w) {
+        float re = v.x * w.x;
+        re = fmaf(v.y, w.y, re);
+        re = fmaf(v.z, w.z, re);
+        re = fmaf(v.w, w.w, re);
+        float im = v.x * w.y;
+        im = fmaf(-v.y, w.x, im);
+        im = fmaf(v.z, w.w, im);
+        im = fmaf(-v.w, w.z, im);
+        return make_double2(re, im);
+    }
+    static __device__ __forceinline__ double nrm2(P w) {
+        float a = w.x * w.x;
+        a = fmaf(w.y, w.y, a);
+        a = fmaf(w.z, w.z, a);
+        a = fmaf(w.w, w.w, a);
+        return a;
+    }
+    static __device__ __forceinline__ void sub_cv(P& w, C c, P v) {
+        w.x = fmaf(-c.x, v.x, w.x);
+        w.x = fmaf(c.y, v.y, w.x);
+        w.y = fmaf(-c.x, v.y, w.y);
+        w.y = fmaf(-c.y, v.x, w.y);
+        w.z = fmaf(-c.x, v.z, w.z);
+        w.z = fmaf(c.y, v.w, w.z);
+        w.w = fmaf(-c.x, v.w, w.w);
+        w.w = fmaf(-c.y, v.z, w.w);
+    }
+    static __device__ __forceinline__ void add_cv(P& a, C c, P v) {
+        a.x = fmaf(c.x, v.x, a.x);
+        a.x = fmaf(-c.y, v.y, a.x);
+        a.y = fmaf(c.x, v.y, a.y);
+        a.y = fmaf(c.y, v.x, a.y);
+        a.z = fmaf(c.x, v.z, a.z);
+        a.z = fmaf(-c.y, v.w, a.z);
+        a.w = fmaf(c.x, v.w, a.w);
+        a.w = fmaf(c.y, v.z, a.w);
+    }
+    static __device__ __forceinline__ P scal(P v, double s) {
+        float f = (float)s;
+        return make_float4(v.x * f, v.y * f, v.z * f, v.w * f);
+    }
+    static __device__ __forceinline__ void add_to(double2* x, int64_t pk, P v) {
+        double2 a = x[2 * pk], b = x[2 * pk + 1];
+        x[2 * pk] = make_double2(a.x + v.x, a.y + v.y);
+        x[2 * pk + 1] = make_double2(b.x + v.z, b.y + v.w);
+    }
+    static __device__ __forceinline__ void add_cv_f64(double2 acc[2], double2 c, P v) {
+        acc[0].x = fma(c.x, (double)v.x, acc[0].x);
+        acc[0].x = fma(-c.y, (double)v.y, acc[0].x);
+        acc[0].y = fma(c.x, (double)v.y, acc[0].y);
+        acc[0].y = fma(c.y, (double)v.x, acc[0].y);
+        acc[1].x = fma(c.x, (double)v.z, acc[1].x);
+        acc[1].x = fma(-c.y, (double)v.w, acc[1].x);
+        acc[1].y = fma(c.x, (double)v.w, acc[1].y);
+        acc[1].y = fma(c.y, (double)v.z, acc[1].y);
+    }
+};
+
+__device__ __forceinline__ double2 warp_sum(double2 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+
+// Store the per-warp values sm[slot][warp] summed over warps into the partials.
+__device__ __forceinline__ void flush_partials(double2 (*sm)[NWARP], int nslot, const Reduce& rd, int col) {
+    __syncthreads();
+    for (int j = threadIdx.x; j < nslot; j += NT) {
+        double2 a = sm[j][0];
+#pragma unroll
+        for (int w = 1; w < NWARP; ++w) a = cadd(a, sm[j][w]);
+        rd.partial[((int64_t)col * rd.stride + j) * rd.nblk + blockIdx.x] = a;
+    }
+}
+
+// ---------------------------------------------------------------- kernels --
+
+// partial[j] = sum_e conj(V_j[e]) w[e], j < J; slot J: ||w||^2 if with_norm.
+template <class T>
+__global__ void __launch_bounds__(NT) k_mdot(Basis<T> V, int J, const T* __restrict__ w, int64_t wsr, int64_t npk,
+                                             Reduce rd, int with_norm, const int* __restrict__ skip) {
+    using O = Ops<T>;
+    const int col = blockIdx.y;
+    if (skip && skip[col]) return;
+    __shared__ double2 sm[MAXSLOT][NWARP];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const T* wc = w + col * wsr;
+    const int64_t base = (int64_t)blockIdx.x * NT * PK + threadIdx.x;
+    typename O::P wv[PK];
+#pragma unroll
+    for (int p = 0; p < PK; ++p) {
+        int64_t i = base + p * NT;
+        wv[p] = i < npk ? O::ld_ro(wc, i) : O::zero();
+    }
+    const T* vb = V.base + col * V.sr;
+    for (int j = 0; j < J; ++j) {
+        const T* vj = vb + j * V.sj;
+        double2 acc;
+        if constexpr (O::CPX == 2) {
+            float ax = 0.f, ay = 0.f;  // FP32 chunk of PK packs
+#pragma unroll
+            for (int p = 0; p < PK; ++p) {
+                int64_t i = base + p * NT;
+                if (i < npk) {
+                    double2 d = O::dot(O::ld_ro(vj, i), wv[p]);
+                    ax += (float)d.x;
+                    ay += (float)d.y;
+                }
+            }
+            acc = make_double2(ax, ay);
+        } else {
+            acc = make_double2(0, 0);
+#pragma unroll
+            for (int p = 0; p < PK; ++p) {
+                int64_t i = base + p * NT;
+                if (i < npk) acc = cadd(acc, O::dot(O::ld_ro(vj, i), wv[p]));
+            }
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) sm[j][warp] = acc;
+    }
+    if (with_norm) {
+        double a = 0;
+#pragma unroll
+        for (int p = 0; p < PK; ++p) a += O::nrm2(wv[p]);
+        double2 acc = warp_sum(make_double2(a, 0));
+        if (lane == 0) sm[J][warp] = acc;
+    }
+    flush_partials(sm, J + (with_norm ? 1 : 0), rd, col);
+}
+
+// w -= sum_j c_j V_j; then partial[j] = V_j^dag w (j < J) and slot J = ||w||^2.
+template <class T>
+__global__ void __launch_bounds__(NT) k_maxpy_mdot(Basis<T> V, int J, const double2* __restrict__ coef, int cstride,
+                                                   T* w, int64_t wsr, int64_t npk, Reduce rd,
+                                                   const int* __restrict__ skip) {
+    using O = Ops<T>;
+    const int col = blockIdx.y;
+    if (skip && skip[col]) return;
+    __shared__ double2 sm[MAXSLOT][NWARP];
+    __shared__ typename O::C cs[MAXSLOT];
+    for (int j = threadIdx.x; j < J; j += NT) cs[j] = O::coef(coef[(int64_t)col * cstride + j]);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T* wc = w + col * wsr;
+    const int64_t base = (int64_t)blockIdx.x * NT * PK + threadIdx.x;
+    typename O::P wv[PK];
+#pragma unroll
+    for (int p = 0; p < PK; ++p) {
+        int64_t i = base + p * NT;
+        wv[p] = i < npk ? O::ld(wc, i) : O::zero();
+    }
+    const T* vb = V.base + col * V.sr;
+    for (int j = 0; j < J; ++j) {
+        const T* vj = vb + j * V.sj;
+        const typename O::C c = cs[j];
+#pragma unroll
+        for (int p = 0; p < PK; ++p) {
+            int64_t i = base + p * NT;
+            if (i < npk) O::sub_cv(wv[p], c, O::ld_ro(vj, i));
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < PK; ++p) {
+        int64_t i = base + p * NT;
+        if (i < npk) O::st(wc, i, wv[p]);
+    }
+    for (int j = 0; j < J; ++j) {
+        const T* vj = vb + j * V.sj;
+        double2 acc;
+        if constexpr (O::CPX == 2) {
+            float ax = 0.f, ay = 0.f;
+#pragma unroll
+            for (int p = 0; p < PK; ++p) {
+                int64_t i = base + p * NT;
+                if (i < npk) {
+                    double2 d = O::dot(O::ld_ro(vj, i), wv[p]);
+                    ax += (float)d.x;
+                    ay += (float)d.y;
+                }
+            }
+            acc = make_double2(ax, ay);
+        } else {
+            acc = make_double2(0, 0);
+#pragma unroll
+            for (int p = 0; p < PK; ++p) {
+                int64_t i = base + p * NT;
+                if (i < npk) acc = cadd(acc, O::dot(O::ld_ro(vj, i), wv[p]));
+            }
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) sm[j][warp] = acc;
+    }
+    {
+        double a = 0;
+#pragma unroll
+        for (int p = 0; p < PK; ++p) a += O::nrm2(wv[p]);
+        double2 acc = warp_sum(make_double2(a, 0));
+        if (lane == 0) sm[J][warp] = acc;
+    }
+    flush_partials(sm, J + 1, rd, col);
+}
+
+// out = (w - sum_j c_j V_j) * scale[col]   (out may alias w)
+template <class T>
+__global__ void __launch_bounds__(NT) k_maxpy_scale(Basis<T> V, int J, const double2* __restrict__ coef, int cstride,
+                                                    const T* w, int64_t wsr, T* out, int64_t osr,
+                                                    const double* __restrict__ scale, int64_t npk,
+                                                    const int* __restrict__ skip) {
+    using O = Ops<T>;
+    const int col = blockIdx.y;
+    if (skip && skip[col]) return;
+    __shared__ typename O::C cs[MAXSLOT];
+    for (int j = threadIdx.x; j < J; j += NT) cs[j] = O::coef(coef[(int64_t)col * cstride + j]);
+    __syncthreads();
+    const T* wc = w + col * wsr;
+    T* oc = out + col * osr;
+    const double sc = scale ? scale[col] : 1.0;
+    const int64_t base = (int64_t)blockIdx.x * NT * PK + threadIdx.x;
+    typename O::P wv[PK];
+#pragma unroll
+    for (int p = 0; p < PK; ++p) {
+        int64_t i = base + p * NT;
+        wv[p] = i < npk ? O::ld(wc, i) : O::zero();
+    }
+    const T* vb = V.base + col * V.sr;
+    for (int j = 0; j < J; ++j) {
+        const T* vj = vb + j * V.sj;
+        const typename O::C c = cs[j];
+#pragma unroll
+        for (int p = 0; p < PK; ++p) {
+            int64_t i = base + p * NT;
+            if (i < npk) O::sub_cv(wv[p], c, O::ld_ro(vj, i));
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < PK; ++p) {
+        int64_t i = base + p * NT;
+        if (i < npk) O::st(oc, i, O::scal(wv[p], sc));
+    }
+}
+
+// x += sum_j c_j V_j in FP64 (x complex128), j < min(J, kk[col]).
+template <class T>
+__global__ void __launch_bounds__(NT) k_update_x(Basis<T> V, int J, const double2* __restrict__ coef, int cstride,
+                                                 double2* __restrict__ x, int64_t xsr, int64_t npk,
+                                                 const int* __restrict__ skip, const int* __restrict__ kk) {
+    using O = Ops<T>;
+    const int col = blockIdx.y;
+    if (skip && skip[col]) return;
+    if (kk && kk[col] < J) J = kk[col];
+    __shared__ double2 cs[MAXSLOT];
+    for (int j = threadIdx.x; j < J; j += NT) cs[j] = coef[(int64_t)col * cstride + j];
+    __syncthreads();
+    double2* xc = x + col * xsr;
+    const T* vb = V.base + col * V.sr;
+    const int64_t base = (int64_t)blockIdx.x * NT * PK + threadIdx.x;
+#pragma unroll
+    for (int p = 0; p < PK; ++p) {
+        int64_t i = base + p * NT;
+        if (i >= npk) break;
+        double2 acc[O::CPX];
+#pragma unroll
+        for (int q = 0; q < O::CPX; ++q) acc[q] = make_double2(0, 0);
+        for (int j = 0; j < J; ++j) O::add_cv_f64(acc, cs[j], O::ld_ro(vb + j * V.sj, i));
+#pragma unroll
+        for (int q = 0; q < O::CPX; ++q) {
+            double2 a = xc[i * O::CPX + q];
+            xc[i * O::CPX + q] = make_double2(a.x + acc[q].x, a.y + acc[q].y);
+        }
+    }
+}
+
+// xs[i] += sum_j y_ij V_j for every shift i, one sweep of V per group of 8 shifts.
+// Products and the sum over j in the storage precision; the add to xs in FP64.
+constexpr int SG = 8;
+template <class T>
+__global__ void __launch_bounds__(NT) k_update_shifts(Basis<T> V, int J, const double2* __restrict__ y, int s,
+                                                      int kmax, double2* __restrict__ xs, int64_t xs_shift,
+                                                      int64_t xs_col, int64_t npk, const int* __restrict__ skip,
+                                                      const int* __restrict__ kk) {
+    using O = Ops<T>;
+    const int col = blockIdx.y;
+    if (skip && skip[col]) return;
+    if (kk && kk[col] < J) J = kk[col];
+    extern __shared__ unsigned char smraw[];
+    typename O::C* ys = reinterpret_cast<typename O::C*>(smraw);  // [s][J]
+    for (int t = threadIdx.x; t < s * J; t += NT) {
+        int i = t / J, j = t % J;
+        ys[t] = O::coef(y[((int64_t)col * s + i) * kmax + j]);
+    }
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (i >= npk) return;
+    const T* vb = V.base + col * V.sr;
+    for (int g0 = 0; g0 < s; g0 += SG) {
+        const int ng = (s - g0) < SG ? (s - g0) : SG;
+        typename O::P acc[SG];
+#pragma unroll
+        for (int g = 0; g < SG; ++g) acc[g] = O::zero();
+        for (int j = 0; j < J; ++j) {
+            typename O::P v = O::ld_ro(vb + j * V.sj, i);
+#pragma unroll
+            for (int g = 0; g < SG; ++g)
+                if (g < ng) O::add_cv(acc[g], ys[(g0 + g) * J + j], v);
+        }
+#pragma unroll
+        for (int g = 0; g < SG; ++g)
+            if (g < ng) O::add_to(xs + (int64_t)(g0 + g) * xs_shift + col * xs_col, i, acc[g]);
+    }
+}
+
+// Second stage of every reduction plus the scalar bookkeeping that consumes it.
+__global__ void __launch_bounds__(NT) k_reduce(Reduce rd, int nslot, int mode, int colidx, DevState S,
+                                               const double2* __restrict__ lambda) {
+    const int col = blockIdx.x;
+    // RM_BETA_FIRST starts a solve; RM_BETA_RESTART must still see columns that
+    // broke down in this cycle; every other mode is column work proper.
+    if (mode == RM_BETA_RESTART && S.done[col]) return;
+    if (mode != RM_BETA_FIRST && mode != RM_BETA_RESTART && S.skip[col]) return;
+    __shared__ double2 sums[MAXSLOT];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = warp; j < nslot; j += NWARP) {
+        const double2* p = rd.partial + ((int64_t)col * rd.stride + j) * rd.nblk;
+        double2 a = make_double2(0, 0);
+        for (int b = lane; b < rd.nblk; b += 32) a = cadd(a, p[b]);
+        a = warp_sum(a);
+        if (lane == 0) sums[j] = a;
+    }
+    __syncthreads();
+    const int64_t cr = (int64_t)col * S.rstride;
+    switch (mode) {
+        case RM_STORE:
+            for (int j = threadIdx.x; j < nslot; j += NT) S.red[cr + j] = sums[j];
+            break;
+        case RM_SIGNED:
+            for (int j = threadIdx.x; j < nslot; j += NT) {
+                double sg = lambda[j].x > 0 ? 1.0 : -1.0;
+                S.red[cr + j] = make_double2(sg * sums[j].x, sg * sums[j].y);
+            }
+            break;
+        case RM_H1:
+            for (int j = threadIdx.x; j < nslot - 1; j += NT) S.h1[cr + j] = sums[j];
+            if (threadIdx.x == 0) S.norm0[col] = sqrt(sums[nslot - 1].x);
+            break;
+        case RM_P2: {
+            const int J = nslot - 1;  // = colidx + 1
+            const int64_t hb = (int64_t)col * (S.kmax + 1) * S.kmax;
+            for (int l = threadIdx.x; l < J; l += NT) {
+                S.red[cr + l] = sums[l];
+                S.H[hb + (int64_t)l * S.kmax + colidx] = cadd(S.h1[cr + l], sums[l]);
+            }
+            if (threadIdx.x == 0) {
+                double h2 = 0;
+                for (int l = 0; l < J; ++l) h2 += cabs2(sums[l]);
+                double hn2 = sums[J].x - h2;
+                double hn = hn2 > 0 ? sqrt(hn2) : 0.0;
+                S.H[hb + (int64_t)(colidx + 1) * S.kmax + colidx] = make_double2(hn, 0);
+                if (!(hn > S.bd_tol * S.norm0[col])) {
+                    S.kk[col] = colidx + 1;
+                    S.skip[col] = 1;
+                    S.scale[col] = 0;
+                    if (!isfinite(hn2)) atomicOr(S.err, 2);
+                } else {
+                    S.scale[col] = 1.0 / hn;
+                }
+            }
+            break;
+        }
+        case RM_BETA_FIRST:
+            if (threadIdx.x == 0) {
+                double beta = sqrt(sums[0].x);
+                S.beta[col] = beta;
+                S.bnorm[col] = beta;
+                S.kk[col] = S.kmax;
+                for (int i = 0; i < S.s; ++i) S.rho[(int64_t)col * S.s + i] = make_double2(1, 0);
+                if (!isfinite(beta)) atomicOr(S.err, 2);
+                if (beta > 0 && isfinite(beta)) {
+                    S.scale[col] = 1.0 / beta;
+                    S.resest[col] = 1.0;
+                    S.skip[col] = 0;
+                    S.done[col] = 0;
+                } else {
+                    S.scale[col] = 0;
+                    S.resest[col] = 0;
+                    S.skip[col] = 1;
+                    S.done[col] = 1;
+                }
+            }
+            break;
+        case RM_BETA_RESTART:
+            if (threadIdx.x == 0) {
+                if (S.kk[col] < S.kmax) {  // invariant subspace met: FOM is exact
+                    S.resest[col] = 0;
+                    S.done[col] = 1;
+                    S.skip[col] = 1;
+                    S.scale[col] = 0;
+                    break;
+                }
+                double beta = sqrt(sums[0].x);
+                double rmax = 0;
+                for (int i = 0; i < S.s; ++i) {
+                    double2 r = S.rho[(int64_t)col * S.s + i];
+                    double a = sqrt(cabs2(r)) * beta / S.bnorm[col];
+                    rmax = a > rmax ? a : rmax;
+                }
+                S.beta[col] = beta;
+                S.resest[col] = rmax;
+                if (!isfinite(rmax)) {
+                    atomicOr(S.err, 2);
+                    S.done[col] = 1;
+                    S.skip[col] = 1;
+                    S.scale[col] = 0;
+                    break;
+                }
+                const int conv = rmax <= S.tol || beta == 0;
+                S.done[col] = conv;
+                S.skip[col] = conv;
+                S.scale[col] = beta > 0 ? 1.0 / beta : 0.0;
+            }
+            break;
+    }
+}
+
+__global__ void k_f64_to_f32(const double2* __restrict__ in, float2* __restrict__ out, int64_t count) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 v = in[i];
+        out[i] = make_float2((float)v.x, (float)v.y);
+    }
+}
+__global__ void k_f32_to_f64(const float2* __restrict__ in, double2* __restrict__ out, int64_t count) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        float2 v = in[i];
+        out[i] = make_double2(v.x, v.y);
+    }
+}
+__global__ void k_f64_to_bf16(const double2* __restrict__ in, __nv_bfloat162* __restrict__ out, int64_t count) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 v = in[i];
+        out[i] = __floats2bfloat162_rn((float)v.x, (float)v.y);
+    }
+}
+
+inline unsigned grid_for(int64_t count) {
+    int64_t g = (count + 255) / 256;
+    if (g > 152 * 16) g = 152 * 16;
+    if (g < 1) g = 1;
+    return (unsigned)g;
+}
+
+}  // namespace
+
+template <class T>
+int reduce_blocks(int64_t n) {
+    int64_t npk = n / Ops<T>::CPX;
+    int64_t b = (npk + (int64_t)NT * PK - 1) / ((int64_t)NT * PK);
+    return (int)(b < 1 ? 1 : b);
+}
+
+template <class T>
+cudaError_t mdot(Basis<T> V, int J, const T* w, int64_t wsr, int64_t n, int ncol, const Reduce& rd, int with_norm,
+                 const int* skip, cudaStream_t st) {
+    if (J + 1 > MAXSLOT) return cudaErrorInvalidValue;
+    int64_t npk = n / Ops<T>::CPX;
+    dim3 grid(rd.nblk, ncol);
+    k_mdot<T><<<grid, NT, 0, st>>>(V, J, w, wsr, npk, rd, with_norm, skip);
+    return cudaGetLastError();
+}
+
+cudaError_t reduce(const Reduce& rd, int nslot, int ncol, int mode, int colidx, const DevState& S,
+                   const double2* lambda, cudaStream_t st) {
+    if (nslot > MAXSLOT) return cudaErrorInvalidValue;
+    k_reduce<<<ncol, NT, 0, st>>>(rd, nslot, mode, colidx, S, lambda);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t maxpy_mdot(Basis<T> V, int J, const double2* coef, int cstride, T* w, int64_t wsr, int64_t n, int ncol,
+                       const Reduce& rd, const int* skip, cudaStream_t st) {
+    if (J + 1 > MAXSLOT) return cudaErrorInvalidValue;
+    int64_t npk = n / Ops<T>::CPX;
+    dim3 grid(rd.nblk, ncol);
+    k_maxpy_mdot<T><<<grid, NT, 0, st>>>(V, J, coef, cstride, w, wsr, npk, rd, skip);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t maxpy_scale(Basis<T> V, int J, const double2* coef, int cstride, const T* w, int64_t wsr, T* out,
+                        int64_t osr, const double* scale, int64_t n, int ncol, const int* skip, cudaStream_t st) {
+    if (J > MAXSLOT) return cudaErrorInvalidValue;
+    int64_t npk = n / Ops<T>::CPX;
+    dim3 grid(reduce_blocks<T>(n), ncol);
+    k_maxpy_scale<T><<<grid, NT, 0, st>>>(V, J, coef, cstride, w, wsr, out, osr, scale, npk, skip);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t update_x(Basis<T> V, int J, const double2* coef, int cstride, double2* x, int64_t xsr, int64_t n,
+                     int ncol, const int* skip, const int* kk, cudaStream_t st) {
+    if (J > MAXSLOT) return cudaErrorInvalidValue;
+    int64_t npk = n / Ops<T>::CPX;
+    dim3 grid(reduce_blocks<T>(n), ncol);
+    k_update_x<T><<<grid, NT, 0, st>>>(V, J, coef, cstride, x, xsr, npk, skip, kk);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t update_shifts(Basis<T> V, int J, const double2* y, int s, int kmax, double2* xs, int64_t xs_shift,
+                          int64_t xs_col, int64_t n, int ncol, const int* skip, const int* kk, cudaStream_t st) {
+    int64_t npk = n / Ops<T>::CPX;
+    size_t smem = sizeof(typename Ops<T>::C) * (size_t)s * (size_t)J;
+    if (smem > 48 * 1024) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)((npk + NT - 1) / NT), ncol);
+    k_update_shifts<T><<<grid, NT, smem, st>>>(V, J, y, s, kmax, xs, xs_shift, xs_col, npk, skip, kk);
+    return cudaGetLastError();
+}
+
+cudaError_t convert_f64_to_f32(const double2* in, float2* out, int64_t count, cudaStream_t st) {
+    k_f64_to_f32<<<grid_for(count), 256, 0, st>>>(in, out, count);
+    return cudaGetLastError();
+}
+cudaError_t convert_f32_to_f64(const float2* in, double2* out, int64_t count, cudaStream_t st) {
+    k_f32_to_f64<<<grid_for(count), 256, 0, st>>>(in, out, count);
+    return cudaGetLastError();
+}
+cudaError_t links_f64_to_bf16(const double2* in, __nv_bfloat162* out, int64_t count, cudaStream_t st) {
+    k_f64_to_bf16<<<grid_for(count), 256, 0, st>>>(in, out, count);
+    return cudaGetLastError();
+}
+
+#define SGN_INST(T)                                                                                              \
+    template int reduce_blocks<T>(int64_t);                                                                      \
+    template cudaError_t mdot<T>(Basis<T>, int, const T*, int64_t, int64_t, int, const Reduce&, int, const int*, \
+                                 cudaStream_t);                                                                  \
+    template cudaError_t maxpy_mdot<T>(Basis<T>, int, const double2*, int, T*, int64_t, int64_t, int,           \
+                                       const Reduce&, const int*, cudaStream_t);                                 \
+    template cudaError_t maxpy_scale<T>(Basis<T>, int, const double2*, int, const T*, int64_t, T*, int64_t,     \
+                                        const double*, int64_t, int, const int*, cudaStream_t);                  \
+    template cudaError_t update_x<T>(Basis<T>, int, const double2*, int, double2*, int64_t, int64_t, int,       \
+                                     const int*, const int*, cudaStream_t);                                      \
+    template cudaError_t update_shifts<T>(Basis<T>, int, const double2*, int, int, double2*, int64_t, int64_t,  \
+                                          int64_t, int, const int*, const int*, cudaStream_t);
+SGN_INST(double2)
+SGN_INST(float2)
+
+}  // namespace sgn

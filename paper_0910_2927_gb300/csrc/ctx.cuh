@@ -1,0 +1,112 @@
+// The context behind the opaque sgn_ctx handle and its device arena.
+#pragma once
+
+#include "blas.cuh"
+
+#include <cmath>
+#include <complex>
+#include <map>
+#include <memory>
+
+struct sgn_ctx;
+
+namespace sgn {
+
+// A device allocation obtained through the caller's allocator (or cudaMalloc).
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+int dev_alloc(sgn_ctx* c, DevBuf& b, size_t bytes);
+void dev_free(sgn_ctx* c, DevBuf& b);
+
+template <class T>
+inline T* as(DevBuf& b) {
+    return reinterpret_cast<T*>(b.p);
+}
+
+// Workspace of one FOM-LR engine configuration (columns, restart length,
+// number of shifts, storage precision).  Carved out of one allocation.
+struct Engine {
+    int ncol = 0, k = 0, s = 0, prec = -1, m = 0;
+    int64_t n = 0;
+    int nblk = 0, rstride = 0;
+    DevBuf arena;
+    void* V = nullptr;  // (k+1) * ncol * n elements of the storage type
+    void* w = nullptr;  // ncol * n
+    void* t = nullptr;  // ncol * n
+    double2* partial = nullptr;
+    DevState S{};
+    double* sigma_dev = nullptr;  // [ncol][s]
+    double* omega_dev = nullptr;
+    // host mirrors of the per-column flags (pinned)
+    int* h_done = nullptr;
+    double* h_resest = nullptr;
+    int* h_err = nullptr;
+    int* h_kk = nullptr;
+    // captured restart cycle
+    cudaGraphExec_t graph = nullptr;
+    uint64_t graph_key = 0;
+};
+
+}  // namespace sgn
+
+struct sgn_ctx {
+    int dims[4] = {0, 0, 0, 0};
+    int64_t vol = 0, n = 0;
+    int ap[4] = {0, 0, 0, 1};
+    double mu = 0.0, mass = -1.6;
+    cudaStream_t user_stream = nullptr;
+    cudaStream_t work = nullptr;  // internal stream (capturable); ordered against user_stream by events
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+    sgn_alloc_fn alloc = nullptr;
+    sgn_free_fn free_ = nullptr;
+    void* user = nullptr;
+    int device = 0;
+
+    // gauge field: FP64 master copy, FP32 and BF16 copies for the FP32 stencil
+    sgn::DevBuf U64, U32, U16;
+    bool have_gauge = false;
+
+    // rational function
+    std::vector<double> sigma, omega;
+    // restart parameters
+    int k = 40;
+    double tol = 1e-10;
+    int max_cycles = 1000;
+    int project = 1;
+    // precision
+    int precision = SGN_PREC_FP64;
+    double target = 1e-8;
+    int link_storage = SGN_LINKS_FP32;
+
+    // deflation (R, L as n x m column blocks)
+    int m = 0;
+    sgn::DevBuf R64, L64, R32, L32, lam_dev, lamc_dev;
+    std::vector<std::complex<double>> lam;
+
+    // engines keyed by configuration
+    std::map<uint64_t, std::unique_ptr<sgn::Engine>> engines;
+    // scratch fields for apply (b copy, x accumulators, FP64 temporaries)
+    sgn::DevBuf io;
+    sgn::DevBuf stage;  // device staging of host b / x
+    size_t io_bytes = 0;
+    double2* h_pinned = nullptr;
+    size_t h_pinned_bytes = 0;
+};
+
+namespace sgn {
+
+StencilParams stencil_params(const sgn_ctx* c, bool adjoint);
+// H_W applied in FP64 / FP32 to ncol fields (skip may be null).
+cudaError_t apply_hw64(const sgn_ctx* c, double2* out, const double2* in, int ncol, bool adjoint, const int* skip,
+                       cudaStream_t st);
+cudaError_t apply_hw32(const sgn_ctx* c, float2* out, const float2* in, int ncol, bool adjoint, const int* skip,
+                       cudaStream_t st);
+
+int solve(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int ncol, bool adjoint, sgn_report* rep);
+int build_deflation(sgn_ctx* c, int m, int extra, double eig_tol, double* lambda_out);
+void release_engines(sgn_ctx* c);
+
+}  // namespace sgn

@@ -1,0 +1,151 @@
+// The small dense steps of Algorithm 1, kept on the device:
+//   y_i = beta rho_i (H_k - sigma_i I)^{-1} e_1          (one warp per column and shift)
+//   rho_i <- -h_{k+1,k} e_k^T y_i                        (collinearity factor, eq. (3.1))
+//   c = sum_i omega_i y_i                                (the combination of eq. (2.3))
+// The shifted Hessenberg systems are solved by Gaussian elimination with
+// partial pivoting: on a Hessenberg matrix the pivot of column r is chosen
+// between the running row r and the untouched row r+1 (larger modulus, the
+// running row on ties), and each lane of the warp owns two matrix columns.
+#include "blas.cuh"
+
+namespace sgn {
+namespace {
+
+constexpr int KMAX = 64;
+
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+    double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__device__ __forceinline__ double2 shfl(double2 v, int src) {
+    return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+__global__ void __launch_bounds__(32) k_shifted_solve(DevState S) {
+    const int i = blockIdx.x;    // shift
+    const int col = blockIdx.y;  // column
+    if (S.done[col]) return;
+    const int lane = threadIdx.x;
+    const int km = S.kmax;
+    const int kk = S.kk[col];
+    const double2* H = S.H + (int64_t)col * (km + 1) * km;
+    const double sigma = S.sigma[(int64_t)col * S.s + i];
+    extern __shared__ double2 U[];  // [kk][km] upper factor, row-major
+    __shared__ double2 zU[KMAX];
+    const int c0 = lane, c1 = lane + 32;
+    auto Hm = [&](int r, int c) -> double2 {  // (H - sigma I)[r][c]
+        double2 h = H[(int64_t)r * km + c];
+        if (r == c) h.x -= sigma;
+        return h;
+    };
+    double2 w0 = c0 < kk ? Hm(0, c0) : make_double2(0, 0);
+    double2 w1 = c1 < kk ? Hm(0, c1) : make_double2(0, 0);
+    const double beta = S.beta[col];
+    const double2 rho = S.rho[(int64_t)col * S.s + i];
+    double2 zw = make_double2(beta * rho.x, beta * rho.y);
+    bool singular = false;
+    for (int r = 0; r < kk; ++r) {
+        const int owner = r & 31;
+        const bool hi = r >= 32;
+        double2 a = shfl(hi ? w1 : w0, owner);
+        if (r == kk - 1) {
+            if (c0 >= r && c0 < kk) U[r * km + c0] = w0;
+            if (c1 >= r && c1 < kk) U[r * km + c1] = w1;
+            if (lane == 0) zU[r] = zw;
+            if (a.x == 0 && a.y == 0) singular = true;
+            break;
+        }
+        double2 n0 = (c0 >= r && c0 < kk) ? Hm(r + 1, c0) : make_double2(0, 0);
+        double2 n1 = (c1 >= r && c1 < kk) ? Hm(r + 1, c1) : make_double2(0, 0);
+        double2 b = Hm(r + 1, r);
+        double2 p0, p1, o0, o1, zp, zo;
+        if (cabs2(b) > cabs2(a)) {  // swap: row r+1 becomes the pivot row
+            p0 = n0; p1 = n1; zp = make_double2(0, 0);
+            o0 = w0; o1 = w1; zo = zw;
+        } else {
+            p0 = w0; p1 = w1; zp = zw;
+            o0 = n0; o1 = n1; zo = make_double2(0, 0);
+        }
+        double2 piv = cabs2(b) > cabs2(a) ? b : a;
+        double2 oth = cabs2(b) > cabs2(a) ? a : b;
+        if (piv.x == 0 && piv.y == 0) {
+            singular = true;
+            break;
+        }
+        double2 l = cdiv(oth, piv);
+        if (c0 >= r && c0 < kk) U[r * km + c0] = p0;
+        if (c1 >= r && c1 < kk) U[r * km + c1] = p1;
+        if (lane == 0) zU[r] = zp;
+        w0 = c0 > r ? csub(o0, cmul(l, p0)) : make_double2(0, 0);
+        w1 = c1 > r ? csub(o1, cmul(l, p1)) : make_double2(0, 0);
+        zw = csub(zo, cmul(l, zp));
+    }
+    double2* y = S.y + ((int64_t)col * S.s + i) * km;
+    if (singular) {
+        if (lane == 0) atomicOr(S.err, 1);
+        for (int j = lane; j < km; j += 32) y[j] = make_double2(0, 0);
+        return;
+    }
+    __syncwarp();
+    // column-oriented back substitution; lane owns rows lane and lane + 32
+    double2 z0 = c0 < kk ? zU[c0] : make_double2(0, 0);
+    double2 z1 = c1 < kk ? zU[c1] : make_double2(0, 0);
+    double2 ylast = make_double2(0, 0);
+    for (int r = kk - 1; r >= 0; --r) {
+        const int owner = r & 31;
+        double2 zr = shfl(r >= 32 ? z1 : z0, owner);
+        double2 yr = cdiv(zr, U[r * km + r]);
+        if (r == kk - 1) ylast = yr;
+        if (lane == owner) y[r] = yr;
+        if (c0 < r) z0 = csub(z0, cmul(U[c0 * km + r], yr));
+        if (c1 < r) z1 = csub(z1, cmul(U[c1 * km + r], yr));
+    }
+    for (int j = kk + lane; j < km; j += 32) y[j] = make_double2(0, 0);
+    if (lane == 0) {
+        double2 rnew = make_double2(0, 0);
+        if (kk == km) {
+            double2 h = H[(int64_t)kk * km + (kk - 1)];
+            rnew = cmul(h, ylast);
+            rnew.x = -rnew.x;
+            rnew.y = -rnew.y;
+        }
+        S.rho[(int64_t)col * S.s + i] = rnew;
+    }
+}
+
+__global__ void k_combine(DevState S) {
+    const int col = blockIdx.x;
+    if (S.done[col]) return;
+    const int km = S.kmax;
+    for (int j = threadIdx.x; j < km; j += blockDim.x) {
+        double2 c = make_double2(0, 0);
+        for (int i = 0; i < S.s; ++i) {
+            double2 y = S.y[((int64_t)col * S.s + i) * km + j];
+            double w = S.omega[(int64_t)col * S.s + i];
+            c.x = fma(w, y.x, c.x);
+            c.y = fma(w, y.y, c.y);
+        }
+        S.coef[(int64_t)col * S.rstride + j] = c;
+    }
+}
+
+}  // namespace
+
+cudaError_t prepare_small_kernels() {
+    return cudaFuncSetAttribute(k_shifted_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(double2) * KMAX * KMAX));
+}
+
+cudaError_t shifted_solves(const DevState& S, int ncol, cudaStream_t st) {
+    if (S.kmax > KMAX) return cudaErrorInvalidValue;
+    size_t smem = sizeof(double2) * (size_t)S.kmax * S.kmax;
+    k_shifted_solve<<<dim3(S.s, ncol), 32, smem, st>>>(S);
+    return cudaGetLastError();
+}
+
+cudaError_t combine_shifts(const DevState& S, int ncol, cudaStream_t st) {
+    k_combine<<<ncol, 64, 0, st>>>(S);
+    return cudaGetLastError();
+}
+
+}  // namespace sgn

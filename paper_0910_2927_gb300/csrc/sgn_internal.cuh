@@ -1,0 +1,80 @@
+// Internal declarations shared by the CUDA translation units of libsgn.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sgn.h"
+
+namespace sgn {
+
+// ----------------------------------------------------------------- errors --
+void set_error(const std::string& msg);
+#define SGN_CUDA(call)                                                                 \
+    do {                                                                               \
+        cudaError_t _e = (call);                                                       \
+        if (_e != cudaSuccess) {                                                       \
+            ::sgn::set_error(std::string(#call) + ": " + cudaGetErrorString(_e));      \
+            return SGN_ERR_CUDA;                                                       \
+        }                                                                              \
+    } while (0)
+#define SGN_CHECK(call)            \
+    do {                           \
+        int _s = (call);           \
+        if (_s != SGN_OK) return _s; \
+    } while (0)
+
+// ---------------------------------------------------------------- complex --
+__host__ __device__ inline double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline double2 cconjmul(double2 a, double2 b) {  // conj(a) * b
+    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ inline double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+
+// Lattice geometry and operator parameters passed by value to the stencil.
+struct StencilParams {
+    int L[4];          // Lx, Ly, Lz, Lt
+    int64_t vol;       // sites
+    int64_t stride_rhs;  // complex elements between consecutive fields (= 12 vol)
+    double diag;       // 4 + m_W
+    double cf[4];      // forward hop coefficient -1/2 e^{+mu d_nu,t}
+    double cb[4];      // backward hop coefficient -1/2 e^{-mu d_nu,t}
+    int ap[4];         // antiperiodic flags
+};
+
+// ---------------------------------------------------------- kernel entry --
+// Stencil: out = H_W in for nrhs fields.  Real = double or float; links in
+// double, float or bf16 (Link).  skip: per-field flags (non-zero: skip), may be null.
+cudaError_t launch_hw_f64(double2* out, const double2* in, const double2* U, int nrhs,
+                          const StencilParams& p, const int* skip, cudaStream_t st);
+cudaError_t launch_hw_f32(float2* out, const float2* in, const float2* U, int nrhs,
+                          const StencilParams& p, const int* skip, cudaStream_t st);
+cudaError_t launch_hw_f32_bf16links(float2* out, const float2* in, const __nv_bfloat162* U, int nrhs,
+                                    const StencilParams& p, const int* skip, cudaStream_t st);
+
+// ------------------------------------------------------------ vector ops --
+// A "basis" is J fields per column: element e of vector j of column r lives at
+// base[j * sj + r * sr + e] (sr = 0 for a basis shared by every column).
+template <class T>
+struct Basis {
+    const T* base;
+    int64_t sj;
+    int64_t sr;
+};
+
+// Block layout of the two-stage reductions: partials[(r * stride + j) * nblk + b].
+struct Reduce {
+    double2* partial;  // scratch
+    int nblk;          // blocks per column
+    int stride;        // slots per column (>= J + 1)
+};
+
+}  // namespace sgn

@@ -1,0 +1,502 @@
+// Restarted LR-deflated multishift FOM, Algorithm 1 ("FOM-LR(m,k)"), on the
+// GPU.  The s shifted systems of eq. (2.2) are read with t^2 as in eq. (6.2):
+// (A^2 - sigma_i) x_i = b~ with b~ = A (I - P) b, so one Arnoldi process on
+// A^2 serves all shifts (shift invariance, Sec. 2) and every restart keeps the
+// residuals collinear (eq. (3.1)).
+//
+// Host orchestration.  Every scalar of the method (Hessenberg entries, norms,
+// collinearity factors, convergence flags) lives on the device, so a restart
+// cycle -- k Arnoldi steps, the shifted solves, the update, the projection
+// step and the restart -- is a fixed launch sequence.  It is captured once as
+// a CUDA graph and replayed; the host reads back only the per-column
+// convergence flags between cycles.  Columns (right-hand sides) run in
+// lockstep with separate Krylov spaces; a converged column skips its work.
+#include "ctx.cuh"
+
+#include <algorithm>
+#include <cstring>
+
+namespace sgn {
+
+int dev_alloc(sgn_ctx* c, DevBuf& b, size_t bytes) {
+    if (b.p && b.bytes >= bytes) return SGN_OK;
+    dev_free(c, b);
+    if (bytes == 0) return SGN_OK;
+    bytes = (bytes + 255) & ~size_t(255);
+    void* p = nullptr;
+    if (c->alloc) {
+        p = c->alloc(bytes, c->user);
+        if (!p) {
+            set_error("device allocation of " + std::to_string(bytes) + " bytes failed (caller allocator)");
+            return SGN_ERR_ALLOC;
+        }
+    } else {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            set_error("cudaMalloc(" + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+            return SGN_ERR_ALLOC;
+        }
+    }
+    b.p = p;
+    b.bytes = bytes;
+    return SGN_OK;
+}
+
+void dev_free(sgn_ctx* c, DevBuf& b) {
+    if (!b.p) return;
+    if (c->free_)
+        c->free_(b.p, b.bytes, c->user);
+    else
+        cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+StencilParams stencil_params(const sgn_ctx* c, bool adjoint) {
+    StencilParams p{};
+    for (int d = 0; d < 4; ++d) {
+        p.L[d] = c->dims[d];
+        p.ap[d] = c->ap[d];
+        p.cf[d] = -0.5;
+        p.cb[d] = -0.5;
+    }
+    const double mu = adjoint ? -c->mu : c->mu;
+    p.cf[3] = -0.5 * std::exp(mu);
+    p.cb[3] = -0.5 * std::exp(-mu);
+    p.vol = c->vol;
+    p.stride_rhs = c->n;
+    p.diag = 4.0 + c->mass;
+    return p;
+}
+
+cudaError_t apply_hw64(const sgn_ctx* c, double2* out, const double2* in, int ncol, bool adjoint, const int* skip,
+                       cudaStream_t st) {
+    return launch_hw_f64(out, in, reinterpret_cast<const double2*>(c->U64.p), ncol, stencil_params(c, adjoint), skip,
+                         st);
+}
+
+cudaError_t apply_hw32(const sgn_ctx* c, float2* out, const float2* in, int ncol, bool adjoint, const int* skip,
+                       cudaStream_t st) {
+    StencilParams p = stencil_params(c, adjoint);
+    if (c->link_storage == SGN_LINKS_BF16)
+        return launch_hw_f32_bf16links(out, in, reinterpret_cast<const __nv_bfloat162*>(c->U16.p), ncol, p, skip, st);
+    return launch_hw_f32(out, in, reinterpret_cast<const float2*>(c->U32.p), ncol, p, skip, st);
+}
+
+namespace {
+
+template <class T>
+cudaError_t apply_hw(const sgn_ctx* c, T* out, const T* in, int ncol, bool adjoint, const int* skip,
+                     cudaStream_t st);
+template <>
+cudaError_t apply_hw<double2>(const sgn_ctx* c, double2* out, const double2* in, int ncol, bool adjoint,
+                              const int* skip, cudaStream_t st) {
+    return apply_hw64(c, out, in, ncol, adjoint, skip, st);
+}
+template <>
+cudaError_t apply_hw<float2>(const sgn_ctx* c, float2* out, const float2* in, int ncol, bool adjoint, const int* skip,
+                             cudaStream_t st) {
+    return apply_hw32(c, out, in, ncol, adjoint, skip, st);
+}
+
+#define CU(x)                                     \
+    do {                                          \
+        cudaError_t _e = (x);                     \
+        if (_e != cudaSuccess) return _e;         \
+    } while (0)
+
+inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+uint64_t mix(uint64_t h, uint64_t v) {
+    h ^= v + 0x9e3779b97f4a7c15ULL + (h << 6) + (h >> 2);
+    return h;
+}
+
+// Everything a captured cycle depends on besides the engine's own buffers.
+struct CycleArgs {
+    bool adjoint = false;
+    const void* L = nullptr;  // deflation blocks in the storage precision (n x m)
+    const void* R = nullptr;
+    int m = 0;
+    int project = 1;
+    double2* xacc = nullptr;  // FP64 accumulator of x (combined), may be null
+    int64_t xsr = 0;
+    double2* xs = nullptr;    // FP64 per-shift iterates, may be null
+    int64_t xs_shift = 0, xs_col = 0;
+};
+
+uint64_t cycle_key(const sgn_ctx* c, const Engine& E, const CycleArgs& a) {
+    uint64_t h = 1469598103934665603ULL;
+    auto mixd = [&](double d) {
+        uint64_t u;
+        std::memcpy(&u, &d, 8);
+        h = mix(h, u);
+    };
+    h = mix(h, a.adjoint);
+    h = mix(h, (uint64_t)(uintptr_t)a.L);
+    h = mix(h, (uint64_t)(uintptr_t)a.R);
+    h = mix(h, a.m);
+    h = mix(h, a.project);
+    h = mix(h, (uint64_t)(uintptr_t)a.xacc);
+    h = mix(h, a.xsr);
+    h = mix(h, (uint64_t)(uintptr_t)a.xs);
+    h = mix(h, a.xs_shift);
+    h = mix(h, a.xs_col);
+    h = mix(h, (uint64_t)(uintptr_t)c->U64.p);
+    h = mix(h, (uint64_t)(uintptr_t)c->U32.p);
+    h = mix(h, (uint64_t)(uintptr_t)c->U16.p);
+    h = mix(h, c->link_storage);
+    mixd(c->mu);
+    mixd(c->mass);
+    for (int d = 0; d < 4; ++d) h = mix(h, c->ap[d]);
+    mixd(E.S.tol);
+    return h;
+}
+
+// One restart cycle of Algorithm 1 for all columns.
+template <class T>
+cudaError_t cycle(const sgn_ctx* c, Engine& E, const CycleArgs& a, cudaStream_t st) {
+    const int64_t n = E.n;
+    const int ncol = E.ncol, k = E.k;
+    T* V = reinterpret_cast<T*>(E.V);
+    T* w = reinterpret_cast<T*>(E.w);
+    T* t = reinterpret_cast<T*>(E.t);
+    const int64_t sj = (int64_t)ncol * n, sr = n;
+    const Reduce rd{E.partial, E.nblk, E.rstride};
+    const DevState& S = E.S;
+    const Basis<T> VB{V, sj, sr};
+    for (int j = 0; j < k; ++j) {
+        // w = A^2 v_j
+        CU(apply_hw<T>(c, t, V + j * sj, ncol, a.adjoint, S.skip, st));
+        CU(apply_hw<T>(c, w, t, ncol, a.adjoint, S.skip, st));
+        // CGS2: h1 = V^dag w; w -= V h1, h2 = V^dag w; v_{j+1} = (w - V h2) / h_{j+1,j}
+        CU(mdot<T>(VB, j + 1, w, sr, n, ncol, rd, 1, S.skip, st));
+        CU(reduce(rd, j + 2, ncol, RM_H1, j, S, nullptr, st));
+        CU(maxpy_mdot<T>(VB, j + 1, S.h1, S.rstride, w, sr, n, ncol, rd, S.skip, st));
+        CU(reduce(rd, j + 2, ncol, RM_P2, j, S, nullptr, st));
+        CU(maxpy_scale<T>(VB, j + 1, S.red, S.rstride, w, sr, V + (j + 1) * sj, sr, S.scale, n, ncol, S.skip, st));
+    }
+    // y_i = beta rho_i (H_k - sigma_i)^{-1} e_1, rho_i update, c = sum omega_i y_i
+    CU(shifted_solves(S, ncol, st));
+    CU(combine_shifts(S, ncol, st));
+    // x += V_k c  (and x_i += V_k y_i)
+    if (a.xacc) CU(update_x<T>(VB, k, S.coef, S.rstride, a.xacc, a.xsr, n, ncol, S.done, S.kk, st));
+    if (a.xs) CU(update_shifts<T>(VB, k, S.y, E.s, k, a.xs, a.xs_shift, a.xs_col, n, ncol, S.done, S.kk, st));
+    // r = v_{k+1}; projection step r = (I - P) r
+    T* Vk = V + k * sj;
+    if (a.project && a.m > 0) {
+        const Basis<T> LB{reinterpret_cast<const T*>(a.L), n, 0};
+        const Basis<T> RB{reinterpret_cast<const T*>(a.R), n, 0};
+        CU(mdot<T>(LB, a.m, Vk, sr, n, ncol, rd, 0, S.skip, st));
+        CU(reduce(rd, a.m, ncol, RM_STORE, 0, S, nullptr, st));
+        CU(maxpy_scale<T>(RB, a.m, S.red, S.rstride, Vk, sr, Vk, sr, nullptr, n, ncol, S.skip, st));
+    }
+    // beta = ||r||, convergence test, v_1 = r / beta
+    CU(mdot<T>(VB, 0, Vk, sr, n, ncol, rd, 1, S.skip, st));
+    CU(reduce(rd, 1, ncol, RM_BETA_RESTART, 0, S, nullptr, st));
+    CU(maxpy_scale<T>(VB, 0, S.red, S.rstride, Vk, sr, V, sr, S.scale, n, ncol, S.skip, st));
+    return cudaSuccess;
+}
+
+int get_engine(sgn_ctx* c, int ncol, int k, int s, int prec, Engine** out) {
+    const uint64_t key = mix(mix(mix(mix((uint64_t)ncol, (uint64_t)k), (uint64_t)s), (uint64_t)prec),
+                             (uint64_t)c->m);
+    auto it = c->engines.find(key);
+    if (it != c->engines.end()) {
+        *out = it->second.get();
+        return SGN_OK;
+    }
+    auto E = std::make_unique<Engine>();
+    E->ncol = ncol;
+    E->k = k;
+    E->s = s;
+    E->prec = prec;
+    E->m = c->m;
+    E->n = c->n;
+    const size_t esz = prec == SGN_PREC_FP64 ? sizeof(double2) : sizeof(float2);
+    E->nblk = prec == SGN_PREC_FP64 ? reduce_blocks<double2>(c->n) : reduce_blocks<float2>(c->n);
+    int rs = std::max(k + 2, c->m + 1);
+    E->rstride = (rs + 7) & ~7;
+    const size_t nc = (size_t)ncol;
+    const size_t field = (size_t)c->n * esz;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += align256(bytes);
+        return o;
+    };
+    size_t oV = take((size_t)(k + 1) * nc * field);
+    size_t ow = take(nc * field);
+    size_t ot = take(nc * field);
+    size_t op = take(nc * E->rstride * (size_t)E->nblk * sizeof(double2));
+    size_t oH = take(nc * (size_t)(k + 1) * k * sizeof(double2));
+    size_t ored = take(nc * E->rstride * sizeof(double2));
+    size_t oh1 = take(nc * E->rstride * sizeof(double2));
+    size_t ocoef = take(nc * E->rstride * sizeof(double2));
+    size_t oy = take(nc * (size_t)s * k * sizeof(double2));
+    size_t orho = take(nc * (size_t)s * sizeof(double2));
+    size_t od[5];
+    for (int i = 0; i < 5; ++i) od[i] = take(nc * sizeof(double));
+    size_t osig = take(nc * (size_t)s * sizeof(double));
+    size_t oom = take(nc * (size_t)s * sizeof(double));
+    size_t oi[3];
+    for (int i = 0; i < 3; ++i) oi[i] = take(nc * sizeof(int));
+    size_t oerr = take(sizeof(int));
+    SGN_CHECK(dev_alloc(c, E->arena, off));
+    char* base = reinterpret_cast<char*>(E->arena.p);
+    E->V = base + oV;
+    E->w = base + ow;
+    E->t = base + ot;
+    E->partial = reinterpret_cast<double2*>(base + op);
+    DevState& S = E->S;
+    S.H = reinterpret_cast<double2*>(base + oH);
+    S.red = reinterpret_cast<double2*>(base + ored);
+    S.h1 = reinterpret_cast<double2*>(base + oh1);
+    S.coef = reinterpret_cast<double2*>(base + ocoef);
+    S.y = reinterpret_cast<double2*>(base + oy);
+    S.rho = reinterpret_cast<double2*>(base + orho);
+    S.norm0 = reinterpret_cast<double*>(base + od[0]);
+    S.scale = reinterpret_cast<double*>(base + od[1]);
+    S.beta = reinterpret_cast<double*>(base + od[2]);
+    S.bnorm = reinterpret_cast<double*>(base + od[3]);
+    S.resest = reinterpret_cast<double*>(base + od[4]);
+    E->sigma_dev = reinterpret_cast<double*>(base + osig);
+    E->omega_dev = reinterpret_cast<double*>(base + oom);
+    S.sigma = E->sigma_dev;
+    S.omega = E->omega_dev;
+    S.kk = reinterpret_cast<int*>(base + oi[0]);
+    S.done = reinterpret_cast<int*>(base + oi[1]);
+    S.skip = reinterpret_cast<int*>(base + oi[2]);
+    S.err = reinterpret_cast<int*>(base + oerr);
+    S.kmax = k;
+    S.s = s;
+    S.rstride = E->rstride;
+    S.bd_tol = prec == SGN_PREC_FP64 ? 1e-14 : 1e-6;
+    // zero the whole arena once so no kernel ever reads uninitialised memory
+    SGN_CUDA(cudaMemsetAsync(E->arena.p, 0, off, c->work));
+    SGN_CUDA(cudaHostAlloc(&E->h_done, nc * sizeof(int), cudaHostAllocDefault));
+    SGN_CUDA(cudaHostAlloc(&E->h_resest, nc * sizeof(double), cudaHostAllocDefault));
+    SGN_CUDA(cudaHostAlloc(&E->h_err, sizeof(int), cudaHostAllocDefault));
+    SGN_CUDA(cudaHostAlloc(&E->h_kk, nc * sizeof(int), cudaHostAllocDefault));
+    *out = E.get();
+    c->engines[key] = std::move(E);
+    return SGN_OK;
+}
+
+}  // namespace
+
+void release_engines(sgn_ctx* c) {
+    for (auto& kv : c->engines) {
+        Engine& E = *kv.second;
+        if (E.graph) cudaGraphExecDestroy(E.graph);
+        dev_free(c, E.arena);
+        if (E.h_done) cudaFreeHost(E.h_done);
+        if (E.h_resest) cudaFreeHost(E.h_resest);
+        if (E.h_err) cudaFreeHost(E.h_err);
+        if (E.h_kk) cudaFreeHost(E.h_kk);
+    }
+    c->engines.clear();
+}
+
+namespace {
+
+struct RunResult {
+    int cycles = 0;
+    int converged = 0;
+    int breakdown = 0;
+    int err = 0;
+    double resmax = 0;
+};
+
+// Run restart cycles until every column has converged.  On entry V[0] holds
+// the (unnormalised) first restart vector of every column and the shift
+// tables of the engine are filled.
+template <class T>
+int run_engine(sgn_ctx* c, Engine& E, const CycleArgs& a, double tol, int max_cycles, RunResult* res) {
+    cudaStream_t st = c->work;
+    const int ncol = E.ncol;
+    const int64_t n = E.n;
+    E.S.tol = tol;
+    SGN_CUDA(cudaMemsetAsync(E.S.done, 0, ncol * sizeof(int), st));
+    SGN_CUDA(cudaMemsetAsync(E.S.skip, 0, ncol * sizeof(int), st));
+    SGN_CUDA(cudaMemsetAsync(E.S.err, 0, sizeof(int), st));
+    T* V = reinterpret_cast<T*>(E.V);
+    const Reduce rd{E.partial, E.nblk, E.rstride};
+    const Basis<T> VB{V, (int64_t)ncol * n, n};
+    // beta = ||b~||, rho_i = 1, v_1 = b~ / beta
+    SGN_CUDA(mdot<T>(VB, 0, V, n, n, ncol, rd, 1, nullptr, st));
+    SGN_CUDA(reduce(rd, 1, ncol, RM_BETA_FIRST, 0, E.S, nullptr, st));
+    SGN_CUDA(maxpy_scale<T>(VB, 0, E.S.red, E.S.rstride, V, n, V, n, E.S.scale, n, ncol, E.S.skip, st));
+
+    const uint64_t key = cycle_key(c, E, a);
+    if (E.graph && E.graph_key != key) {
+        cudaGraphExecDestroy(E.graph);
+        E.graph = nullptr;
+    }
+    static const bool no_graph = [] {
+        const char* s = getenv("SGN_NO_GRAPH");
+        return s && s[0] == '1';
+    }();
+    if (!E.graph && !no_graph) {
+        cudaGraph_t g = nullptr;
+        SGN_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        cudaError_t ce = cycle<T>(c, E, a, st);
+        cudaError_t ee = cudaStreamEndCapture(st, &g);
+        if (ce != cudaSuccess || ee != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            set_error(std::string("capturing the restart cycle failed: ") +
+                      cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+            return SGN_ERR_CUDA;
+        }
+        cudaError_t ie = cudaGraphInstantiate(&E.graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) {
+            E.graph = nullptr;
+            set_error(std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+            return SGN_ERR_CUDA;
+        }
+        E.graph_key = key;
+    }
+    int cyc = 0;
+    bool all_done = false;
+    for (; cyc < max_cycles; ++cyc) {
+        if (E.graph) {
+            SGN_CUDA(cudaGraphLaunch(E.graph, st));
+        } else {
+            SGN_CUDA(cycle<T>(c, E, a, st));
+        }
+        SGN_CUDA(cudaMemcpyAsync(E.h_done, E.S.done, ncol * sizeof(int), cudaMemcpyDeviceToHost, st));
+        SGN_CUDA(cudaMemcpyAsync(E.h_err, E.S.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        SGN_CUDA(cudaStreamSynchronize(st));
+        if (*E.h_err) break;
+        all_done = true;
+        for (int i = 0; i < ncol; ++i) all_done = all_done && E.h_done[i];
+        if (all_done) {
+            ++cyc;
+            break;
+        }
+    }
+    SGN_CUDA(cudaMemcpyAsync(E.h_resest, E.S.resest, ncol * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SGN_CUDA(cudaMemcpyAsync(E.h_kk, E.S.kk, ncol * sizeof(int), cudaMemcpyDeviceToHost, st));
+    SGN_CUDA(cudaStreamSynchronize(st));
+    res->cycles = cyc;
+    res->converged = all_done;
+    res->err = *E.h_err;
+    res->resmax = 0;
+    for (int i = 0; i < ncol; ++i) res->resmax = std::max(res->resmax, E.h_resest[i]);
+    if (res->err & 1) {
+        set_error("a shifted Hessenberg system was singular (a shift lies on a Ritz value)");
+        return SGN_ERR_BREAKDOWN;
+    }
+    if (res->err & 2) {
+        set_error("non-finite value met in the Arnoldi process");
+        return SGN_ERR_NONFINITE;
+    }
+    return SGN_OK;
+}
+
+int ensure_io(sgn_ctx* c, size_t bytes) {
+    if (c->io.p && c->io.bytes >= bytes) return SGN_OK;
+    SGN_CUDA(cudaStreamSynchronize(c->work));
+    return dev_alloc(c, c->io, bytes);
+}
+
+int fill_shift_tables(sgn_ctx* c, Engine& E, const double* sig_cols, const double* om_cols) {
+    SGN_CUDA(cudaMemcpyAsync(E.sigma_dev, sig_cols, sizeof(double) * E.ncol * E.s, cudaMemcpyHostToDevice, c->work));
+    SGN_CUDA(cudaMemcpyAsync(E.omega_dev, om_cols, sizeof(double) * E.ncol * E.s, cudaMemcpyHostToDevice, c->work));
+    return SGN_OK;
+}
+
+}  // namespace
+
+// x = x_P + sum_i omega_i x_i on ncol device fields (FP64).  See sgn_apply.
+int solve(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int ncol, bool adjoint, sgn_report* rep) {
+    cudaStream_t st = c->work;
+    const int64_t n = c->n;
+    const int s = (int)c->sigma.size();
+    const int k = c->k;
+    const int m = c->m;
+    const bool mixed = c->precision == SGN_PREC_MIXED;
+    if (mixed) {
+        set_error("mixed-precision solve is not available in this build");
+        return SGN_ERR_ARG;
+    }
+    Engine* E = nullptr;
+    SGN_CHECK(get_engine(c, ncol, k, s, c->precision, &E));
+    // io: xacc (ncol n) | r0 (ncol n) | xs (s ncol n, optional)
+    const size_t field = (size_t)n * sizeof(double2);
+    const size_t f_cols = align256(field * ncol);
+    const size_t need = 2 * f_cols + (x_shift ? align256(field * ncol * s) : 0);
+    SGN_CHECK(ensure_io(c, need));
+    char* io = reinterpret_cast<char*>(c->io.p);
+    double2* xacc = reinterpret_cast<double2*>(io);
+    double2* r0 = reinterpret_cast<double2*>(io + f_cols);
+    double2* xs = x_shift ? reinterpret_cast<double2*>(io + 2 * f_cols) : nullptr;
+
+    std::vector<double> sig_cols((size_t)ncol * s), om_cols((size_t)ncol * s);
+    for (int col = 0; col < ncol; ++col)
+        for (int i = 0; i < s; ++i) {
+            sig_cols[(size_t)col * s + i] = c->sigma[i];
+            om_cols[(size_t)col * s + i] = c->omega[i];
+        }
+    SGN_CHECK(fill_shift_tables(c, *E, sig_cols.data(), om_cols.data()));
+
+    const double2* Lb = reinterpret_cast<const double2*>(adjoint ? c->R64.p : c->L64.p);
+    const double2* Rb = reinterpret_cast<const double2*>(adjoint ? c->L64.p : c->R64.p);
+    const double2* lam = reinterpret_cast<const double2*>(adjoint ? c->lamc_dev.p : c->lam_dev.p);
+    const Reduce rd{E->partial, E->nblk, E->rstride};
+    SGN_CUDA(cudaMemsetAsync(E->S.done, 0, ncol * sizeof(int), st));
+    SGN_CUDA(cudaMemsetAsync(E->S.skip, 0, ncol * sizeof(int), st));
+    SGN_CUDA(cudaMemsetAsync(xacc, 0, field * ncol, st));
+    if (xs) SGN_CUDA(cudaMemsetAsync(xs, 0, field * ncol * s, st));
+    const double2* rstart = b;
+    if (m > 0) {
+        // x = x_P = R f(Lambda) L^dag b (eq. (4.3)); r = (I - P) b (eq. (4.2))
+        const Basis<double2> LB{Lb, n, 0}, RB{Rb, n, 0};
+        SGN_CUDA(mdot<double2>(LB, m, b, n, n, ncol, rd, 0, nullptr, st));
+        SGN_CUDA(reduce(rd, m, ncol, RM_SIGNED, 0, E->S, lam, st));
+        SGN_CUDA(update_x<double2>(RB, m, E->S.red, E->rstride, xacc, n, n, ncol, nullptr, nullptr, st));
+        SGN_CUDA(reduce(rd, m, ncol, RM_STORE, 0, E->S, nullptr, st));
+        SGN_CUDA(maxpy_scale<double2>(RB, m, E->S.red, E->rstride, b, n, r0, n, nullptr, n, ncol, nullptr, st));
+        rstart = r0;
+    }
+    // b~ = A (I - P) b is the first restart vector (A^2 reading of eq. (6.2))
+    SGN_CUDA(apply_hw64(c, reinterpret_cast<double2*>(E->V), rstart, ncol, adjoint, nullptr, st));
+
+    CycleArgs a;
+    a.adjoint = adjoint;
+    a.L = Lb;
+    a.R = Rb;
+    a.m = m;
+    a.project = c->project;
+    a.xacc = xacc;
+    a.xsr = n;
+    a.xs = xs;
+    a.xs_shift = (int64_t)ncol * n;
+    a.xs_col = n;
+    RunResult rr;
+    int status = run_engine<double2>(c, *E, a, c->tol, c->max_cycles, &rr);
+    if (status == SGN_OK) {
+        SGN_CUDA(cudaMemcpyAsync(x, xacc, field * ncol, cudaMemcpyDeviceToDevice, st));
+        if (x_shift) SGN_CUDA(cudaMemcpyAsync(x_shift, xs, field * ncol * s, cudaMemcpyDeviceToDevice, st));
+        if (!rr.converged) {
+            status = SGN_ERR_NOT_CONVERGED;
+            set_error("max_cycles reached before every shifted system met the tolerance");
+        }
+    }
+    if (rep) {
+        rep->status = status;
+        rep->cycles = rr.cycles;
+        rep->matvecs = 1 + 2 * k * rr.cycles;
+        rep->refine_rounds = 0;
+        rep->refine_cycles = 0;
+        rep->res_est = rr.resmax;
+        rep->err_est = 0;
+        int bd = 0;
+        for (int i = 0; i < ncol; ++i) bd |= E->h_kk[i] < k;
+        rep->breakdown = bd;
+    }
+    return status;
+}
+
+}  // namespace sgn
