@@ -84,6 +84,7 @@ typedef struct {
     double res_est;       /* max over columns and shifts of |rho_i| ||r|| / ||b~|| */
     double err_est;       /* mixed form: estimated relative error of x after refinement */
     double ms;            /* wall time of the call in milliseconds (device events) */
+    long long kernels;    /* kernel launches issued by the call (graph nodes counted per replay) */
 } sgn_report;
 
 /* Create a context for a lattice of extent dims[4] = {Lx, Ly, Lz, Lt} (each >= 2).

@@ -22,7 +22,8 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
 class Report(C.Structure):
     _fields_ = [("status", C.c_int), ("cycles", C.c_int), ("matvecs", C.c_int), ("refine_rounds", C.c_int),
                 ("refine_cycles", C.c_int), ("breakdown", C.c_int), ("res_est", C.c_double),
-                ("err_est", C.c_double), ("ms", C.c_double)]
+                ("err_est", C.c_double), ("ms", C.c_double),
+                ("kernels", C.c_longlong)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -9,6 +9,7 @@
 namespace sgn {
 
 static thread_local std::string g_last_error;
+thread_local long long g_launches = 0;
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
@@ -291,6 +292,7 @@ int apply_common(sgn_ctx* c, const double* b, double* x, double* x_shift, int nr
     if (host && !finite_host(b, 2 * (size_t)c->n * nrhs))
         return fail(SGN_ERR_NONFINITE, "sgn_apply: non-finite entry in b");
     SGN_CHECK(enter(c));
+    const long long launches0 = g_launches;
     SGN_CUDA(cudaEventRecord(c->ev_t0, c->work));
     const double2* bd = reinterpret_cast<const double2*>(b);
     double2* xd = reinterpret_cast<double2*>(x);
@@ -310,6 +312,7 @@ int apply_common(sgn_ctx* c, const double* b, double* x, double* x_shift, int nr
         float ms = 0;
         cudaEventElapsedTime(&ms, c->ev_t0, c->ev_t1);
         rep->ms = ms;
+        rep->kernels = g_launches - launches0;
     }
     SGN_CHECK(leave(c));
     return status;

@@ -504,6 +504,87 @@ __global__ void __launch_bounds__(NT) k_reduce(Reduce rd, int nslot, int mode, i
     }
 }
 
+// out = a x + b y + c z on whole blocks (real coefficients; z may be null).
+template <class T>
+__global__ void __launch_bounds__(NT) k_axpby3(T* __restrict__ out, double a, const T* __restrict__ x, double b,
+                                               const T* __restrict__ y, double c, const T* __restrict__ z,
+                                               int64_t npk) {
+    using O = Ops<T>;
+    for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < npk; i += (int64_t)gridDim.x * NT) {
+        typename O::P v = O::scal(O::ld(x, i), a);
+        typename O::P w = O::scal(O::ld(y, i), b);
+        typename O::P r;
+        if constexpr (O::CPX == 1) {
+            r = make_double2(v.x + w.x, v.y + w.y);
+        } else {
+            r = make_float4(v.x + w.x, v.y + w.y, v.z + w.z, v.w + w.w);
+        }
+        if (z) {
+            typename O::P u = O::scal(O::ld(z, i), c);
+            if constexpr (O::CPX == 1) {
+                r = make_double2(r.x + u.x, r.y + u.y);
+            } else {
+                r = make_float4(r.x + u.x, r.y + u.y, r.z + u.z, r.w + u.w);
+            }
+        }
+        O::st(out, i, r);
+    }
+}
+
+// Z_j = sum_i C[i][j] Y_i  (Y: q fields, Z: r fields, each n complex apart; C row-major q x r).
+template <class T>
+__global__ void __launch_bounds__(NT) k_block_combine(const T* __restrict__ Y, int q, const double2* __restrict__ Cm,
+                                                      int r, T* __restrict__ Z, int64_t n, int64_t npk) {
+    using O = Ops<T>;
+    __shared__ typename O::C cs[72 * SG];
+    const int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
+    for (int g0 = 0; g0 < r; g0 += SG) {
+        const int ng = (r - g0) < SG ? (r - g0) : SG;
+        __syncthreads();
+        for (int t = threadIdx.x; t < q * SG; t += NT) {
+            int a = t / SG, g = t % SG;
+            cs[t] = g < ng ? O::coef(Cm[(int64_t)a * r + g0 + g]) : O::coef(make_double2(0, 0));
+        }
+        __syncthreads();
+        if (i < npk) {
+            typename O::P acc[SG];
+#pragma unroll
+            for (int g = 0; g < SG; ++g) acc[g] = O::zero();
+            for (int a = 0; a < q; ++a) {
+                typename O::P v = O::ld_ro(Y + a * n, i);
+#pragma unroll
+                for (int g = 0; g < SG; ++g) O::add_cv(acc[g], cs[a * SG + g], v);
+            }
+#pragma unroll
+            for (int g = 0; g < SG; ++g)
+                if (g < ng) O::st(Z + (int64_t)(g0 + g) * n, i, acc[g]);
+        }
+    }
+}
+
+// Counter-based Gaussian start vectors: SplitMix64 of (seed, index), Box-Muller.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    x += 0x9e3779b97f4a7c15ULL;
+    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    x = (x ^ (x >> 27)) * 0x94d049bb133111ebULL;
+    return x ^ (x >> 31);
+}
+template <class T>
+__global__ void k_random_fill(T* out, int64_t count, uint64_t seed) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t h1 = splitmix64(seed ^ (2 * (uint64_t)i)), h2 = splitmix64(seed ^ (2 * (uint64_t)i + 1));
+        double u1 = ((h1 >> 11) + 1.0) * (1.0 / 9007199254740993.0);
+        double u2 = (h2 >> 11) * (1.0 / 9007199254740992.0);
+        double rr = sqrt(-2.0 * log(u1));
+        double re = rr * cos(6.283185307179586 * u2), im = rr * sin(6.283185307179586 * u2);
+        if constexpr (sizeof(T) == 16) {
+            out[i] = T{re, im};
+        } else {
+            out[i] = T{(float)re, (float)im};
+        }
+    }
+}
+
 __global__ void k_f64_to_f32(const double2* __restrict__ in, float2* __restrict__ out, int64_t count) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
         double2 v = in[i];
@@ -546,6 +627,7 @@ cudaError_t mdot(Basis<T> V, int J, const T* w, int64_t wsr, int64_t n, int ncol
     int64_t npk = n / Ops<T>::CPX;
     dim3 grid(rd.nblk, ncol);
     k_mdot<T><<<grid, NT, 0, st>>>(V, J, w, wsr, npk, rd, with_norm, skip);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -553,6 +635,7 @@ cudaError_t reduce(const Reduce& rd, int nslot, int ncol, int mode, int colidx, 
                    const double2* lambda, cudaStream_t st) {
     if (nslot > MAXSLOT) return cudaErrorInvalidValue;
     k_reduce<<<ncol, NT, 0, st>>>(rd, nslot, mode, colidx, S, lambda);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -563,6 +646,7 @@ cudaError_t maxpy_mdot(Basis<T> V, int J, const double2* coef, int cstride, T* w
     int64_t npk = n / Ops<T>::CPX;
     dim3 grid(rd.nblk, ncol);
     k_maxpy_mdot<T><<<grid, NT, 0, st>>>(V, J, coef, cstride, w, wsr, npk, rd, skip);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -573,6 +657,7 @@ cudaError_t maxpy_scale(Basis<T> V, int J, const double2* coef, int cstride, con
     int64_t npk = n / Ops<T>::CPX;
     dim3 grid(reduce_blocks<T>(n), ncol);
     k_maxpy_scale<T><<<grid, NT, 0, st>>>(V, J, coef, cstride, w, wsr, out, osr, scale, npk, skip);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -583,6 +668,7 @@ cudaError_t update_x(Basis<T> V, int J, const double2* coef, int cstride, double
     int64_t npk = n / Ops<T>::CPX;
     dim3 grid(reduce_blocks<T>(n), ncol);
     k_update_x<T><<<grid, NT, 0, st>>>(V, J, coef, cstride, x, xsr, npk, skip, kk);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -594,19 +680,58 @@ cudaError_t update_shifts(Basis<T> V, int J, const double2* y, int s, int kmax, 
     if (smem > 48 * 1024) return cudaErrorInvalidValue;
     dim3 grid((unsigned)((npk + NT - 1) / NT), ncol);
     k_update_shifts<T><<<grid, NT, smem, st>>>(V, J, y, s, kmax, xs, xs_shift, xs_col, npk, skip, kk);
+    count_launch();
     return cudaGetLastError();
 }
 
+template <class T>
+cudaError_t axpby3(T* out, double a, const T* x, double b, const T* y, double c, const T* z, int64_t count,
+                   cudaStream_t st) {
+    int64_t npk = count / Ops<T>::CPX;
+    k_axpby3<T><<<grid_for(npk), NT, 0, st>>>(out, a, x, b, y, c, z, npk);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t block_combine(const T* Y, int q, const double2* Cm, int r, T* Z, int64_t n, cudaStream_t st) {
+    if (q > 72 || r < 1) return cudaErrorInvalidValue;
+    int64_t npk = n / Ops<T>::CPX;
+    k_block_combine<T><<<(unsigned)((npk + NT - 1) / NT), NT, 0, st>>>(Y, q, Cm, r, Z, n, npk);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t random_fill(T* out, int64_t count, uint64_t seed, cudaStream_t st) {
+    k_random_fill<T><<<grid_for(count), 256, 0, st>>>(out, count, seed);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template cudaError_t axpby3<double2>(double2*, double, const double2*, double, const double2*, double,
+                                     const double2*, int64_t, cudaStream_t);
+template cudaError_t axpby3<float2>(float2*, double, const float2*, double, const float2*, double, const float2*,
+                                    int64_t, cudaStream_t);
+template cudaError_t block_combine<double2>(const double2*, int, const double2*, int, double2*, int64_t,
+                                            cudaStream_t);
+template cudaError_t block_combine<float2>(const float2*, int, const double2*, int, float2*, int64_t, cudaStream_t);
+template cudaError_t random_fill<double2>(double2*, int64_t, uint64_t, cudaStream_t);
+template cudaError_t random_fill<float2>(float2*, int64_t, uint64_t, cudaStream_t);
+
 cudaError_t convert_f64_to_f32(const double2* in, float2* out, int64_t count, cudaStream_t st) {
     k_f64_to_f32<<<grid_for(count), 256, 0, st>>>(in, out, count);
+    count_launch();
     return cudaGetLastError();
 }
 cudaError_t convert_f32_to_f64(const float2* in, double2* out, int64_t count, cudaStream_t st) {
     k_f32_to_f64<<<grid_for(count), 256, 0, st>>>(in, out, count);
+    count_launch();
     return cudaGetLastError();
 }
 cudaError_t links_f64_to_bf16(const double2* in, __nv_bfloat162* out, int64_t count, cudaStream_t st) {
     k_f64_to_bf16<<<grid_for(count), 256, 0, st>>>(in, out, count);
+    count_launch();
     return cudaGetLastError();
 }
 

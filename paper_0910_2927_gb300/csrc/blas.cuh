@@ -60,6 +60,17 @@ template <class T>
 cudaError_t update_shifts(Basis<T> V, int J, const double2* y, int s, int kmax, double2* xs, int64_t xs_shift,
                           int64_t xs_col, int64_t n, int ncol, const int* skip, const int* kk, cudaStream_t st);
 
+// out = a x + b y + c z over `count` complex elements (z may be null).
+template <class T>
+cudaError_t axpby3(T* out, double a, const T* x, double b, const T* y, double c, const T* z, int64_t count,
+                   cudaStream_t st);
+// Z_j = sum_i C[i][j] Y_i for q input and r output fields of n complex (C: device, row-major q x r).
+template <class T>
+cudaError_t block_combine(const T* Y, int q, const double2* C, int r, T* Z, int64_t n, cudaStream_t st);
+// Seeded complex Gaussian entries (counter-based, SplitMix64 + Box-Muller).
+template <class T>
+cudaError_t random_fill(T* out, int64_t count, uint64_t seed, cudaStream_t st);
+
 // Type conversions of whole fields.
 cudaError_t convert_f64_to_f32(const double2* in, float2* out, int64_t count, cudaStream_t st);
 cudaError_t convert_f32_to_f64(const float2* in, double2* out, int64_t count, cudaStream_t st);

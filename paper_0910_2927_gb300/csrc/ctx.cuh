@@ -48,6 +48,7 @@ struct Engine {
     // captured restart cycle
     cudaGraphExec_t graph = nullptr;
     uint64_t graph_key = 0;
+    long long graph_kernels = 0;  // kernel nodes of the captured cycle
 };
 
 }  // namespace sgn

@@ -1,16 +1,468 @@
-// Deflation set-up: critical eigenpairs of H_W(mu) on the GPU (Sec. 4).
+// Deflation set-up: the critical eigenpairs of A = H_W(mu) for LR deflation
+// (Sec. 4, eq. (4.1)).  The paper takes R, L, Lambda as given; this file
+// computes them on the GPU.
+//
+// Right eigenvectors: the m + extra eigenvalues of smallest |lambda|.  They are
+// the eigenvalues of A^2 of smallest modulus, i.e. the low end of the
+// spectrum of A^2, which a Chebyshev polynomial in A^2 on [a, b] amplifies
+// (b bounds |lambda|^2 from above, a is the top of the current block).  Block
+// subspace iteration with that filter, SVQB orthonormalisation (Gram matrix,
+// Hermitian eigendecomposition, rank-safe inverse square root) and a
+// Rayleigh-Ritz step with A itself, which separates the eigenvectors of A
+// whose eigenvalues share a square.  The filter runs in FP32 until the
+// eigen-residuals reach 1e-5, then in FP64 to the requested tolerance.
+// Left eigenvectors: the same on A^dag = H_W(-mu) (eigenvalues conj(lambda)).
+// Finally L is rescaled to the dual basis, L <- L (L^dag R)^{-dag}, so that
+// L^dag R = I.
 #include "ctx.cuh"
+#include "dense_eig.h"
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
 
 namespace sgn {
+namespace {
+
+using cd = std::complex<double>;
+
+template <class T>
+cudaError_t hw(const sgn_ctx* c, T* out, const T* in, int ncol, bool adj, cudaStream_t st);
+template <>
+cudaError_t hw<double2>(const sgn_ctx* c, double2* out, const double2* in, int ncol, bool adj, cudaStream_t st) {
+    return apply_hw64(c, out, in, ncol, adj, nullptr, st);
+}
+template <>
+cudaError_t hw<float2>(const sgn_ctx* c, float2* out, const float2* in, int ncol, bool adj, cudaStream_t st) {
+    return apply_hw32(c, out, in, ncol, adj, nullptr, st);
+}
+
+struct Work {
+    sgn_ctx* c = nullptr;
+    int q = 0;
+    int64_t n = 0;
+    DevBuf buf;
+    void* blk[5] = {};  // Y, Yprev, Ynext, T1, T2 (q fields each, storage type of the phase)
+    double2* partial = nullptr;
+    int nblk = 0;
+    int rstride = 0;
+    DevState S{};
+    double2* Cdev = nullptr;   // q x q coefficients
+    double2* coef = nullptr;   // q x rstride per-column coefficients
+    std::vector<double2> hred;
+};
+
+int setup(Work& W, sgn_ctx* c, int q, size_t esz, int nblk) {
+    W.c = c;
+    W.q = q;
+    W.n = c->n;
+    W.nblk = nblk;
+    W.rstride = 80;
+    const size_t blkb = (size_t)q * c->n * esz;
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        size_t o = off;
+        off += (b + 255) & ~size_t(255);
+        return o;
+    };
+    size_t ob[5];
+    for (int i = 0; i < 5; ++i) ob[i] = take(blkb);
+    size_t op = take((size_t)q * W.rstride * nblk * sizeof(double2));
+    size_t ored = take((size_t)q * W.rstride * sizeof(double2));
+    size_t oc = take((size_t)q * q * sizeof(double2));
+    size_t ocoef = take((size_t)q * W.rstride * sizeof(double2));
+    size_t oint = take((size_t)3 * q * sizeof(int));
+    SGN_CHECK(dev_alloc(c, W.buf, off));
+    char* b = reinterpret_cast<char*>(W.buf.p);
+    for (int i = 0; i < 5; ++i) W.blk[i] = b + ob[i];
+    W.partial = reinterpret_cast<double2*>(b + op);
+    W.S.red = reinterpret_cast<double2*>(b + ored);
+    W.Cdev = reinterpret_cast<double2*>(b + oc);
+    W.coef = reinterpret_cast<double2*>(b + ocoef);
+    W.S.skip = reinterpret_cast<int*>(b + oint);
+    W.S.done = W.S.skip + q;
+    W.S.kk = W.S.skip + 2 * q;
+    W.S.rstride = W.rstride;
+    SGN_CUDA(cudaMemsetAsync(W.buf.p, 0, off, c->work));
+    W.hred.resize((size_t)q * W.rstride);
+    return SGN_OK;
+}
+
+// G[i][j] = X_i^dag Y_j for p fields X and r fields Y (row-major p x r on the host).
+template <class T>
+int gram(Work& W, const T* X, int p, const T* Y, int r, std::vector<cd>& G) {
+    cudaStream_t st = W.c->work;
+    const Reduce rd{W.partial, W.nblk, W.rstride};
+    SGN_CUDA(mdot<T>(Basis<T>{X, W.n, 0}, p, Y, W.n, W.n, r, rd, 0, nullptr, st));
+    SGN_CUDA(reduce(rd, p, r, RM_STORE, 0, W.S, nullptr, st));
+    SGN_CUDA(cudaMemcpyAsync(W.hred.data(), W.S.red, sizeof(double2) * r * W.rstride, cudaMemcpyDeviceToHost, st));
+    SGN_CUDA(cudaStreamSynchronize(st));
+    G.assign((size_t)p * r, 0.0);
+    for (int j = 0; j < r; ++j)
+        for (int i = 0; i < p; ++i) {
+            double2 v = W.hred[(size_t)j * W.rstride + i];
+            G[(size_t)i * r + j] = cd(v.x, v.y);
+        }
+    return SGN_OK;
+}
+
+// Z = Y C (C host row-major q x r).
+template <class T>
+int combine(Work& W, const T* Y, int q, const std::vector<cd>& Cm, int r, T* Z) {
+    cudaStream_t st = W.c->work;
+    std::vector<double2> h((size_t)q * r);
+    for (size_t i = 0; i < h.size(); ++i) h[i] = make_double2(Cm[i].real(), Cm[i].imag());
+    SGN_CUDA(cudaMemcpyAsync(W.Cdev, h.data(), sizeof(double2) * h.size(), cudaMemcpyHostToDevice, st));
+    SGN_CUDA(block_combine<T>(Y, q, W.Cdev, r, Z, W.n, st));
+    SGN_CUDA(cudaStreamSynchronize(st));  // h is released on return
+    return SGN_OK;
+}
+
+// Orthonormalise the q fields of Y in place (tmp: q fields of scratch).  SVQB:
+// G = Y^dag Y, D = diag(G)^{-1/2}, D G D = V diag(l) V^dag, Y <- Y D V diag(l)^{-1/2}
+// with l floored at eps * max(l) so that dependent columns do not blow up.
+template <class T>
+int svqb(Work& W, T* Y, T* tmp, double eps) {
+    const int q = W.q;
+    std::vector<cd> G;
+    SGN_CHECK(gram<T>(W, Y, q, Y, q, G));
+    std::vector<double> d(q);
+    for (int i = 0; i < q; ++i) {
+        double g = G[(size_t)i * q + i].real();
+        d[i] = g > 0 ? 1.0 / std::sqrt(g) : 0.0;
+    }
+    for (int i = 0; i < q; ++i)
+        for (int j = 0; j < q; ++j) G[(size_t)i * q + j] *= d[i] * d[j];
+    // make exactly Hermitian
+    for (int i = 0; i < q; ++i)
+        for (int j = 0; j < i; ++j) {
+            cd a = 0.5 * (G[(size_t)i * q + j] + std::conj(G[(size_t)j * q + i]));
+            G[(size_t)i * q + j] = a;
+            G[(size_t)j * q + i] = std::conj(a);
+        }
+    std::vector<cd> w, V;
+    if (dense_eig(q, G, w, V)) {
+        set_error("deflation set-up: eigendecomposition of the Gram matrix failed");
+        return SGN_ERR_DEFLATION;
+    }
+    double lmax = 0;
+    for (auto& z : w) lmax = std::max(lmax, z.real());
+    std::vector<cd> Cm((size_t)q * q);
+    for (int j = 0; j < q; ++j) {
+        double l = std::max(w[j].real(), eps * lmax);
+        double sc = 1.0 / std::sqrt(l);
+        for (int i = 0; i < q; ++i) Cm[(size_t)i * q + j] = d[i] * V[(size_t)i * q + j] * sc;
+    }
+    SGN_CHECK(combine<T>(W, Y, q, Cm, q, tmp));
+    SGN_CUDA(cudaMemcpyAsync(Y, tmp, sizeof(T) * q * W.n, cudaMemcpyDeviceToDevice, W.c->work));
+    return SGN_OK;
+}
+
+// Chebyshev filter T_d(s(A^2)) Y, s(t) = (2t - (a+b)) / (b - a), in place.
+template <class T>
+int filter(Work& W, bool adj, T* Y, double a, double b, int deg) {
+    cudaStream_t st = W.c->work;
+    const int q = W.q;
+    const int64_t cnt = (int64_t)q * W.n;
+    T* Yp = reinterpret_cast<T*>(W.blk[1]);
+    T* Yn = reinterpret_cast<T*>(W.blk[2]);
+    T* T1 = reinterpret_cast<T*>(W.blk[3]);
+    T* T2 = reinterpret_cast<T*>(W.blk[4]);
+    const double al = 2.0 / (b - a), be = -(a + b) / (b - a);
+    T* cur = Y;
+    // Y1 = s(A^2) Y0
+    SGN_CUDA(hw<T>(W.c, T1, cur, q, adj, st));
+    SGN_CUDA(hw<T>(W.c, T2, T1, q, adj, st));
+    SGN_CUDA(cudaMemcpyAsync(Yp, cur, sizeof(T) * cnt, cudaMemcpyDeviceToDevice, st));
+    SGN_CUDA(axpby3<T>(Yn, al, T2, be, Yp, 0.0, nullptr, cnt, st));
+    T* prev = Yp;
+    T* now = Yn;
+    T* spare = cur;
+    for (int j = 1; j < deg; ++j) {
+        SGN_CUDA(hw<T>(W.c, T1, now, q, adj, st));
+        SGN_CUDA(hw<T>(W.c, T2, T1, q, adj, st));
+        SGN_CUDA(axpby3<T>(spare, 2 * al, T2, 2 * be, now, -1.0, prev, cnt, st));
+        T* t = prev;
+        prev = now;
+        now = spare;
+        spare = t;
+    }
+    if (now != Y) SGN_CUDA(cudaMemcpyAsync(Y, now, sizeof(T) * cnt, cudaMemcpyDeviceToDevice, st));
+    return SGN_OK;
+}
+
+struct Ritz {
+    std::vector<cd> theta;
+    std::vector<double> res;  // relative eigen-residuals
+};
+
+bool ritz_less(cd a, cd b) {
+    if (std::abs(a) != std::abs(b)) return std::abs(a) < std::abs(b);
+    if (a.real() != b.real()) return a.real() < b.real();
+    return a.imag() < b.imag();
+}
+
+// Rayleigh-Ritz with A on span(Y) (Y orthonormal): Y <- Ritz vectors sorted by |theta|.
+template <class T>
+int rayleigh_ritz(Work& W, bool adj, T* Y, Ritz& out) {
+    cudaStream_t st = W.c->work;
+    const int q = W.q;
+    T* Z = reinterpret_cast<T*>(W.blk[3]);
+    T* Yw = reinterpret_cast<T*>(W.blk[1]);
+    T* Zw = reinterpret_cast<T*>(W.blk[2]);
+    SGN_CUDA(hw<T>(W.c, Z, Y, q, adj, st));
+    std::vector<cd> G;
+    SGN_CHECK(gram<T>(W, Y, q, Z, q, G));
+    std::vector<cd> w, X;
+    if (dense_eig(q, G, w, X)) {
+        set_error("deflation set-up: Rayleigh-Ritz eigendecomposition failed");
+        return SGN_ERR_DEFLATION;
+    }
+    std::vector<int> ord(q);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::sort(ord.begin(), ord.end(), [&](int i, int j) { return ritz_less(w[i], w[j]); });
+    std::vector<cd> Xs((size_t)q * q);
+    out.theta.resize(q);
+    for (int j = 0; j < q; ++j) {
+        out.theta[j] = w[ord[j]];
+        for (int i = 0; i < q; ++i) Xs[(size_t)i * q + j] = X[(size_t)i * q + ord[j]];
+    }
+    SGN_CHECK(combine<T>(W, Y, q, Xs, q, Yw));
+    SGN_CHECK(combine<T>(W, Z, q, Xs, q, Zw));
+    // residuals ||Z_j - theta_j Y_j||, ||Y_j||
+    std::vector<double2> th((size_t)q * W.rstride, make_double2(0, 0));
+    for (int j = 0; j < q; ++j) th[(size_t)j * W.rstride] = make_double2(out.theta[j].real(), out.theta[j].imag());
+    SGN_CUDA(cudaMemcpyAsync(W.coef, th.data(), sizeof(double2) * th.size(), cudaMemcpyHostToDevice, st));
+    const Reduce rd{W.partial, W.nblk, W.rstride};
+    SGN_CUDA(mdot<T>(Basis<T>{Yw, 0, W.n}, 0, Yw, W.n, W.n, q, rd, 1, nullptr, st));
+    SGN_CUDA(reduce(rd, 1, q, RM_STORE, 0, W.S, nullptr, st));
+    SGN_CUDA(cudaMemcpyAsync(W.hred.data(), W.S.red, sizeof(double2) * q * W.rstride, cudaMemcpyDeviceToHost, st));
+    SGN_CUDA(cudaStreamSynchronize(st));
+    std::vector<double> ynorm(q);
+    for (int j = 0; j < q; ++j) ynorm[j] = std::sqrt(W.hred[(size_t)j * W.rstride].x);
+    SGN_CUDA(maxpy_mdot<T>(Basis<T>{Yw, 0, W.n}, 1, W.coef, W.rstride, Zw, W.n, W.n, q, rd, nullptr, st));
+    SGN_CUDA(reduce(rd, 2, q, RM_STORE, 0, W.S, nullptr, st));
+    SGN_CUDA(cudaMemcpyAsync(W.hred.data(), W.S.red, sizeof(double2) * q * W.rstride, cudaMemcpyDeviceToHost, st));
+    SGN_CUDA(cudaStreamSynchronize(st));
+    out.res.resize(q);
+    for (int j = 0; j < q; ++j) {
+        double rn = std::sqrt(std::max(W.hred[(size_t)j * W.rstride + 1].x, 0.0));
+        double den = std::abs(out.theta[j]) * (ynorm[j] > 0 ? ynorm[j] : 1.0);
+        out.res[j] = den > 0 ? rn / den : INFINITY;
+    }
+    // Y <- normalised Ritz vectors
+    std::vector<double> sc(q);
+    for (int j = 0; j < q; ++j) sc[j] = ynorm[j] > 0 ? 1.0 / ynorm[j] : 0.0;
+    std::vector<cd> Dm((size_t)q * q, 0.0);
+    for (int j = 0; j < q; ++j) Dm[(size_t)j * q + j] = sc[j];
+    SGN_CHECK(combine<T>(W, Yw, q, Dm, q, Y));
+    return SGN_OK;
+}
+
+// Upper bound of |lambda|^2 over the spectrum of A: with the orthogonal spin
+// projectors (1 -/+ gamma)/2, each hop pair of direction nu has norm at most
+// sqrt(e^{2 mu d} + e^{-2 mu d}), so ||A|| <= |4 + m_W| + 3 sqrt(2) + sqrt(2 cosh 2mu).
+double spectral_bound2(const sgn_ctx* c) {
+    double nb = std::abs(4.0 + c->mass) + 3.0 * std::sqrt(2.0) + std::sqrt(2.0 * std::cosh(2.0 * c->mu));
+    return nb * nb * 1.0001;
+}
+
+int degree_for(double t_want, double a, double b, double amp) {
+    double sw = std::abs((2 * t_want - b - a) / (b - a));
+    if (!(sw > 1.0 + 1e-12)) return 120;
+    double d = std::acosh(amp) / std::acosh(sw);
+    int di = (int)std::ceil(d);
+    return std::min(120, std::max(4, di));
+}
+
+template <class T>
+int iterate(Work& W, bool adj, T* Y, int want, double tol, int max_it, Ritz& rz, bool fresh, int* its) {
+    const double b = spectral_bound2(W.c);
+    T* tmp = reinterpret_cast<T*>(W.blk[1]);
+    const double eps = sizeof(T) == 16 ? 1e-15 : 1e-7;
+    if (fresh) {
+        SGN_CHECK(svqb<T>(W, Y, tmp, eps));
+        SGN_CHECK(svqb<T>(W, Y, tmp, eps));
+        SGN_CHECK(rayleigh_ritz<T>(W, adj, Y, rz));
+    }
+    for (int it = 0; it < max_it; ++it) {
+        double worst = 0;
+        for (int j = 0; j < want; ++j) worst = std::max(worst, rz.res[j]);
+        if (worst <= tol) {
+            *its = it;
+            return SGN_OK;
+        }
+        const double tw = std::norm(rz.theta[want - 1]);
+        double a = std::norm(rz.theta[W.q - 1]);
+        a = std::max(a, 1.05 * tw);
+        a = std::min(a, 0.9 * b);
+        const int deg = degree_for(tw, a, b, sizeof(T) == 16 ? 1e6 : 1e4);
+        SGN_CHECK(filter<T>(W, adj, Y, a, b, deg));
+        SGN_CHECK(svqb<T>(W, Y, tmp, eps));
+        SGN_CHECK(svqb<T>(W, Y, tmp, eps));
+        SGN_CHECK(rayleigh_ritz<T>(W, adj, Y, rz));
+    }
+    double worst = 0;
+    for (int j = 0; j < want; ++j) worst = std::max(worst, rz.res[j]);
+    *its = max_it;
+    if (worst <= tol) return SGN_OK;
+    set_error("deflation set-up: eigenpairs did not converge (worst relative residual " + std::to_string(worst) +
+              ")");
+    return SGN_ERR_DEFLATION;
+}
+
+// One side: `want` eigenpairs of A (adj = false) or A^dag (adj = true) into V64 (want fields, FP64).
+int eig_side(sgn_ctx* c, bool adj, int want, int q, double tol, uint64_t seed, double2* V64, std::vector<cd>& lam) {
+    cudaStream_t st = c->work;
+    Ritz rz;
+    int its32 = 0, its64 = 0;
+    // FP32 phase
+    {
+        Work W;
+        SGN_CHECK(setup(W, c, q, sizeof(float2), reduce_blocks<float2>(c->n)));
+        float2* Y = reinterpret_cast<float2*>(W.blk[0]);
+        SGN_CUDA(random_fill<float2>(Y, (int64_t)q * c->n, seed, st));
+        int rc = iterate<float2>(W, adj, Y, want, std::max(tol, 1e-5), 60, rz, true, &its32);
+        if (rc != SGN_OK) {
+            dev_free(c, W.buf);
+            return rc;
+        }
+        // hand the block over to the FP64 phase through V64's first q fields? V64 holds only `want`
+        // fields, so stage through a fresh FP64 work buffer instead.
+        Work W64;
+        rc = setup(W64, c, q, sizeof(double2), reduce_blocks<double2>(c->n));
+        if (rc != SGN_OK) {
+            dev_free(c, W.buf);
+            return rc;
+        }
+        double2* Y64 = reinterpret_cast<double2*>(W64.blk[0]);
+        SGN_CUDA(convert_f32_to_f64(Y, Y64, (int64_t)q * c->n, st));
+        SGN_CUDA(cudaStreamSynchronize(st));
+        dev_free(c, W.buf);
+        rc = iterate<double2>(W64, adj, Y64, want, tol, 20, rz, true, &its64);
+        if (rc == SGN_OK)
+            SGN_CUDA(cudaMemcpyAsync(V64, Y64, sizeof(double2) * want * c->n, cudaMemcpyDeviceToDevice, st));
+        SGN_CUDA(cudaStreamSynchronize(st));
+        dev_free(c, W64.buf);
+        if (rc != SGN_OK) return rc;
+    }
+    lam.assign(rz.theta.begin(), rz.theta.begin() + want);
+    return SGN_OK;
+}
+
+}  // namespace
 
 int build_deflation(sgn_ctx* c, int m, int extra, double eig_tol, double* lambda_out) {
-    (void)c;
-    (void)m;
-    (void)extra;
-    (void)eig_tol;
-    (void)lambda_out;
-    set_error("sgn_build_deflation: the eigensolver is not part of this build");
-    return SGN_ERR_DEFLATION;
+    cudaStream_t st = c->work;
+    const int want = m + extra;
+    const int q = std::min(71, want + std::max(8, want / 3));
+    const int64_t n = c->n;
+    DevBuf RL;
+    SGN_CHECK(dev_alloc(c, RL, sizeof(double2) * (size_t)n * (2 * want + m)));
+    double2* Rw = reinterpret_cast<double2*>(RL.p);
+    double2* Lw = Rw + (size_t)want * n;
+    double2* Lm = Lw + (size_t)want * n;
+    std::vector<cd> lamR, lamL;
+    int rc = eig_side(c, false, want, q, eig_tol, 0x5eed0001ULL, Rw, lamR);
+    if (rc == SGN_OK) rc = eig_side(c, true, want, q, eig_tol, 0x5eed0002ULL, Lw, lamL);
+    if (rc != SGN_OK) {
+        dev_free(c, RL);
+        return rc;
+    }
+    // the selection must be unambiguous: |lambda_m| < |lambda_{m+1}|
+    if (extra > 0 && !(std::abs(lamR[m]) - std::abs(lamR[m - 1]) > 1e-8 * std::abs(lamR[m - 1]))) {
+        dev_free(c, RL);
+        set_error("deflation set-up: |lambda_m| and |lambda_m+1| coincide; choose another m");
+        return SGN_ERR_DEFLATION;
+    }
+    // pair every right eigenvalue with the left one whose conjugate is closest
+    std::vector<int> pick(m, -1);
+    std::vector<char> used(want, 0);
+    for (int j = 0; j < m; ++j) {
+        double best = INFINITY;
+        for (int l = 0; l < want; ++l) {
+            if (used[l]) continue;
+            double d = std::abs(lamR[j] - std::conj(lamL[l]));
+            if (d < best) {
+                best = d;
+                pick[j] = l;
+            }
+        }
+        used[pick[j]] = 1;
+        if (best > 1e-6 * std::max(1.0, std::abs(lamR[j]))) {
+            dev_free(c, RL);
+            set_error("deflation set-up: left and right spectra do not match");
+            return SGN_ERR_DEFLATION;
+        }
+    }
+    for (int j = 0; j < m; ++j)
+        SGN_CUDA(cudaMemcpyAsync(Lm + (size_t)j * n, Lw + (size_t)pick[j] * n, sizeof(double2) * n,
+                                 cudaMemcpyDeviceToDevice, st));
+    // L <- L M^{-dag}, M = L^dag R  (then L^dag R = I)
+    {
+        Work W;
+        rc = setup(W, c, m, sizeof(double2), reduce_blocks<double2>(n));
+        std::vector<cd> M;
+        if (rc == SGN_OK) rc = gram<double2>(W, Lm, m, Rw, m, M);
+        std::vector<cd> Mh((size_t)m * m), X((size_t)m * m, 0.0);
+        if (rc == SGN_OK) {
+            for (int i = 0; i < m; ++i)
+                for (int j = 0; j < m; ++j) Mh[(size_t)i * m + j] = std::conj(M[(size_t)j * m + i]);
+            for (int i = 0; i < m; ++i) X[(size_t)i * m + i] = 1.0;
+            if (dense_solve(m, m, Mh, X)) {
+                set_error("deflation set-up: L^dag R is singular");
+                rc = SGN_ERR_DEFLATION;
+            }
+        }
+        // X = M^{-dag}; L_new = L X, written to the Lw slot
+        if (rc == SGN_OK) rc = combine<double2>(W, Lm, m, X, m, Lw);
+        std::vector<cd> chk;
+        if (rc == SGN_OK) rc = gram<double2>(W, Lw, m, Rw, m, chk);
+        if (rc == SGN_OK) {
+            double e = 0;
+            for (int i = 0; i < m; ++i)
+                for (int j = 0; j < m; ++j) e = std::max(e, std::abs(chk[(size_t)i * m + j] - (i == j ? 1.0 : 0.0)));
+            if (!(e < 1e-8)) {
+                set_error("deflation set-up: biorthonormalisation failed (||L^dag R - I|| = " + std::to_string(e) +
+                          ")");
+                rc = SGN_ERR_DEFLATION;
+            }
+        }
+        dev_free(c, W.buf);
+        if (rc != SGN_OK) {
+            dev_free(c, RL);
+            return rc;
+        }
+    }
+    // install as the context's deflation data
+    const size_t cnt = (size_t)n * m;
+    SGN_CHECK(dev_alloc(c, c->R64, cnt * sizeof(double2)));
+    SGN_CHECK(dev_alloc(c, c->L64, cnt * sizeof(double2)));
+    SGN_CHECK(dev_alloc(c, c->R32, cnt * sizeof(float2)));
+    SGN_CHECK(dev_alloc(c, c->L32, cnt * sizeof(float2)));
+    SGN_CHECK(dev_alloc(c, c->lam_dev, (size_t)m * sizeof(double2)));
+    SGN_CHECK(dev_alloc(c, c->lamc_dev, (size_t)m * sizeof(double2)));
+    SGN_CUDA(cudaMemcpyAsync(c->R64.p, Rw, cnt * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    SGN_CUDA(cudaMemcpyAsync(c->L64.p, Lw, cnt * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    SGN_CUDA(convert_f64_to_f32(as<double2>(c->R64), as<float2>(c->R32), (int64_t)cnt, st));
+    SGN_CUDA(convert_f64_to_f32(as<double2>(c->L64), as<float2>(c->L32), (int64_t)cnt, st));
+    std::vector<double2> hl(m), hlc(m);
+    for (int j = 0; j < m; ++j) {
+        hl[j] = make_double2(lamR[j].real(), lamR[j].imag());
+        hlc[j] = make_double2(lamR[j].real(), -lamR[j].imag());
+    }
+    SGN_CUDA(cudaMemcpyAsync(c->lam_dev.p, hl.data(), sizeof(double2) * m, cudaMemcpyHostToDevice, st));
+    SGN_CUDA(cudaMemcpyAsync(c->lamc_dev.p, hlc.data(), sizeof(double2) * m, cudaMemcpyHostToDevice, st));
+    SGN_CUDA(cudaStreamSynchronize(st));
+    dev_free(c, RL);
+    c->lam.assign(lamR.begin(), lamR.begin() + m);
+    c->m = m;
+    if (lambda_out)
+        for (int j = 0; j < want; ++j) {
+            lambda_out[2 * j] = lamR[j].real();
+            lambda_out[2 * j + 1] = lamR[j].imag();
+        }
+    return SGN_OK;
 }
 
 }  // namespace sgn

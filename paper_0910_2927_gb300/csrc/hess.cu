@@ -140,11 +140,13 @@ cudaError_t shifted_solves(const DevState& S, int ncol, cudaStream_t st) {
     if (S.kmax > KMAX) return cudaErrorInvalidValue;
     size_t smem = sizeof(double2) * (size_t)S.kmax * S.kmax;
     k_shifted_solve<<<dim3(S.s, ncol), 32, smem, st>>>(S);
+    count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t combine_shifts(const DevState& S, int ncol, cudaStream_t st) {
     k_combine<<<ncol, 64, 0, st>>>(S);
+    count_launch();
     return cudaGetLastError();
 }
 

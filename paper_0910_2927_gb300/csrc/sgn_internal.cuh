@@ -28,6 +28,11 @@ void set_error(const std::string& msg);
         if (_s != SGN_OK) return _s; \
     } while (0)
 
+// Kernel launches issued by this host thread (launch helpers add 1 each; a graph
+// replay adds its kernel-node count).
+extern thread_local long long g_launches;
+inline void count_launch(long long k = 1) { g_launches += k; }
+
 // ---------------------------------------------------------------- complex --
 __host__ __device__ inline double2 cmul(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);

@@ -340,8 +340,11 @@ int run_engine(sgn_ctx* c, Engine& E, const CycleArgs& a, double tol, int max_cy
     if (!E.graph && !no_graph) {
         cudaGraph_t g = nullptr;
         SGN_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        const long long before = g_launches;
         cudaError_t ce = cycle<T>(c, E, a, st);
         cudaError_t ee = cudaStreamEndCapture(st, &g);
+        E.graph_kernels = g_launches - before;
+        g_launches = before;  // capturing launches nothing
         if (ce != cudaSuccess || ee != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
             set_error(std::string("capturing the restart cycle failed: ") +
@@ -362,6 +365,7 @@ int run_engine(sgn_ctx* c, Engine& E, const CycleArgs& a, double tol, int max_cy
     for (; cyc < max_cycles; ++cyc) {
         if (E.graph) {
             SGN_CUDA(cudaGraphLaunch(E.graph, st));
+            count_launch(E.graph_kernels);
         } else {
             SGN_CUDA(cycle<T>(c, E, a, st));
         }
@@ -409,6 +413,227 @@ int fill_shift_tables(sgn_ctx* c, Engine& E, const double* sig_cols, const doubl
 
 }  // namespace
 
+namespace {
+
+// Mixed form.  Phase 1: Algorithm 1 with the FP32 stencil and FP32 Krylov
+// basis (inner products, norms, Hessenberg matrix, shifted solves, rho and the
+// projection coefficients in FP64), accumulating every shifted iterate x_i in
+// FP64.  Phase 2 (iterative refinement, not part of the paper): the true
+// residual r_i = b~ - (A^2 - sigma_i) x_i of every shifted system is formed in
+// FP64; systems whose relative residual exceeds the tolerance get a correction
+// d_i from restarted FOM on (A^2 - sigma_i) d = (I - P) r_i, again FP32 basis
+// with FP64 scalars, batched one system per column; x_i += d_i.  Rounds repeat
+// until every true residual meets the tolerance that stops the FP64 form.
+constexpr size_t kRefineBudgetBytes = size_t(48) << 30;
+
+int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int ncol, bool adjoint,
+                sgn_report* rep) {
+    cudaStream_t st = c->work;
+    const int64_t n = c->n;
+    const int s = (int)c->sigma.size();
+    const int k = c->k;
+    const int m = c->m;
+    Engine* E = nullptr;
+    SGN_CHECK(get_engine(c, ncol, k, s, SGN_PREC_MIXED, &E));
+    // refinement batch: one shifted system per column, bounded by memory
+    const size_t per_col = (size_t)(k + 4) * n * sizeof(float2) + (size_t)n * sizeof(double2);
+    int B = (int)std::min<size_t>((size_t)s * ncol, std::max<size_t>(1, kRefineBudgetBytes / per_col));
+    Engine* E1 = nullptr;
+    SGN_CHECK(get_engine(c, B, k, 1, SGN_PREC_MIXED, &E1));
+
+    // io: xs (s ncol) | r0, bt, xP, t, u (ncol each) | d (B) | omega table | FP64 partials
+    const size_t field = (size_t)n * sizeof(double2);
+    const int nblk64 = reduce_blocks<double2>(n);
+    const int rs64 = ((std::max(m, s) + 2) + 7) & ~7;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += align256(bytes);
+        return o;
+    };
+    size_t o_xs = take(field * ncol * s);
+    size_t o_r0 = take(field * ncol), o_bt = take(field * ncol), o_xp = take(field * ncol);
+    size_t o_t = take(field * ncol), o_u = take(field * ncol);
+    size_t o_d = take(field * B);
+    size_t o_om = take(sizeof(double2) * ncol * rs64);
+    size_t o_red = take(sizeof(double2) * ncol * rs64);
+    size_t o_part = take(sizeof(double2) * (size_t)std::max(ncol, B) * rs64 * nblk64);
+    size_t o_flags = take(sizeof(int) * 2 * std::max(ncol, B));
+    SGN_CHECK(ensure_io(c, off));
+    char* io = reinterpret_cast<char*>(c->io.p);
+    double2* xs = reinterpret_cast<double2*>(io + o_xs);
+    double2* r0 = reinterpret_cast<double2*>(io + o_r0);
+    double2* bt = reinterpret_cast<double2*>(io + o_bt);
+    double2* xP = reinterpret_cast<double2*>(io + o_xp);
+    double2* t64 = reinterpret_cast<double2*>(io + o_t);
+    double2* u64 = reinterpret_cast<double2*>(io + o_u);
+    double2* d = reinterpret_cast<double2*>(io + o_d);
+    double2* omtab = reinterpret_cast<double2*>(io + o_om);
+    // FP64 reductions use their own partials and state (the FP32 engines size theirs for float packs)
+    DevState S64{};
+    S64.red = reinterpret_cast<double2*>(io + o_red);
+    S64.skip = reinterpret_cast<int*>(io + o_flags);
+    S64.done = S64.skip + std::max(ncol, B);
+    S64.rstride = rs64;
+    const Reduce rd64{reinterpret_cast<double2*>(io + o_part), nblk64, rs64};
+    SGN_CUDA(cudaMemsetAsync(S64.skip, 0, sizeof(int) * 2 * std::max(ncol, B), st));
+
+    std::vector<double> sig_cols((size_t)ncol * s), om_cols((size_t)ncol * s);
+    std::vector<double2> omh((size_t)ncol * rs64, make_double2(0, 0));
+    for (int col = 0; col < ncol; ++col)
+        for (int i = 0; i < s; ++i) {
+            sig_cols[(size_t)col * s + i] = c->sigma[i];
+            om_cols[(size_t)col * s + i] = c->omega[i];
+            omh[(size_t)col * rs64 + i] = make_double2(c->omega[i], 0);
+        }
+    SGN_CHECK(fill_shift_tables(c, *E, sig_cols.data(), om_cols.data()));
+    SGN_CUDA(cudaMemcpyAsync(omtab, omh.data(), sizeof(double2) * omh.size(), cudaMemcpyHostToDevice, st));
+
+    const double2* Lb = reinterpret_cast<const double2*>(adjoint ? c->R64.p : c->L64.p);
+    const double2* Rb = reinterpret_cast<const double2*>(adjoint ? c->L64.p : c->R64.p);
+    const float2* Lb32 = reinterpret_cast<const float2*>(adjoint ? c->R32.p : c->L32.p);
+    const float2* Rb32 = reinterpret_cast<const float2*>(adjoint ? c->L32.p : c->R32.p);
+    const double2* lam = reinterpret_cast<const double2*>(adjoint ? c->lamc_dev.p : c->lam_dev.p);
+    const Basis<double2> LB{Lb, n, 0}, RB{Rb, n, 0};
+
+    SGN_CUDA(cudaMemsetAsync(xs, 0, field * ncol * s, st));
+    SGN_CUDA(cudaMemsetAsync(xP, 0, field * ncol, st));
+    const double2* rstart = b;
+    if (m > 0) {
+        SGN_CUDA(mdot<double2>(LB, m, b, n, n, ncol, rd64, 0, nullptr, st));
+        SGN_CUDA(reduce(rd64, m, ncol, RM_SIGNED, 0, S64, lam, st));
+        SGN_CUDA(update_x<double2>(RB, m, S64.red, rs64, xP, n, n, ncol, nullptr, nullptr, st));
+        SGN_CUDA(reduce(rd64, m, ncol, RM_STORE, 0, S64, nullptr, st));
+        SGN_CUDA(maxpy_scale<double2>(RB, m, S64.red, rs64, b, n, r0, n, nullptr, n, ncol, nullptr, st));
+        rstart = r0;
+    }
+    SGN_CUDA(apply_hw64(c, bt, rstart, ncol, adjoint, nullptr, st));  // b~ in FP64
+    SGN_CUDA(convert_f64_to_f32(bt, reinterpret_cast<float2*>(E->V), (int64_t)ncol * n, st));
+
+    CycleArgs a;
+    a.adjoint = adjoint;
+    a.L = Lb32;
+    a.R = Rb32;
+    a.m = m;
+    a.project = c->project;
+    a.xs = xs;
+    a.xs_shift = (int64_t)ncol * n;
+    a.xs_col = n;
+    const double tol_inner = std::max(c->tol, 1e-6);
+    RunResult rr;
+    int status = run_engine<float2>(c, *E, a, tol_inner, c->max_cycles, &rr);
+    if (status != SGN_OK) return status;
+    const int ms_cycles = rr.cycles;
+    int ref_rounds = 0, ref_cycles = 0;
+    double worst = 0;
+
+    // ||b~|| per column (FP64)
+    std::vector<double> bnorm(ncol);
+    {
+        SGN_CUDA(mdot<double2>(Basis<double2>{bt, 0, n}, 0, bt, n, n, ncol, rd64, 1, nullptr, st));
+        SGN_CUDA(reduce(rd64, 1, ncol, RM_STORE, 0, S64, nullptr, st));
+        std::vector<double2> h((size_t)ncol * rs64);
+        SGN_CUDA(cudaMemcpyAsync(h.data(), S64.red, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost, st));
+        SGN_CUDA(cudaStreamSynchronize(st));
+        for (int col = 0; col < ncol; ++col) bnorm[col] = std::sqrt(h[(size_t)col * rs64].x);
+    }
+
+    CycleArgs a1;
+    a1.adjoint = adjoint;
+    a1.L = Lb32;
+    a1.R = Rb32;
+    a1.m = m;
+    a1.project = c->project;
+    a1.xs = d;
+    a1.xs_shift = (int64_t)B * n;
+    a1.xs_col = n;
+    const int max_rounds = 8;
+    std::vector<double2> hres((size_t)ncol * rs64);
+    std::vector<double> sig1(B), om1(B, 1.0);
+    for (int round = 0; round <= max_rounds; ++round) {
+        // true residuals r_i = b~ - (A^2 - sigma_i) x_i, projected, in xs-shaped staging one shift at a time
+        std::vector<std::pair<int, int>> todo;  // (shift, column)
+        worst = 0;
+        for (int i = 0; i < s; ++i) {
+            double2* xi = xs + (size_t)i * ncol * n;
+            SGN_CUDA(apply_hw64(c, t64, xi, ncol, adjoint, nullptr, st));
+            SGN_CUDA(apply_hw64(c, u64, t64, ncol, adjoint, nullptr, st));
+            // t64 <- b~ - u + sigma_i x_i
+            SGN_CUDA(axpby3<double2>(t64, 1.0, bt, -1.0, u64, c->sigma[i], xi, (int64_t)ncol * n, st));
+            SGN_CUDA(mdot<double2>(Basis<double2>{t64, 0, n}, 0, t64, n, n, ncol, rd64, 1, nullptr, st));
+            SGN_CUDA(reduce(rd64, 1, ncol, RM_STORE, 0, S64, nullptr, st));
+            SGN_CUDA(cudaMemcpyAsync(hres.data(), S64.red, sizeof(double2) * hres.size(), cudaMemcpyDeviceToHost,
+                                     st));
+            SGN_CUDA(cudaStreamSynchronize(st));
+            for (int col = 0; col < ncol; ++col) {
+                double rel = bnorm[col] > 0 ? std::sqrt(hres[(size_t)col * rs64].x) / bnorm[col] : 0.0;
+                if (!std::isfinite(rel)) {
+                    set_error("non-finite true residual in refinement");
+                    return SGN_ERR_NONFINITE;
+                }
+                worst = std::max(worst, rel);
+                if (rel > c->tol) todo.emplace_back(i, col);
+            }
+        }
+        if (todo.empty() || round == max_rounds) break;
+        ++ref_rounds;
+        // correction solves, B systems at a time
+        for (size_t t0 = 0; t0 < todo.size(); t0 += B) {
+            const int nb = (int)std::min<size_t>(B, todo.size() - t0);
+            float2* V0 = reinterpret_cast<float2*>(E1->V);
+            SGN_CUDA(cudaMemsetAsync(V0, 0, sizeof(float2) * (size_t)B * n, st));
+            for (int j = 0; j < B; ++j) sig1[j] = j < nb ? c->sigma[todo[t0 + j].first] : c->sigma[0];
+            SGN_CHECK(fill_shift_tables(c, *E1, sig1.data(), om1.data()));
+            for (int j = 0; j < nb; ++j) {
+                const int i = todo[t0 + j].first, col = todo[t0 + j].second;
+                double2* xi = xs + ((size_t)i * ncol + col) * n;
+                SGN_CUDA(apply_hw64(c, t64, xi, 1, adjoint, nullptr, st));
+                SGN_CUDA(apply_hw64(c, u64, t64, 1, adjoint, nullptr, st));
+                SGN_CUDA(axpby3<double2>(t64, 1.0, bt + (size_t)col * n, -1.0, u64, c->sigma[i], xi, n, st));
+                if (m > 0 && c->project) {  // keep the correction problem in range(I - P)
+                    SGN_CUDA(mdot<double2>(LB, m, t64, n, n, 1, rd64, 0, nullptr, st));
+                    SGN_CUDA(reduce(rd64, m, 1, RM_STORE, 0, S64, nullptr, st));
+                    SGN_CUDA(maxpy_scale<double2>(RB, m, S64.red, rs64, t64, n, t64, n, nullptr, n, 1, nullptr, st));
+                }
+                SGN_CUDA(convert_f64_to_f32(t64, V0 + (size_t)j * n, n, st));
+            }
+            SGN_CUDA(cudaMemsetAsync(d, 0, field * B, st));
+            RunResult r1;
+            int st1 = run_engine<float2>(c, *E1, a1, std::max(c->tol, 1e-5), c->max_cycles, &r1);
+            if (st1 != SGN_OK) return st1;
+            ref_cycles += r1.cycles;
+            for (int j = 0; j < nb; ++j) {
+                const int i = todo[t0 + j].first, col = todo[t0 + j].second;
+                double2* xi = xs + ((size_t)i * ncol + col) * n;
+                SGN_CUDA(axpby3<double2>(xi, 1.0, xi, 1.0, d + (size_t)j * n, 0.0, nullptr, n, st));
+            }
+        }
+    }
+    // x = x_P + sum_i omega_i x_i
+    SGN_CUDA(cudaMemcpyAsync(x, xP, field * ncol, cudaMemcpyDeviceToDevice, st));
+    SGN_CUDA(update_x<double2>(Basis<double2>{xs, (int64_t)ncol * n, n}, s, omtab, rs64, x, n, n, ncol, nullptr,
+                               nullptr, st));
+    if (x_shift) SGN_CUDA(cudaMemcpyAsync(x_shift, xs, field * ncol * s, cudaMemcpyDeviceToDevice, st));
+    SGN_CUDA(cudaStreamSynchronize(st));
+    if (worst > c->tol) {
+        status = SGN_ERR_NOT_CONVERGED;
+        set_error("mixed form: refinement did not bring every true residual below the tolerance");
+    }
+    if (rep) {
+        rep->status = status;
+        rep->cycles = ms_cycles;
+        rep->matvecs = 1 + 2 * k * ms_cycles;
+        rep->refine_rounds = ref_rounds;
+        rep->refine_cycles = ref_cycles;
+        rep->res_est = rr.resmax;
+        rep->err_est = worst;
+        rep->breakdown = 0;
+    }
+    return status;
+}
+
+}  // namespace
+
 // x = x_P + sum_i omega_i x_i on ncol device fields (FP64).  See sgn_apply.
 int solve(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int ncol, bool adjoint, sgn_report* rep) {
     cudaStream_t st = c->work;
@@ -416,11 +641,7 @@ int solve(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int ncol, 
     const int s = (int)c->sigma.size();
     const int k = c->k;
     const int m = c->m;
-    const bool mixed = c->precision == SGN_PREC_MIXED;
-    if (mixed) {
-        set_error("mixed-precision solve is not available in this build");
-        return SGN_ERR_ARG;
-    }
+    if (c->precision == SGN_PREC_MIXED) return solve_mixed(c, b, x, x_shift, ncol, adjoint, rep);
     Engine* E = nullptr;
     SGN_CHECK(get_engine(c, ncol, k, s, c->precision, &E));
     // io: xacc (ncol n) | r0 (ncol n) | xs (s ncol n, optional)

@@ -248,6 +248,7 @@ cudaError_t launch(typename Field<R>::T* out, const typename Field<R>::T* in, co
     dim3 block(sx, rb);
     dim3 grid((unsigned)((p.vol + sx - 1) / sx), (unsigned)((nrhs + rb - 1) / rb));
     k_hw<R, LinkT><<<grid, block, 0, st>>>(out, in, U, nrhs, p, skip);
+    count_launch();
     return cudaGetLastError();
 }
 
