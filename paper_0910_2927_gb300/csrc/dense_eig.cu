@@ -80,13 +80,66 @@ void givens(cd a, cd b, double& c, cd& s) {
 
 }  // namespace
 
+namespace {
+// Complex Schur form G = Q T Q^dag (T, Q row-major).  Returns 0 on success.
+int schur(int n, const std::vector<cd>& G_in, std::vector<cd>& T, std::vector<cd>& Q, double& norm, int max_iter);
+}  // namespace
+
 int dense_eig(int n, const std::vector<cd>& G_in, std::vector<cd>& w, std::vector<cd>& X, int max_iter) {
-    std::vector<cd> T(G_in);
-    std::vector<cd> Q((size_t)n * n, 0.0);
+    std::vector<cd> T, Q;
+    double norm = 0;
+    if (schur(n, G_in, T, Q, norm, max_iter)) return 1;
+    auto A = [&](int i, int j) -> cd& { return T[(size_t)i * n + j]; };
+    const double eps = 2.220446049250313e-16;
+    // eigenvalues and eigenvectors of the triangular T
+    w.resize(n);
+    for (int i = 0; i < n; ++i) w[i] = A(i, i);
+    std::vector<cd> V((size_t)n * n, 0.0);
+    const double small = eps * std::max(norm, 1e-300);
+    for (int k = 0; k < n; ++k) {
+        V[(size_t)k * n + k] = 1.0;
+        for (int i = k - 1; i >= 0; --i) {
+            cd s = 0;
+            for (int j = i + 1; j <= k; ++j) s += A(i, j) * V[(size_t)j * n + k];
+            cd den = A(i, i) - w[k];
+            if (std::abs(den) < small) den = small;
+            V[(size_t)i * n + k] = -s / den;
+        }
+    }
+    X.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) {
+            cd s = 0;
+            for (int j = 0; j <= k; ++j) s += Q[(size_t)i * n + j] * V[(size_t)j * n + k];
+            X[(size_t)i * n + k] = s;
+        }
+    for (int k = 0; k < n; ++k) {
+        double nr = 0;
+        for (int i = 0; i < n; ++i) nr += std::norm(X[(size_t)i * n + k]);
+        nr = std::sqrt(nr);
+        if (nr > 0)
+            for (int i = 0; i < n; ++i) X[(size_t)i * n + k] /= nr;
+    }
+    return 0;
+}
+
+int herm_eig(int n, const std::vector<cd>& G, std::vector<double>& w, std::vector<cd>& X) {
+    std::vector<cd> T;
+    double norm = 0;
+    if (schur(n, G, T, X, norm, 60)) return 1;
+    w.resize(n);
+    for (int i = 0; i < n; ++i) w[i] = T[(size_t)i * n + i].real();
+    return 0;
+}
+
+namespace {
+int schur(int n, const std::vector<cd>& G_in, std::vector<cd>& T, std::vector<cd>& Q, double& norm, int max_iter) {
+    T = G_in;
+    Q.assign((size_t)n * n, 0.0);
     for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
     auto A = [&](int i, int j) -> cd& { return T[(size_t)i * n + j]; };
     if (n > 2) hessenberg(n, T, Q);
-    double norm = 0;
+    norm = 0;
     for (auto& z : T) norm = std::max(norm, std::abs(z));
     const double eps = 2.220446049250313e-16;
     // shifted QR on the active window [lo, hi]
@@ -147,37 +200,9 @@ int dense_eig(int n, const std::vector<cd>& G_in, std::vector<cd>& w, std::vecto
             }
         }
     }
-    // eigenvalues and eigenvectors of the triangular T
-    w.resize(n);
-    for (int i = 0; i < n; ++i) w[i] = A(i, i);
-    std::vector<cd> V((size_t)n * n, 0.0);
-    const double small = eps * std::max(norm, 1e-300);
-    for (int k = 0; k < n; ++k) {
-        V[(size_t)k * n + k] = 1.0;
-        for (int i = k - 1; i >= 0; --i) {
-            cd s = 0;
-            for (int j = i + 1; j <= k; ++j) s += A(i, j) * V[(size_t)j * n + k];
-            cd den = A(i, i) - w[k];
-            if (std::abs(den) < small) den = small;
-            V[(size_t)i * n + k] = -s / den;
-        }
-    }
-    X.assign((size_t)n * n, 0.0);
-    for (int i = 0; i < n; ++i)
-        for (int k = 0; k < n; ++k) {
-            cd s = 0;
-            for (int j = 0; j <= k; ++j) s += Q[(size_t)i * n + j] * V[(size_t)j * n + k];
-            X[(size_t)i * n + k] = s;
-        }
-    for (int k = 0; k < n; ++k) {
-        double nr = 0;
-        for (int i = 0; i < n; ++i) nr += std::norm(X[(size_t)i * n + k]);
-        nr = std::sqrt(nr);
-        if (nr > 0)
-            for (int i = 0; i < n; ++i) X[(size_t)i * n + k] /= nr;
-    }
     return 0;
 }
+}  // namespace
 
 // Solve A X = B for X (A n x n, B n x r, row-major), Gaussian elimination with partial pivoting.
 int dense_solve(int n, int r, std::vector<cd> A, std::vector<cd>& B) {

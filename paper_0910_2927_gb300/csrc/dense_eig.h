@@ -12,6 +12,11 @@ namespace sgn {
 int dense_eig(int n, const std::vector<std::complex<double>>& G, std::vector<std::complex<double>>& w,
               std::vector<std::complex<double>>& X, int max_iter = 60);
 
+// Hermitian G: eigenvalues (real parts of the Schur diagonal) and the unitary
+// Schur vectors, which are the orthonormal eigenvectors.  Returns 1 on failure.
+int herm_eig(int n, const std::vector<std::complex<double>>& G, std::vector<double>& w,
+             std::vector<std::complex<double>>& X);
+
 // Solve A X = B (A n x n, B n x r, both row-major) in place of B.  Returns 1 if singular.
 int dense_solve(int n, int r, std::vector<std::complex<double>> A, std::vector<std::complex<double>>& B);
 

@@ -7,10 +7,13 @@
 // spectrum of A^2, which a Chebyshev polynomial in A^2 on [a, b] amplifies
 // (b bounds |lambda|^2 from above, a is the top of the current block).  Block
 // subspace iteration with that filter, SVQB orthonormalisation (Gram matrix,
-// Hermitian eigendecomposition, rank-safe inverse square root) and a
-// Rayleigh-Ritz step with A itself, which separates the eigenvectors of A
-// whose eigenvalues share a square.  The filter runs in FP32 until the
-// eigen-residuals reach 1e-5, then in FP64 to the requested tolerance.
+// Hermitian eigendecomposition, rank-safe inverse square root) and
+// Rayleigh-Ritz with A^2, where the wanted eigenvalues are extremal (with the
+// indefinite A itself an unconverged block gives spurious Ritz values near 0,
+// mixtures of eigenvectors of +lambda and -lambda).  Once the invariant
+// subspace of A^2 has converged, one Rayleigh-Ritz step with A on it gives the
+// eigenpairs of A, including pairs whose eigenvalues share a square.  The
+// filter runs in FP32 until the residuals reach 1e-5, then in FP64.
 // Left eigenvectors: the same on A^dag = H_W(-mu) (eigenvalues conj(lambda)).
 // Finally L is rescaled to the dual basis, L <- L (L^dag R)^{-dag}, so that
 // L^dag R = I.
@@ -122,8 +125,7 @@ int combine(Work& W, const T* Y, int q, const std::vector<cd>& Cm, int r, T* Z) 
 // G = Y^dag Y, D = diag(G)^{-1/2}, D G D = V diag(l) V^dag, Y <- Y D V diag(l)^{-1/2}
 // with l floored at eps * max(l) so that dependent columns do not blow up.
 template <class T>
-int svqb(Work& W, T* Y, T* tmp, double eps) {
-    const int q = W.q;
+int svqb(Work& W, T* Y, int q, T* tmp, double eps) {
     std::vector<cd> G;
     SGN_CHECK(gram<T>(W, Y, q, Y, q, G));
     std::vector<double> d(q);
@@ -133,23 +135,23 @@ int svqb(Work& W, T* Y, T* tmp, double eps) {
     }
     for (int i = 0; i < q; ++i)
         for (int j = 0; j < q; ++j) G[(size_t)i * q + j] *= d[i] * d[j];
-    // make exactly Hermitian
-    for (int i = 0; i < q; ++i)
+    for (int i = 0; i < q; ++i)  // make exactly Hermitian
         for (int j = 0; j < i; ++j) {
             cd a = 0.5 * (G[(size_t)i * q + j] + std::conj(G[(size_t)j * q + i]));
             G[(size_t)i * q + j] = a;
             G[(size_t)j * q + i] = std::conj(a);
         }
-    std::vector<cd> w, V;
-    if (dense_eig(q, G, w, V)) {
+    std::vector<double> w;
+    std::vector<cd> V;
+    if (herm_eig(q, G, w, V)) {
         set_error("deflation set-up: eigendecomposition of the Gram matrix failed");
         return SGN_ERR_DEFLATION;
     }
     double lmax = 0;
-    for (auto& z : w) lmax = std::max(lmax, z.real());
+    for (double l : w) lmax = std::max(lmax, l);
     std::vector<cd> Cm((size_t)q * q);
     for (int j = 0; j < q; ++j) {
-        double l = std::max(w[j].real(), eps * lmax);
+        double l = std::max(w[j], eps * lmax);
         double sc = 1.0 / std::sqrt(l);
         for (int i = 0; i < q; ++i) Cm[(size_t)i * q + j] = d[i] * V[(size_t)i * q + j] * sc;
     }
@@ -202,15 +204,22 @@ bool ritz_less(cd a, cd b) {
     return a.imag() < b.imag();
 }
 
-// Rayleigh-Ritz with A on span(Y) (Y orthonormal): Y <- Ritz vectors sorted by |theta|.
+// Rayleigh-Ritz with M = A^2 (squared) or M = A on span(Y), Y orthonormal (q
+// fields): Y <- normalised Ritz vectors sorted by |theta|, with their relative
+// eigen-residuals ||M y - theta y|| / |theta|.
 template <class T>
-int rayleigh_ritz(Work& W, bool adj, T* Y, Ritz& out) {
+int rayleigh_ritz(Work& W, bool adj, bool squared, T* Y, int q, Ritz& out) {
     cudaStream_t st = W.c->work;
-    const int q = W.q;
     T* Z = reinterpret_cast<T*>(W.blk[3]);
     T* Yw = reinterpret_cast<T*>(W.blk[1]);
     T* Zw = reinterpret_cast<T*>(W.blk[2]);
-    SGN_CUDA(hw<T>(W.c, Z, Y, q, adj, st));
+    if (squared) {
+        T* T1 = reinterpret_cast<T*>(W.blk[4]);
+        SGN_CUDA(hw<T>(W.c, T1, Y, q, adj, st));
+        SGN_CUDA(hw<T>(W.c, Z, T1, q, adj, st));
+    } else {
+        SGN_CUDA(hw<T>(W.c, Z, Y, q, adj, st));
+    }
     std::vector<cd> G;
     SGN_CHECK(gram<T>(W, Y, q, Z, q, G));
     std::vector<cd> w, X;
@@ -277,13 +286,14 @@ int degree_for(double t_want, double a, double b, double amp) {
 
 template <class T>
 int iterate(Work& W, bool adj, T* Y, int want, double tol, int max_it, Ritz& rz, bool fresh, int* its) {
+    const int q = W.q;
     const double b = spectral_bound2(W.c);
     T* tmp = reinterpret_cast<T*>(W.blk[1]);
     const double eps = sizeof(T) == 16 ? 1e-15 : 1e-7;
     if (fresh) {
-        SGN_CHECK(svqb<T>(W, Y, tmp, eps));
-        SGN_CHECK(svqb<T>(W, Y, tmp, eps));
-        SGN_CHECK(rayleigh_ritz<T>(W, adj, Y, rz));
+        SGN_CHECK(svqb<T>(W, Y, q, tmp, eps));
+        SGN_CHECK(svqb<T>(W, Y, q, tmp, eps));
+        SGN_CHECK(rayleigh_ritz<T>(W, adj, true, Y, q, rz));
     }
     for (int it = 0; it < max_it; ++it) {
         double worst = 0;
@@ -292,15 +302,16 @@ int iterate(Work& W, bool adj, T* Y, int want, double tol, int max_it, Ritz& rz,
             *its = it;
             return SGN_OK;
         }
-        const double tw = std::norm(rz.theta[want - 1]);
-        double a = std::norm(rz.theta[W.q - 1]);
+        // Ritz values are eigenvalue estimates of A^2: |theta| ~ |lambda|^2
+        const double tw = std::abs(rz.theta[want - 1]);
+        double a = std::abs(rz.theta[q - 1]);
         a = std::max(a, 1.05 * tw);
         a = std::min(a, 0.9 * b);
         const int deg = degree_for(tw, a, b, sizeof(T) == 16 ? 1e6 : 1e4);
         SGN_CHECK(filter<T>(W, adj, Y, a, b, deg));
-        SGN_CHECK(svqb<T>(W, Y, tmp, eps));
-        SGN_CHECK(svqb<T>(W, Y, tmp, eps));
-        SGN_CHECK(rayleigh_ritz<T>(W, adj, Y, rz));
+        SGN_CHECK(svqb<T>(W, Y, q, tmp, eps));
+        SGN_CHECK(svqb<T>(W, Y, q, tmp, eps));
+        SGN_CHECK(rayleigh_ritz<T>(W, adj, true, Y, q, rz));
     }
     double worst = 0;
     for (int j = 0; j < want; ++j) worst = std::max(worst, rz.res[j]);
@@ -311,43 +322,67 @@ int iterate(Work& W, bool adj, T* Y, int want, double tol, int max_it, Ritz& rz,
     return SGN_ERR_DEFLATION;
 }
 
+// Orthonormalise the `want` fields F (block 4) and run Rayleigh-Ritz with A on
+// them; the eigenvector estimates replace F.  Scratch: blocks 1..3.
+int svqb_final(Work& W, double2* F, int want, bool adj, Ritz& ra) {
+    double2* tmp = reinterpret_cast<double2*>(W.blk[1]);
+    SGN_CHECK(svqb<double2>(W, F, want, tmp, 1e-15));
+    SGN_CHECK(svqb<double2>(W, F, want, tmp, 1e-15));
+    return rayleigh_ritz<double2>(W, adj, false, F, want, ra);
+}
+
 // One side: `want` eigenpairs of A (adj = false) or A^dag (adj = true) into V64 (want fields, FP64).
 int eig_side(sgn_ctx* c, bool adj, int want, int q, double tol, uint64_t seed, double2* V64, std::vector<cd>& lam) {
     cudaStream_t st = c->work;
     Ritz rz;
-    int its32 = 0, its64 = 0;
-    // FP32 phase
-    {
-        Work W;
-        SGN_CHECK(setup(W, c, q, sizeof(float2), reduce_blocks<float2>(c->n)));
-        float2* Y = reinterpret_cast<float2*>(W.blk[0]);
-        SGN_CUDA(random_fill<float2>(Y, (int64_t)q * c->n, seed, st));
-        int rc = iterate<float2>(W, adj, Y, want, std::max(tol, 1e-5), 60, rz, true, &its32);
-        if (rc != SGN_OK) {
-            dev_free(c, W.buf);
-            return rc;
-        }
-        // hand the block over to the FP64 phase through V64's first q fields? V64 holds only `want`
-        // fields, so stage through a fresh FP64 work buffer instead.
-        Work W64;
-        rc = setup(W64, c, q, sizeof(double2), reduce_blocks<double2>(c->n));
-        if (rc != SGN_OK) {
-            dev_free(c, W.buf);
-            return rc;
-        }
-        double2* Y64 = reinterpret_cast<double2*>(W64.blk[0]);
-        SGN_CUDA(convert_f32_to_f64(Y, Y64, (int64_t)q * c->n, st));
-        SGN_CUDA(cudaStreamSynchronize(st));
+    int its = 0;
+    Work W;
+    SGN_CHECK(setup(W, c, q, sizeof(float2), reduce_blocks<float2>(c->n)));
+    float2* Y = reinterpret_cast<float2*>(W.blk[0]);
+    SGN_CUDA(random_fill<float2>(Y, (int64_t)q * c->n, seed, st));
+    // FP32 filter until the A^2 residuals reach 1e-5
+    int rc = iterate<float2>(W, adj, Y, want, std::max(tol, 1e-5), 80, rz, true, &its);
+    if (rc != SGN_OK) {
         dev_free(c, W.buf);
-        rc = iterate<double2>(W64, adj, Y64, want, tol, 20, rz, true, &its64);
-        if (rc == SGN_OK)
-            SGN_CUDA(cudaMemcpyAsync(V64, Y64, sizeof(double2) * want * c->n, cudaMemcpyDeviceToDevice, st));
-        SGN_CUDA(cudaStreamSynchronize(st));
-        dev_free(c, W64.buf);
-        if (rc != SGN_OK) return rc;
+        return rc;
     }
-    lam.assign(rz.theta.begin(), rz.theta.begin() + want);
-    return SGN_OK;
+    Work W64;
+    rc = setup(W64, c, q, sizeof(double2), reduce_blocks<double2>(c->n));
+    if (rc != SGN_OK) {
+        dev_free(c, W.buf);
+        return rc;
+    }
+    double2* Y64 = reinterpret_cast<double2*>(W64.blk[0]);
+    SGN_CUDA(convert_f32_to_f64(Y, Y64, (int64_t)q * c->n, st));
+    SGN_CUDA(cudaStreamSynchronize(st));
+    dev_free(c, W.buf);
+    // FP64: converge the A^2 subspace, then split it with one Rayleigh-Ritz step on A
+    double tol2 = tol / 10;
+    for (int attempt = 0; attempt < 4 && rc == SGN_OK; ++attempt) {
+        rc = iterate<double2>(W64, adj, Y64, want, tol2, 20, rz, attempt == 0, &its);
+        if (rc != SGN_OK) break;
+        double2* F = reinterpret_cast<double2*>(W64.blk[4]);
+        SGN_CUDA(cudaMemcpyAsync(F, Y64, sizeof(double2) * want * c->n, cudaMemcpyDeviceToDevice, st));
+        Ritz ra;
+        rc = svqb_final(W64, F, want, adj, ra);
+        if (rc != SGN_OK) break;
+        double worst = 0;
+        for (int j = 0; j < want; ++j) worst = std::max(worst, ra.res[j]);
+        if (worst <= tol) {
+            SGN_CUDA(cudaMemcpyAsync(V64, F, sizeof(double2) * want * c->n, cudaMemcpyDeviceToDevice, st));
+            SGN_CUDA(cudaStreamSynchronize(st));
+            lam = ra.theta;
+            dev_free(c, W64.buf);
+            return SGN_OK;
+        }
+        tol2 /= 10;
+    }
+    dev_free(c, W64.buf);
+    if (rc == SGN_OK) {
+        set_error("deflation set-up: eigenpairs of A did not reach the tolerance");
+        rc = SGN_ERR_DEFLATION;
+    }
+    return rc;
 }
 
 }  // namespace

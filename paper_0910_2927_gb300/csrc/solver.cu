@@ -590,10 +590,24 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
                 SGN_CUDA(apply_hw64(c, t64, xi, 1, adjoint, nullptr, st));
                 SGN_CUDA(apply_hw64(c, u64, t64, 1, adjoint, nullptr, st));
                 SGN_CUDA(axpby3<double2>(t64, 1.0, bt + (size_t)col * n, -1.0, u64, c->sigma[i], xi, n, st));
-                if (m > 0 && c->project) {  // keep the correction problem in range(I - P)
+                if (m > 0) {
+                    // the range(P) part of the residual is solved exactly in the eigenbasis,
+                    // (A^2 - sigma)^{-1} R = R (Lambda^2 - sigma)^{-1}: x_i += R (Lambda^2 - sigma_i)^{-1} L^dag r_i;
+                    // the Krylov correction then works on (I - P) r_i
                     SGN_CUDA(mdot<double2>(LB, m, t64, n, n, 1, rd64, 0, nullptr, st));
                     SGN_CUDA(reduce(rd64, m, 1, RM_STORE, 0, S64, nullptr, st));
                     SGN_CUDA(maxpy_scale<double2>(RB, m, S64.red, rs64, t64, n, t64, n, nullptr, n, 1, nullptr, st));
+                    std::vector<double2> cp(m);
+                    SGN_CUDA(cudaMemcpyAsync(cp.data(), S64.red, sizeof(double2) * m, cudaMemcpyDeviceToHost, st));
+                    SGN_CUDA(cudaStreamSynchronize(st));
+                    for (int l = 0; l < m; ++l) {
+                        std::complex<double> lj = adjoint ? std::conj(c->lam[l]) : c->lam[l];
+                        std::complex<double> q = std::complex<double>(cp[l].x, cp[l].y) / (lj * lj - c->sigma[i]);
+                        cp[l] = make_double2(q.real(), q.imag());
+                    }
+                    SGN_CUDA(cudaMemcpyAsync(S64.red, cp.data(), sizeof(double2) * m, cudaMemcpyHostToDevice, st));
+                    SGN_CUDA(update_x<double2>(RB, m, S64.red, rs64, xi, n, n, 1, nullptr, nullptr, st));
+                    SGN_CUDA(cudaStreamSynchronize(st));
                 }
                 SGN_CUDA(convert_f64_to_f32(t64, V0 + (size_t)j * n, n, st));
             }

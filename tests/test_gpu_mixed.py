@@ -42,7 +42,7 @@ def test_mixed_matches_oracle(small, links):
         ctx.set_precision(pkg.PREC_MIXED, 1e-8, pkg.LINKS_BF16 if links == "bf16" else pkg.LINKS_FP32)
         x, rep = ctx.apply(torch.from_numpy(b).cuda())
         x = x.cpu().numpy()
-    assert rep["status"] == 0 and rep["err_est"] <= 1e-10
+    assert rep["status"] == 0 and rep["err_est"] <= 1e-10, rep
     for r in range(3):
         xo, _, _ = O.fom_lr(d["dims"], d["U"], b[r], d["mu"], sigma, omega, k=16, tol=1e-12, max_cycles=5000,
                             R=d["R"], L=d["L"], lam=d["lam"])
@@ -64,7 +64,7 @@ def test_mixed_point_sources_config1(lattice4):
         ctx.set_precision(pkg.PREC_MIXED, 1e-8)
         x, rep = ctx.apply(torch.from_numpy(b).cuda())
         x = x.cpu().numpy()
-    assert rep["status"] == 0
+    assert rep["status"] == 0, rep
     for r in (0, 5, 11):
         xo, _, _ = O.fom_lr(d["dims"], d["U"], b[r], d["mu"], sigma, omega, k=30, tol=1e-12, R=d["R"],
                             L=d["L"], lam=d["lam"])
