@@ -22,6 +22,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <numeric>
 
 namespace sgn {
@@ -276,38 +278,65 @@ double spectral_bound2(const sgn_ctx* c) {
     return nb * nb * 1.0001;
 }
 
-int degree_for(double t_want, double a, double b, double amp) {
+int degree_for(double t_want, double a, double b, double amp, int dmax) {
     double sw = std::abs((2 * t_want - b - a) / (b - a));
-    if (!(sw > 1.0 + 1e-12)) return 120;
+    if (!(sw > 1.0 + 1e-12)) return dmax;
     double d = std::acosh(amp) / std::acosh(sw);
     int di = (int)std::ceil(d);
-    return std::min(120, std::max(4, di));
+    return std::min(dmax, std::max(4, di));
 }
 
+bool debug_on() {
+    static const bool on = [] {
+        const char* s = getenv("SGN_DEBUG");
+        return s && s[0] == '1';
+    }();
+    return on;
+}
+
+// Iterate until the wanted Ritz pairs of A^2 reach `tol`, or (stop_on_stall)
+// until the worst residual stops improving: the FP32 phase cannot go below
+// its rounding floor, about eps_32 ||A^2|| / |theta|.
 template <class T>
-int iterate(Work& W, bool adj, T* Y, int want, double tol, int max_it, Ritz& rz, bool fresh, int* its) {
+int iterate(Work& W, bool adj, T* Y, int want, double tol, int max_it, Ritz& rz, bool fresh, bool stop_on_stall,
+            int* its) {
     const int q = W.q;
     const double b = spectral_bound2(W.c);
     T* tmp = reinterpret_cast<T*>(W.blk[1]);
-    const double eps = sizeof(T) == 16 ? 1e-15 : 1e-7;
+    const bool f64 = sizeof(T) == 16;
+    const double eps = f64 ? 1e-15 : 1e-7;
     if (fresh) {
         SGN_CHECK(svqb<T>(W, Y, q, tmp, eps));
         SGN_CHECK(svqb<T>(W, Y, q, tmp, eps));
         SGN_CHECK(rayleigh_ritz<T>(W, adj, true, Y, q, rz));
     }
+    double best = INFINITY;
+    int stall = 0;
     for (int it = 0; it < max_it; ++it) {
         double worst = 0;
         for (int j = 0; j < want; ++j) worst = std::max(worst, rz.res[j]);
+        if (debug_on())
+            fprintf(stderr, "[sgn eig %s %s] it %d worst %.3e theta_want %.4e theta_top %.4e\n", adj ? "left" : "right",
+                    f64 ? "fp64" : "fp32", it, worst, std::abs(rz.theta[want - 1]), std::abs(rz.theta[q - 1]));
         if (worst <= tol) {
             *its = it;
             return SGN_OK;
+        }
+        if (stop_on_stall) {
+            if (worst < 0.5 * best) {
+                best = worst;
+                stall = 0;
+            } else if (++stall >= 2) {
+                *its = it;
+                return SGN_OK;
+            }
         }
         // Ritz values are eigenvalue estimates of A^2: |theta| ~ |lambda|^2
         const double tw = std::abs(rz.theta[want - 1]);
         double a = std::abs(rz.theta[q - 1]);
         a = std::max(a, 1.05 * tw);
         a = std::min(a, 0.9 * b);
-        const int deg = degree_for(tw, a, b, sizeof(T) == 16 ? 1e6 : 1e4);
+        const int deg = degree_for(tw, a, b, f64 ? 1e6 : 1e4, f64 ? 200 : 400);
         SGN_CHECK(filter<T>(W, adj, Y, a, b, deg));
         SGN_CHECK(svqb<T>(W, Y, q, tmp, eps));
         SGN_CHECK(svqb<T>(W, Y, q, tmp, eps));
@@ -316,7 +345,7 @@ int iterate(Work& W, bool adj, T* Y, int want, double tol, int max_it, Ritz& rz,
     double worst = 0;
     for (int j = 0; j < want; ++j) worst = std::max(worst, rz.res[j]);
     *its = max_it;
-    if (worst <= tol) return SGN_OK;
+    if (worst <= tol || stop_on_stall) return SGN_OK;
     set_error("deflation set-up: eigenpairs did not converge (worst relative residual " + std::to_string(worst) +
               ")");
     return SGN_ERR_DEFLATION;
@@ -340,8 +369,8 @@ int eig_side(sgn_ctx* c, bool adj, int want, int q, double tol, uint64_t seed, d
     SGN_CHECK(setup(W, c, q, sizeof(float2), reduce_blocks<float2>(c->n)));
     float2* Y = reinterpret_cast<float2*>(W.blk[0]);
     SGN_CUDA(random_fill<float2>(Y, (int64_t)q * c->n, seed, st));
-    // FP32 filter until the A^2 residuals reach 1e-5
-    int rc = iterate<float2>(W, adj, Y, want, std::max(tol, 1e-5), 80, rz, true, &its);
+    // FP32 filter until the A^2 residuals reach their FP32 floor (or tol)
+    int rc = iterate<float2>(W, adj, Y, want, std::max(tol, 1e-6), 80, rz, true, true, &its);
     if (rc != SGN_OK) {
         dev_free(c, W.buf);
         return rc;
@@ -359,7 +388,7 @@ int eig_side(sgn_ctx* c, bool adj, int want, int q, double tol, uint64_t seed, d
     // FP64: converge the A^2 subspace, then split it with one Rayleigh-Ritz step on A
     double tol2 = tol / 10;
     for (int attempt = 0; attempt < 4 && rc == SGN_OK; ++attempt) {
-        rc = iterate<double2>(W64, adj, Y64, want, tol2, 20, rz, attempt == 0, &its);
+        rc = iterate<double2>(W64, adj, Y64, want, tol2, 30, rz, attempt == 0, false, &its);
         if (rc != SGN_OK) break;
         double2* F = reinterpret_cast<double2*>(W64.blk[4]);
         SGN_CUDA(cudaMemcpyAsync(F, Y64, sizeof(double2) * want * c->n, cudaMemcpyDeviceToDevice, st));
@@ -390,7 +419,7 @@ int eig_side(sgn_ctx* c, bool adj, int want, int q, double tol, uint64_t seed, d
 int build_deflation(sgn_ctx* c, int m, int extra, double eig_tol, double* lambda_out) {
     cudaStream_t st = c->work;
     const int want = m + extra;
-    const int q = std::min(71, want + std::max(8, want / 3));
+    const int q = std::min(71, want + std::max(12, want / 2));
     const int64_t n = c->n;
     DevBuf RL;
     SGN_CHECK(dev_alloc(c, RL, sizeof(double2) * (size_t)n * (2 * want + m)));
