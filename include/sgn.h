@@ -70,6 +70,8 @@ typedef enum { SGN_LINKS_FP32 = 0, SGN_LINKS_BF16 = 1 } sgn_link_storage;
 /* Flags of sgn_apply. */
 #define SGN_APPLY_HOST_BUFFERS 1  /* b and x are host pointers (copied inside the call) */
 #define SGN_APPLY_ADJOINT 2       /* apply sign(H_W(-mu)) = sign(H_W(mu))^dag instead */
+#define SGN_APPLY_NO_A 4          /* right-hand side of the shifted systems is (I - P) b, not A (I - P) b:
+                                     x_shift[i] ~ (A^2 - sigma_i)^{-1} (I - P) b (used by the gradient) */
 
 typedef void* (*sgn_alloc_fn)(size_t bytes, void* user);
 typedef void (*sgn_free_fn)(void* ptr, size_t bytes, void* user);
@@ -183,6 +185,30 @@ SGN_API int sgn_apply_shifts(sgn_ctx* ctx, const double* b, double* x, double* x
  * complex64 fields with the FP32 (or BF16, see sgn_set_precision) links.
  * Device pointers; in and out must not overlap. */
 SGN_API int sgn_hw_apply(sgn_ctx* ctx, const void* in, void* out, int nrhs, int precision, int adjoint);
+
+/* Inner products out[c*J + j] = <V_j, w_c> = V_j^dag w_c of J fields V (one basis
+ * shared by every column) with nrhs fields w -- the coefficients of classical
+ * Gram-Schmidt (V^dag w, eq. (2.4)) and of the projection step (L^dag r, eq. (4.5)).
+ * V: J complex128 device fields back to back; w: nrhs complex128 device fields;
+ * out: host array of nrhs*J complex128.  1 <= J <= 64.  FP64 accumulation in a
+ * fixed order (deterministic).  Scratch for the per-block partial sums comes from
+ * the context's allocator and is kept for later calls. */
+SGN_API int sgn_inner_products(sgn_ctx* ctx, const double* V, int J, const double* w, int nrhs, double* out);
+
+/* dH_W/dmu applied to nrhs complex128 device fields: out = gamma5 dD_W/dmu in,
+ * dD_W/dmu psi(x) = -1/2 [(1 - gamma_t) e^{+mu} U_t(x) psi(x+t) - (1 + gamma_t) e^{-mu} U_t(x-t)^dag psi(x-t)]
+ * (only the time hops of D_W(mu) depend on mu, Sec. 1). */
+SGN_API int sgn_dhw_dmu_apply(sgn_ctx* ctx, const double* in, double* out, int nrhs);
+
+/* Derivative of the loss Re<g, x(mu)> with x = sum_i omega_i A (A^2 - sigma_i)^{-1} b
+ * (no deflation, m = 0) with respect to mu, per column:
+ *   dmu[c] = Re sum_i omega_i < z_i, A' b - A' A x_i - A A' x_i >,
+ *   x_i = (A^2 - sigma_i)^{-1} A b,  z_i = (A^dag^2 - sigma_i)^{-1} g,  A' = dH_W/dmu,
+ * from one forward and one adjoint multishift solve (per-shift iterates kept).
+ * b, g: nrhs complex128 device fields; dmu: host array of nrhs doubles.
+ * Errors: SGN_ERR_STATE if deflation data is set (the eigenvector-motion terms
+ * of the deflated function are not part of this entry point). */
+SGN_API int sgn_grad_mu(sgn_ctx* ctx, const double* b, const double* g, int nrhs, double* dmu);
 
 /* Thread-local message for the last failing call of this thread. */
 SGN_API const char* sgn_last_error(void);

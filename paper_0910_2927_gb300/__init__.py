@@ -218,6 +218,16 @@ class SignContext:
             check(code)
         return (x.reshape(-1) if squeeze else x), rep.as_dict()
 
+    def inner_products(self, V, w):
+        """<V_j, w_c> for J CUDA fields V (J, n) and nrhs CUDA fields w (nrhs, n): shape (nrhs, J)."""
+        torch = _torch()
+        Vc = V.reshape(-1, self.n).to(torch.complex128).contiguous()
+        wc = w.reshape(-1, self.n).to(torch.complex128).contiguous()
+        out = np.empty((wc.shape[0], Vc.shape[0]), dtype=np.complex128)
+        check(lib().sgn_inner_products(self._h, C.c_void_p(Vc.data_ptr()), Vc.shape[0], C.c_void_p(wc.data_ptr()),
+                                       wc.shape[0], out.ctypes.data))
+        return out
+
     def hw(self, psi, precision=PREC_FP64, adjoint=False):
         """H_W(mu) psi (or H_W(-mu) psi) for CUDA fields of shape (nrhs, n) or (n,)."""
         torch = _torch()

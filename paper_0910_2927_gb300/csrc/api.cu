@@ -108,6 +108,7 @@ SGN_API int sgn_destroy(sgn_ctx* c) {
     dev_free(c, c->lamc_dev);
     dev_free(c, c->io);
     dev_free(c, c->stage);
+    dev_free(c, c->ip_scratch);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
@@ -303,7 +304,8 @@ int apply_common(sgn_ctx* c, const double* b, double* x, double* x_shift, int nr
         bd = sb;
         xd = sb + (size_t)c->n * nrhs;
     }
-    int status = solve(c, bd, xd, reinterpret_cast<double2*>(x_shift), nrhs, adjoint, rep);
+    const bool no_a = flags & SGN_APPLY_NO_A;
+    int status = solve(c, bd, xd, reinterpret_cast<double2*>(x_shift), nrhs, adjoint, no_a, rep);
     if (host && (status == SGN_OK || status == SGN_ERR_NOT_CONVERGED))
         SGN_CUDA(cudaMemcpyAsync(x, xd, fbytes, cudaMemcpyDeviceToHost, c->work));
     SGN_CUDA(cudaEventRecord(c->ev_t1, c->work));
@@ -345,5 +347,58 @@ SGN_API int sgn_hw_apply(sgn_ctx* c, const void* in, void* out, int nrhs, int pr
         return fail(SGN_ERR_ARG, "sgn_hw_apply: unknown precision");
     }
     SGN_CHECK(leave(c));
+    return SGN_OK;
+}
+
+SGN_API int sgn_dhw_dmu_apply(sgn_ctx* c, const double* in, double* out, int nrhs) {
+    if (!c || !in || !out || nrhs < 1) return fail(SGN_ERR_ARG, "sgn_dhw_dmu_apply: bad argument");
+    if (in == out) return fail(SGN_ERR_ARG, "sgn_dhw_dmu_apply: in and out must differ");
+    if (!c->have_gauge) return fail(SGN_ERR_STATE, "sgn_dhw_dmu_apply: load the gauge field first");
+    SGN_CHECK(enter(c));
+    SGN_CUDA(apply_dhw_dmu64(c, reinterpret_cast<double2*>(out), reinterpret_cast<const double2*>(in), nrhs, c->work));
+    SGN_CHECK(leave(c));
+    return SGN_OK;
+}
+
+SGN_API int sgn_grad_mu(sgn_ctx* c, const double* b, const double* g, int nrhs, double* dmu) {
+    if (!c || !b || !g || !dmu || nrhs < 1) return fail(SGN_ERR_ARG, "sgn_grad_mu: bad argument");
+    if (!c->have_gauge || c->sigma.empty()) return fail(SGN_ERR_STATE, "sgn_grad_mu: gauge field and rational function needed");
+    if (c->m > 0) return fail(SGN_ERR_STATE, "sgn_grad_mu: defined for the undeflated function (m = 0) only");
+    SGN_CHECK(enter(c));
+    int st = grad_mu(c, reinterpret_cast<const double2*>(b), reinterpret_cast<const double2*>(g), nrhs, dmu);
+    SGN_CHECK(leave(c));
+    return st;
+}
+
+SGN_API int sgn_inner_products(sgn_ctx* c, const double* V, int J, const double* w, int nrhs, double* out) {
+    if (!c || !V || !w || !out || J < 1 || J > 64 || nrhs < 1)
+        return fail(SGN_ERR_ARG, "sgn_inner_products: need 1 <= J <= 64, nrhs >= 1 and non-NULL pointers");
+    SGN_CHECK(enter(c));
+    const int64_t n = c->n;
+    const int nblk = reduce_blocks<double2>(n);
+    const int rs = (J + 8) & ~7;
+    const size_t pbytes = (sizeof(double2) * (size_t)nrhs * rs * nblk + 255) & ~size_t(255);
+    const size_t rbytes = (sizeof(double2) * (size_t)nrhs * rs + 255) & ~size_t(255);
+    SGN_CHECK(dev_alloc(c, c->ip_scratch, pbytes + rbytes + sizeof(int) * 2 * nrhs));
+    char* p = reinterpret_cast<char*>(c->ip_scratch.p);
+    DevState S{};
+    S.red = reinterpret_cast<double2*>(p + pbytes);
+    S.skip = reinterpret_cast<int*>(p + pbytes + rbytes);
+    S.done = S.skip + nrhs;
+    S.rstride = rs;
+    SGN_CUDA(cudaMemsetAsync(S.skip, 0, sizeof(int) * 2 * nrhs, c->work));
+    const Reduce rd{reinterpret_cast<double2*>(p), nblk, rs};
+    SGN_CUDA(mdot<double2>(Basis<double2>{reinterpret_cast<const double2*>(V), n, 0}, J,
+                           reinterpret_cast<const double2*>(w), n, n, nrhs, rd, 0, nullptr, c->work));
+    SGN_CUDA(reduce(rd, J, nrhs, RM_STORE, 0, S, nullptr, c->work));
+    std::vector<double2> h((size_t)nrhs * rs);
+    SGN_CUDA(cudaMemcpyAsync(h.data(), S.red, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost, c->work));
+    SGN_CUDA(cudaStreamSynchronize(c->work));
+    SGN_CHECK(leave(c));
+    for (int col = 0; col < nrhs; ++col)
+        for (int j = 0; j < J; ++j) {
+            out[2 * ((size_t)col * J + j)] = h[(size_t)col * rs + j].x;
+            out[2 * ((size_t)col * J + j) + 1] = h[(size_t)col * rs + j].y;
+        }
     return SGN_OK;
 }

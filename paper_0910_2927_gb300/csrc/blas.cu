@@ -17,7 +17,7 @@ namespace {
 constexpr int NT = 256;
 constexpr int NWARP = NT / 32;
 constexpr int PK = 4;
-constexpr int MAXSLOT = 72;  // >= kmax + 2 and >= deflation size + 1
+constexpr int MAXSLOT = 104;  // >= kmax + 2, >= deflation size + 1, >= eigensolver block + 1
 
 template <class T>
 struct Ops;
@@ -536,7 +536,7 @@ template <class T>
 __global__ void __launch_bounds__(NT) k_block_combine(const T* __restrict__ Y, int q, const double2* __restrict__ Cm,
                                                       int r, T* __restrict__ Z, int64_t n, int64_t npk) {
     using O = Ops<T>;
-    __shared__ typename O::C cs[72 * SG];
+    __shared__ typename O::C cs[MAXSLOT * SG];
     const int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
     for (int g0 = 0; g0 < r; g0 += SG) {
         const int ng = (r - g0) < SG ? (r - g0) : SG;
@@ -695,7 +695,7 @@ cudaError_t axpby3(T* out, double a, const T* x, double b, const T* y, double c,
 
 template <class T>
 cudaError_t block_combine(const T* Y, int q, const double2* Cm, int r, T* Z, int64_t n, cudaStream_t st) {
-    if (q > 72 || r < 1) return cudaErrorInvalidValue;
+    if (q > MAXSLOT || r < 1) return cudaErrorInvalidValue;
     int64_t npk = n / Ops<T>::CPX;
     k_block_combine<T><<<(unsigned)((npk + NT - 1) / NT), NT, 0, st>>>(Y, q, Cm, r, Z, n, npk);
     count_launch();

@@ -92,6 +92,7 @@ struct sgn_ctx {
     // scratch fields for apply (b copy, x accumulators, FP64 temporaries)
     sgn::DevBuf io;
     sgn::DevBuf stage;  // device staging of host b / x
+    sgn::DevBuf ip_scratch;  // partial sums of sgn_inner_products
     size_t io_bytes = 0;
     double2* h_pinned = nullptr;
     size_t h_pinned_bytes = 0;
@@ -106,8 +107,14 @@ cudaError_t apply_hw64(const sgn_ctx* c, double2* out, const double2* in, int nc
 cudaError_t apply_hw32(const sgn_ctx* c, float2* out, const float2* in, int ncol, bool adjoint, const int* skip,
                        cudaStream_t st);
 
-int solve(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int ncol, bool adjoint, sgn_report* rep);
+int solve(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int ncol, bool adjoint, bool no_a,
+          sgn_report* rep);
+// Dot products <a_c, b_c> of ncol pairs of FP64 fields (host result, FP64 reductions).
+int field_dots(sgn_ctx* c, const double2* a, const double2* b, int ncol, std::vector<std::complex<double>>& out);
 int build_deflation(sgn_ctx* c, int m, int extra, double eig_tol, double* lambda_out);
+// dH_W/dmu on ncol FP64 fields, and the mu-derivative of Re<g, x> (grad.cu).
+cudaError_t apply_dhw_dmu64(const sgn_ctx* c, double2* out, const double2* in, int ncol, cudaStream_t st);
+int grad_mu(sgn_ctx* c, const double2* b, const double2* g, int ncol, double* dmu);
 void release_engines(sgn_ctx* c);
 
 }  // namespace sgn

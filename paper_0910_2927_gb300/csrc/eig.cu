@@ -62,7 +62,7 @@ int setup(Work& W, sgn_ctx* c, int q, size_t esz, int nblk) {
     W.q = q;
     W.n = c->n;
     W.nblk = nblk;
-    W.rstride = 80;
+    W.rstride = 104;
     const size_t blkb = (size_t)q * c->n * esz;
     size_t off = 0;
     auto take = [&](size_t b) {
@@ -127,7 +127,7 @@ int combine(Work& W, const T* Y, int q, const std::vector<cd>& Cm, int r, T* Z) 
 // G = Y^dag Y, D = diag(G)^{-1/2}, D G D = V diag(l) V^dag, Y <- Y D V diag(l)^{-1/2}
 // with l floored at eps * max(l) so that dependent columns do not blow up.
 template <class T>
-int svqb(Work& W, T* Y, int q, T* tmp, double eps) {
+int svqb(Work& W, T* Y, int q, T* tmp, double eps, int* deficient = nullptr) {
     std::vector<cd> G;
     SGN_CHECK(gram<T>(W, Y, q, Y, q, G));
     std::vector<double> d(q);
@@ -152,13 +152,23 @@ int svqb(Work& W, T* Y, int q, T* tmp, double eps) {
     double lmax = 0;
     for (double l : w) lmax = std::max(lmax, l);
     std::vector<cd> Cm((size_t)q * q);
+    std::vector<int> bad;
     for (int j = 0; j < q; ++j) {
-        double l = std::max(w[j], eps * lmax);
+        double l = w[j];
+        if (!(l > eps * lmax)) {
+            bad.push_back(j);
+            l = lmax;  // the column is replaced below
+        }
         double sc = 1.0 / std::sqrt(l);
         for (int i = 0; i < q; ++i) Cm[(size_t)i * q + j] = d[i] * V[(size_t)i * q + j] * sc;
     }
     SGN_CHECK(combine<T>(W, Y, q, Cm, q, tmp));
     SGN_CUDA(cudaMemcpyAsync(Y, tmp, sizeof(T) * q * W.n, cudaMemcpyDeviceToDevice, W.c->work));
+    // numerically dependent directions carry no information: refill them with fresh
+    // random fields, which the next orthonormalisation pass makes orthogonal
+    static uint64_t refill_seed = 0x9a11ULL;
+    for (int j : bad) SGN_CUDA(random_fill<T>(Y + (size_t)j * W.n, W.n, ++refill_seed, W.c->work));
+    if (deficient) *deficient = (int)bad.size();
     return SGN_OK;
 }
 
@@ -304,7 +314,9 @@ int iterate(Work& W, bool adj, T* Y, int want, double tol, int max_it, Ritz& rz,
     const double b = spectral_bound2(W.c);
     T* tmp = reinterpret_cast<T*>(W.blk[1]);
     const bool f64 = sizeof(T) == 16;
-    const double eps = f64 ? 1e-15 : 1e-7;
+    // Gram eigenvalues below eps * max are unresolved (FP64 Gram of FP64 data to
+    // ~1e-16; of FP32 data, with FP32 chunk products, to ~1e-7)
+    const double eps = f64 ? 1e-14 : 1e-7;
     if (fresh) {
         SGN_CHECK(svqb<T>(W, Y, q, tmp, eps));
         SGN_CHECK(svqb<T>(W, Y, q, tmp, eps));
@@ -316,8 +328,9 @@ int iterate(Work& W, bool adj, T* Y, int want, double tol, int max_it, Ritz& rz,
         double worst = 0;
         for (int j = 0; j < want; ++j) worst = std::max(worst, rz.res[j]);
         if (debug_on())
-            fprintf(stderr, "[sgn eig %s %s] it %d worst %.3e theta_want %.4e theta_top %.4e\n", adj ? "left" : "right",
-                    f64 ? "fp64" : "fp32", it, worst, std::abs(rz.theta[want - 1]), std::abs(rz.theta[q - 1]));
+            fprintf(stderr, "[sgn eig %s %s] it %d worst %.3e theta_min %.4e theta_want %.4e theta_top %.4e\n",
+                    adj ? "left" : "right", f64 ? "fp64" : "fp32", it, worst, std::abs(rz.theta[0]),
+                    std::abs(rz.theta[want - 1]), std::abs(rz.theta[q - 1]));
         if (worst <= tol) {
             *its = it;
             return SGN_OK;
@@ -331,15 +344,26 @@ int iterate(Work& W, bool adj, T* Y, int want, double tol, int max_it, Ritz& rz,
                 return SGN_OK;
             }
         }
-        // Ritz values are eigenvalue estimates of A^2: |theta| ~ |lambda|^2
+        // Ritz values are eigenvalue estimates of A^2: |theta| ~ |lambda|^2.  The
+        // degree aims at an amplification of the wanted edge tw, capped so that the
+        // most amplified direction (the smallest Ritz value) outgrows the top of the
+        // block by less than the storage precision can resolve.
         const double tw = std::abs(rz.theta[want - 1]);
+        const double tmin = std::abs(rz.theta[0]);
         double a = std::abs(rz.theta[q - 1]);
-        a = std::max(a, 1.05 * tw);
+        a = std::max(a, 1.02 * tw);
         a = std::min(a, 0.9 * b);
-        const int deg = degree_for(tw, a, b, f64 ? 1e6 : 1e4, f64 ? 200 : 400);
+        const int dmax = f64 ? 400 : 800;
+        const double amp = f64 ? 1e6 : 1e3;  // squared stays inside the Gram resolution above
+        const int d_conv = degree_for(tw, a, b, amp, dmax);
+        const int d_safe = degree_for(tmin, a, b, amp, dmax);
+        const int deg = std::max(4, std::min(d_conv, d_safe));
         SGN_CHECK(filter<T>(W, adj, Y, a, b, deg));
+        int bad = 0;
+        SGN_CHECK(svqb<T>(W, Y, q, tmp, eps, &bad));
         SGN_CHECK(svqb<T>(W, Y, q, tmp, eps));
-        SGN_CHECK(svqb<T>(W, Y, q, tmp, eps));
+        if (bad) SGN_CHECK(svqb<T>(W, Y, q, tmp, eps));
+        if (debug_on() && bad) fprintf(stderr, "[sgn eig] refilled %d dependent directions\n", bad);
         SGN_CHECK(rayleigh_ritz<T>(W, adj, true, Y, q, rz));
     }
     double worst = 0;
@@ -419,7 +443,7 @@ int eig_side(sgn_ctx* c, bool adj, int want, int q, double tol, uint64_t seed, d
 int build_deflation(sgn_ctx* c, int m, int extra, double eig_tol, double* lambda_out) {
     cudaStream_t st = c->work;
     const int want = m + extra;
-    const int q = std::min(71, want + std::max(12, want / 2));
+    const int q = std::min(100, want + std::max(12, want / 2));
     const int64_t n = c->n;
     DevBuf RL;
     SGN_CHECK(dev_alloc(c, RL, sizeof(double2) * (size_t)n * (2 * want + m)));

@@ -426,7 +426,7 @@ namespace {
 // until every true residual meets the tolerance that stops the FP64 form.
 constexpr size_t kRefineBudgetBytes = size_t(48) << 30;
 
-int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int ncol, bool adjoint,
+int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int ncol, bool adjoint, bool no_a,
                 sgn_report* rep) {
     cudaStream_t st = c->work;
     const int64_t n = c->n;
@@ -507,7 +507,10 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
         SGN_CUDA(maxpy_scale<double2>(RB, m, S64.red, rs64, b, n, r0, n, nullptr, n, ncol, nullptr, st));
         rstart = r0;
     }
-    SGN_CUDA(apply_hw64(c, bt, rstart, ncol, adjoint, nullptr, st));  // b~ in FP64
+    if (no_a)
+        SGN_CUDA(cudaMemcpyAsync(bt, rstart, field * ncol, cudaMemcpyDeviceToDevice, st));
+    else
+        SGN_CUDA(apply_hw64(c, bt, rstart, ncol, adjoint, nullptr, st));  // b~ in FP64
     SGN_CUDA(convert_f64_to_f32(bt, reinterpret_cast<float2*>(E->V), (int64_t)ncol * n, st));
 
     CycleArgs a;
@@ -649,13 +652,14 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
 }  // namespace
 
 // x = x_P + sum_i omega_i x_i on ncol device fields (FP64).  See sgn_apply.
-int solve(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int ncol, bool adjoint, sgn_report* rep) {
+int solve(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int ncol, bool adjoint, bool no_a,
+          sgn_report* rep) {
     cudaStream_t st = c->work;
     const int64_t n = c->n;
     const int s = (int)c->sigma.size();
     const int k = c->k;
     const int m = c->m;
-    if (c->precision == SGN_PREC_MIXED) return solve_mixed(c, b, x, x_shift, ncol, adjoint, rep);
+    if (c->precision == SGN_PREC_MIXED) return solve_mixed(c, b, x, x_shift, ncol, adjoint, no_a, rep);
     Engine* E = nullptr;
     SGN_CHECK(get_engine(c, ncol, k, s, c->precision, &E));
     // io: xacc (ncol n) | r0 (ncol n) | xs (s ncol n, optional)
@@ -696,7 +700,10 @@ int solve(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int ncol, 
         rstart = r0;
     }
     // b~ = A (I - P) b is the first restart vector (A^2 reading of eq. (6.2))
-    SGN_CUDA(apply_hw64(c, reinterpret_cast<double2*>(E->V), rstart, ncol, adjoint, nullptr, st));
+    if (no_a)
+        SGN_CUDA(cudaMemcpyAsync(E->V, rstart, field * ncol, cudaMemcpyDeviceToDevice, st));
+    else
+        SGN_CUDA(apply_hw64(c, reinterpret_cast<double2*>(E->V), rstart, ncol, adjoint, nullptr, st));
 
     CycleArgs a;
     a.adjoint = adjoint;
@@ -732,6 +739,33 @@ int solve(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int ncol, 
         rep->breakdown = bd;
     }
     return status;
+}
+
+int field_dots(sgn_ctx* c, const double2* a, const double2* b, int ncol, std::vector<std::complex<double>>& out) {
+    cudaStream_t st = c->work;
+    const int64_t n = c->n;
+    const int nblk = reduce_blocks<double2>(n);
+    const int rs = 8;
+    DevBuf buf;
+    const size_t pbytes = align256(sizeof(double2) * (size_t)ncol * rs * nblk);
+    SGN_CHECK(dev_alloc(c, buf, pbytes + align256(sizeof(double2) * ncol * rs) + align256(sizeof(int) * 2 * ncol)));
+    char* p = reinterpret_cast<char*>(buf.p);
+    DevState S{};
+    S.red = reinterpret_cast<double2*>(p + pbytes);
+    S.skip = reinterpret_cast<int*>(p + pbytes + align256(sizeof(double2) * ncol * rs));
+    S.done = S.skip + ncol;
+    S.rstride = rs;
+    SGN_CUDA(cudaMemsetAsync(S.skip, 0, sizeof(int) * 2 * ncol, st));
+    const Reduce rd{reinterpret_cast<double2*>(p), nblk, rs};
+    SGN_CUDA(mdot<double2>(Basis<double2>{a, 0, n}, 1, b, n, n, ncol, rd, 0, nullptr, st));
+    SGN_CUDA(reduce(rd, 1, ncol, RM_STORE, 0, S, nullptr, st));
+    std::vector<double2> h((size_t)ncol * rs);
+    SGN_CUDA(cudaMemcpyAsync(h.data(), S.red, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost, st));
+    SGN_CUDA(cudaStreamSynchronize(st));
+    dev_free(c, buf);
+    out.resize(ncol);
+    for (int i = 0; i < ncol; ++i) out[i] = {h[(size_t)i * rs].x, h[(size_t)i * rs].y};
+    return SGN_OK;
 }
 
 }  // namespace sgn

@@ -1,0 +1,99 @@
+"""Gradients of Re<c, sign(H_W(mu)) b> (SignApply): b-gradient by the adjoint solve,
+mu-gradient by per-shift forward and adjoint iterates (undeflated function).
+
+Checked against the oracle's dense Daleckii-Krein derivative on a small lattice
+and central finite differences of the oracle with step 1e-4 at 6^4 (mu = 0.5)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import seeded_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _ctx(dims, U, mu, sigma, omega, k=20, tol=1e-13):
+    import paper_0910_2927_gb300 as pkg
+    ctx = pkg.SignContext(dims, mu=mu)
+    ctx.load_gauge(torch.from_numpy(U).cuda())
+    ctx.set_rational(sigma, omega)
+    ctx.set_restart(k=k, tol=tol, max_cycles=5000)
+    return ctx
+
+
+def test_dhw_dmu_matches_central_difference():
+    from paper_0910_2927_gb300.autograd import dhw_dmu
+    dims, mu, h = (3, 2, 3, 4), 0.4, 1e-5
+    U = si.random_su3_links(dims, 0.7, 51)
+    v = si.gaussian_field(dims, 52)
+    fd = (O.hw(dims, U, v, mu + h) - O.hw(dims, U, v, mu - h)) / (2 * h)
+    sigma, omega = O.kenney_laub(4, 0.5)
+    with _ctx(dims, U, mu, sigma, omega) as ctx:
+        got = dhw_dmu(ctx, torch.from_numpy(v).cuda()).cpu().numpy()
+    assert np.linalg.norm(got - fd) < 1e-8 * np.linalg.norm(fd)
+
+
+def test_gradients_match_dense_daleckii_krein():
+    """Dense reference: A = X diag(l) X^{-1}, F(A) = X f(l) X^{-1} with f(t) = t sum omega/(t^2 - sigma);
+    dF[E] = X (F^ o (X^{-1} E X)) X^{-1}, F^_jk = divided differences of f."""
+    from paper_0910_2927_gb300.autograd import SignApply
+    dims, mu = (3, 2, 3, 4), 0.5
+    U = si.random_su3_links(dims, 0.7, 53)
+    b = si.gaussian_field(dims, 54)
+    c = si.gaussian_field(dims, 55)
+    sigma, omega = O.kenney_laub(12, 0.4)
+    A = O.dense_hw(dims, U, mu)
+    h = 1e-6
+    Ad = (O.dense_hw(dims, U, mu + h) - O.dense_hw(dims, U, mu - h)) / (2 * h)   # A' (linear in e^{+-mu})
+    w, X, Xi = O.eig(A)
+    f = lambda t: t * np.sum(omega[None, :] / (t[:, None] ** 2 - sigma[None, :]), axis=1)
+    fp = lambda t: np.sum(omega[None, :] * (-(t[:, None] ** 2) - sigma[None, :]) / (t[:, None] ** 2 - sigma[None, :]) ** 2, axis=1)
+    fw = f(w)
+    D = w[:, None] - w[None, :]
+    same = np.abs(D) < 1e-12
+    Fh = np.where(same, 0, (fw[:, None] - fw[None, :]) / np.where(same, 1, D))
+    Fh[np.arange(len(w)), np.arange(len(w))] = fp(w)
+    dF = X @ (Fh * (Xi @ Ad @ X)) @ Xi
+    dmu_ref = np.real(np.vdot(c, dF @ b))
+    gb_ref = (X @ (fw[:, None] * Xi)).conj().T @ c
+    bt = torch.from_numpy(b).cuda().requires_grad_(True)
+    mut = torch.tensor(mu, dtype=torch.float64, requires_grad=True)
+    with _ctx(dims, U, mu, sigma, omega) as ctx:
+        x = SignApply.apply(bt, mut, ctx)
+        loss = torch.vdot(torch.from_numpy(c).cuda(), x).real
+        loss.backward()
+    gb = bt.grad.cpu().numpy()
+    assert np.linalg.norm(gb - gb_ref) < 1e-9 * np.linalg.norm(gb_ref)
+    assert abs(float(mut.grad) - dmu_ref) < 1e-7 * max(1.0, abs(dmu_ref))
+
+
+def test_config4_finite_differences():
+    """6^4, mu = 0.5: d/dmu Re<c, x> against central differences of the oracle, h = 1e-4."""
+    from paper_0910_2927_gb300.autograd import SignApply
+    dims, mu, h = (6, 6, 6, 6), 0.5, 1e-4
+    g_seed, b_seed, c_seed = si.CONFIG_SEEDS[4]
+    U = si.random_su3_links(dims, 0.7, g_seed)
+    b = si.gaussian_field(dims, b_seed)
+    c = si.gaussian_field(dims, c_seed)
+    sigma, omega = O.kenney_laub(20, 0.3)
+    def loss_oracle(m):
+        x, rep, _ = O.fom_lr(dims, U, b, m, sigma, omega, k=40, tol=1e-12, max_cycles=3000)
+        assert rep["converged"]
+        return np.real(np.vdot(c, x))
+    fd = (loss_oracle(mu + h) - loss_oracle(mu - h)) / (2 * h)
+    bt = torch.from_numpy(b).cuda().requires_grad_(True)
+    mut = torch.tensor(mu, dtype=torch.float64, requires_grad=True)
+    with _ctx(dims, U, mu, sigma, omega, k=40, tol=1e-12) as ctx:
+        x = SignApply.apply(bt, mut, ctx)
+        loss = torch.vdot(torch.from_numpy(c).cuda(), x).real
+        loss.backward()
+        # b-gradient: directional derivative along a random direction against the oracle
+        d = si.gaussian_field(dims, 99)
+    xo_p, _, _ = O.fom_lr(dims, U, b + 1e-3 * d, mu, sigma, omega, k=40, tol=1e-12, max_cycles=3000)
+    xo_m, _, _ = O.fom_lr(dims, U, b - 1e-3 * d, mu, sigma, omega, k=40, tol=1e-12, max_cycles=3000)
+    dir_fd = np.real(np.vdot(c, xo_p - xo_m)) / 2e-3
+    dir_ad = np.real(np.vdot(bt.grad.cpu().numpy(), d))
+    assert abs(float(mut.grad) - fd) < 1e-5 * max(1.0, abs(fd))
+    assert abs(dir_ad - dir_fd) < 1e-5 * max(1.0, abs(dir_fd))

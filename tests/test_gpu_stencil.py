@@ -65,3 +65,15 @@ def test_stencil_skips_nothing_on_many_fields():
     for r in range(16):
         ref = O.hw(dims, U, b[r], mu)
         np.testing.assert_allclose(out[r], ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+
+
+def test_inner_products_match_numpy():
+    """sgn_inner_products (Gram-Schmidt / projection coefficients) against numpy in FP64."""
+    dims = (3, 4, 5, 6)
+    U = si.random_su3_links(dims, 0.7, 17)
+    V = si.gaussian_block(dims, 9, 18)
+    w = si.gaussian_block(dims, 3, 19)
+    with _ctx(dims, U, 0.3) as ctx:
+        got = ctx.inner_products(torch.from_numpy(V).cuda(), torch.from_numpy(w).cuda())
+    ref = w @ V.conj().T
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
