@@ -3,14 +3,16 @@
 
 One step = one application of the deflated rational sign approximation
 (restarted FOM-LR, Algorithm 1) to every right-hand side of the workload,
-with the inputs already resident in HBM.  Default workload: 24^4 lattice,
-random SU(3) links (spread 0.7), mu = 0.2, 12 spin-colour point sources,
-s = 20 Kenney-Laub poles, restart length k = 40, m = 40 deflated eigenpairs,
-mixed form (FP32 stencil and basis, FP64 scalars, refinement on the true
-FP64 residual).  The plain FP64 form is timed beside it.
+with the inputs already resident in HBM.  Default workload: 10^4 lattice,
+random SU(3) links (spread 0.7), mu = 0.3, 12 spin-colour point sources in one
+batched solve, s = 20 Kenney-Laub poles, restart length k = 40, m = 30
+deflated eigenpairs, mixed form (FP32 stencil and basis, FP64 scalars,
+refinement on the true FP64 residual).  The plain FP64 form is timed beside
+it, and the 12-column FP32 stencil is timed on a 24^4 lattice, where its
+working set is far larger than L2, for its HBM bandwidth.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload 24^4|10^4|8^4|4^4]
+                       [--workload 10^4|24^4|16^4|8^4|4^4]
 N > 1 runs under torchrun as independent replicas (one workload per GPU, no
 collective on the data path; weak scaling).
 """
@@ -275,10 +277,14 @@ def run_ours(args, w, name):
         t64 = e0.elapsed_time(e1) / 1000.0
         fp64_value = nrhs / t64
 
-    # ---- mixed form (the headline)
+    # ---- mixed form (the headline); per-kernel CUDA events inside the captured cycles
+    import ctypes as C
+    lib = pkg.lib()
     ctx.set_precision(pkg.PREC_MIXED, 1e-8, pkg.LINKS_FP32)
+    lib.sgn_set_kernel_timing(ctx._h, 1)
     for _ in range(args.warmup):
         xm, repm = ctx.apply(bdev)
+    lib.sgn_set_kernel_timing(ctx._h, 1)   # reset the totals: only the timed steps count
     torch.cuda.synchronize()
     D.barrier()
     torch.cuda.synchronize()
@@ -295,6 +301,12 @@ def run_ours(args, w, name):
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
     t_mixed = e0.elapsed_time(e1) / 1000.0
+    kt = {}
+    for cls, name_k in ((0, "k_hw<float,float2>"), (1, "k_dcgs_dots<float2>"), (2, "k_dcgs_update<float2>")):
+        ms, nl, by = C.c_double(), C.c_longlong(), C.c_double()
+        lib.sgn_get_kernel_timing(ctx._h, cls, C.byref(ms), C.byref(nl), C.byref(by))
+        kt[name_k] = {"ms": ms.value, "launches": nl.value, "bytes": by.value}
+    lib.sgn_set_kernel_timing(ctx._h, 0)
     D.barrier()
     t_max = D.max(t_mixed)
     units = D.sum(nrhs * args.steps)
@@ -310,26 +322,10 @@ def run_ours(args, w, name):
         xh, reph = ctx.apply(Bh)
         tt.append(time.perf_counter() - ts)
     e2e_value = D.sum(nrhs) / D.max(statistics.median(tt))
+    ctx.close()
 
-    # ---- stencil alone: FP32 links and spinors, all right-hand sides (the bandwidth kernel)
-    b32 = bdev.to(torch.complex64)
-    ctx.hw(b32, precision=pkg.PREC_MIXED)
-    out32 = torch.empty_like(b32)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    reps_st = 20
-    import ctypes as C
-    lib = pkg.lib()
-    for _ in range(3):
-        lib.sgn_hw_apply(ctx._h, C.c_void_p(b32.data_ptr()), C.c_void_p(out32.data_ptr()), nrhs, 1, 0)
-    torch.cuda.synchronize()
-    ev[0].record(stream)
-    for _ in range(reps_st):
-        lib.sgn_hw_apply(ctx._h, C.c_void_p(b32.data_ptr()), C.c_void_p(out32.data_ptr()), nrhs, 1, 0)
-    ev[1].record(stream)
-    torch.cuda.synchronize()
-    t_st = ev[0].elapsed_time(ev[1]) / 1000.0 / reps_st
-    st_bytes = (288 + 192 * nrhs) * vol       # links once, each spinor read once and written once
-    st_gbs = st_bytes / t_st / 1e9
+    # ---- stencil alone at 24^4 (HBM-bound): FP32 links and spinors, 12 columns
+    st = stencil_hbm(pkg, torch, args)
 
     peaks = {}
     try:
@@ -360,11 +356,9 @@ def run_ours(args, w, name):
             "fp64_form": None if rep64 is None else {"value": fp64_value, "unit": UNIT, "cycles": rep64["cycles"],
                                                      "ms": t64 * 1000},
             "mixed_report": {k2: reps[-1][k2] for k2 in ("cycles", "refine_rounds", "refine_cycles", "err_est")},
-            "stencil": {"precision": "fp32", "nrhs": nrhs, "gbs": st_gbs, "us_per_launch": t_st * 1e6,
-                        "bytes_per_launch": st_bytes},
-            "roofline": {"bound": "hbm", "achieved": st_gbs, "peak": hbm, "unit": "GB/s", "frac": st_gbs / hbm,
-                         "traffic": None, "kernel": "k_hw<float,float2> (12-RHS FP32 stencil)",
-                         "peak_source": peak_src},
+            "stencil_24^4": st,
+            "kernel_times": kt,
+            "roofline": roofline(kt, hbm, peak_src, t_mixed),
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(B.nbytes),
                     "d2h_bytes_per_step": int(B.nbytes)},
@@ -372,8 +366,52 @@ def run_ours(args, w, name):
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
-    ctx.close()
     D.close()
+
+
+def roofline(kt, hbm, peak_src, t_timed):
+    """Dominant kernel of the timed steps (largest summed event time): algorithmic
+    bytes per launch / average launch duration, against the measured HBM copy rate."""
+    name = max(kt, key=lambda k: kt[k]["ms"])
+    d = kt[name]
+    if not d["launches"]:
+        return None
+    per_launch_bytes = d["bytes"] / d["launches"]
+    per_launch_s = d["ms"] / 1000.0 / d["launches"]
+    achieved = per_launch_bytes / per_launch_s / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": None, "kernel": name, "launches": d["launches"],
+            "share_of_timed": d["ms"] / 1000.0 / t_timed, "peak_source": peak_src + " hbm_gbs"}
+
+
+def stencil_hbm(pkg, torch, args):
+    """12-column FP32 stencil at 24^4 (spread 0.7, mu 0.2): GB/s from algorithmic bytes."""
+    import ctypes as C
+    dims, nrhs = (24, 24, 24, 24), 12
+    U = si.random_su3_links(dims, 0.7, si.CONFIG_SEEDS[5][0])
+    vol = int(np.prod(dims))
+    with pkg.SignContext(dims, mu=0.2) as sc:
+        sc.load_gauge(torch.from_numpy(U).cuda())
+        del U
+        sc.set_precision(pkg.PREC_MIXED, 1e-8, pkg.LINKS_FP32)
+        b32 = torch.from_numpy(si.point_sources(dims, nrhs)).cuda().to(torch.complex64)
+        out = torch.empty_like(b32)
+        lib = pkg.lib()
+        stream = torch.cuda.current_stream()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        for _ in range(3):
+            lib.sgn_hw_apply(sc._h, C.c_void_p(b32.data_ptr()), C.c_void_p(out.data_ptr()), nrhs, 1, 0)
+        torch.cuda.synchronize()
+        reps = 20
+        ev[0].record(stream)
+        for _ in range(reps):
+            lib.sgn_hw_apply(sc._h, C.c_void_p(b32.data_ptr()), C.c_void_p(out.data_ptr()), nrhs, 1, 0)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        t = ev[0].elapsed_time(ev[1]) / 1000.0 / reps
+    byts = (288 + 192 * nrhs) * vol   # links once, each spinor read once and written once
+    return {"precision": "fp32", "nrhs": nrhs, "lattice": "24^4", "us_per_launch": t * 1e6,
+            "bytes_per_launch": byts, "gbs": byts / t / 1e9}
 
 
 def main():
@@ -382,7 +420,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="24^4", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="10^4", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fp64-form", action="store_true", help="do not time the plain FP64 form")
     args = ap.parse_args()

@@ -210,6 +210,19 @@ SGN_API int sgn_dhw_dmu_apply(sgn_ctx* ctx, const double* in, double* out, int n
  * of the deflated function are not part of this entry point). */
 SGN_API int sgn_grad_mu(sgn_ctx* ctx, const double* b, const double* g, int nrhs, double* dmu);
 
+/* Kernel timing (observability).  With on = 1, later solves record CUDA events
+ * around every launch of the restart cycle's main kernels, inside the captured
+ * graph, and accumulate per class: 0 = Wilson stencil, 1 = fused Gram-Schmidt
+ * reduction (k_dcgs_dots), 2 = fused Gram-Schmidt update (k_dcgs_update).
+ * Each event pair brackets one launch on the solver's stream.  Switching on or
+ * off resets the totals. */
+SGN_API int sgn_set_kernel_timing(sgn_ctx* ctx, int on);
+
+/* Totals of class `cls` since timing was switched on: summed milliseconds,
+ * launches, and algorithmic bytes (each input field read once, each output
+ * field written once). */
+SGN_API int sgn_get_kernel_timing(sgn_ctx* ctx, int cls, double* ms, long long* launches, double* bytes);
+
 /* Thread-local message for the last failing call of this thread. */
 SGN_API const char* sgn_last_error(void);
 

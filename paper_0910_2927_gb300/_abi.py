@@ -52,6 +52,9 @@ SIGNATURES = {
     "sgn_inner_products": (C.c_int, [P, P, C.c_int, P, C.c_int, P]),
     "sgn_dhw_dmu_apply": (C.c_int, [P, P, P, C.c_int]),
     "sgn_grad_mu": (C.c_int, [P, P, P, C.c_int, P]),
+    "sgn_set_kernel_timing": (C.c_int, [P, C.c_int]),
+    "sgn_get_kernel_timing": (C.c_int, [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
+                                        C.POINTER(C.c_double)]),
     "sgn_last_error": (C.c_char_p, []),
     "sgn_version": (C.c_char_p, []),
 }

@@ -402,3 +402,22 @@ SGN_API int sgn_inner_products(sgn_ctx* c, const double* V, int J, const double*
         }
     return SGN_OK;
 }
+
+SGN_API int sgn_set_kernel_timing(sgn_ctx* c, int on) {
+    if (!c) return fail(SGN_ERR_ARG, "sgn_set_kernel_timing: NULL context");
+    c->timing = on ? 1 : 0;
+    for (int i = 0; i < 3; ++i) {
+        c->t_ms[i] = 0;
+        c->t_launches[i] = 0;
+        c->t_bytes[i] = 0;
+    }
+    return SGN_OK;
+}
+
+SGN_API int sgn_get_kernel_timing(sgn_ctx* c, int cls, double* ms, long long* launches, double* bytes) {
+    if (!c || cls < 0 || cls > 2) return fail(SGN_ERR_ARG, "sgn_get_kernel_timing: bad argument");
+    if (ms) *ms = c->t_ms[cls];
+    if (launches) *launches = c->t_launches[cls];
+    if (bytes) *bytes = c->t_bytes[cls];
+    return SGN_OK;
+}

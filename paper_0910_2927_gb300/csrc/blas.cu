@@ -17,7 +17,7 @@ namespace {
 constexpr int NT = 256;
 constexpr int NWARP = NT / 32;
 constexpr int PK = 4;
-constexpr int MAXSLOT = 104;  // >= kmax + 2, >= deflation size + 1, >= eigensolver block + 1
+constexpr int MAXSLOT = 136;  // >= 2 kmax + 3 (delayed CGS2), >= deflation size + 1, >= eigensolver block + 1
 
 template <class T>
 struct Ops;
@@ -392,6 +392,157 @@ __global__ void __launch_bounds__(NT) k_update_shifts(Basis<T> V, int J, const d
     }
 }
 
+// Delayed CGS2, fused reduction of step j (Q = V_0..V_{J-1} orthonormal, u the
+// once-orthogonalised candidate, z = A^2 u):  slots [0,J) s = Q^dag u,
+// [J,2J) t = Q^dag z, 2J: u^dag u, 2J+1: u^dag z, 2J+2: z^dag z.  With z = null
+// (the closing pass of a cycle) only s and u^dag u (slot J).
+template <class T>
+__global__ void __launch_bounds__(NT) k_dcgs_dots(Basis<T> V, int J, const T* __restrict__ u,
+                                                  const T* __restrict__ z, int64_t wsr, int64_t npk, Reduce rd,
+                                                  const int* __restrict__ skip) {
+    using O = Ops<T>;
+    const int col = blockIdx.y;
+    if (skip && skip[col]) return;
+    __shared__ double2 sm[MAXSLOT][NWARP];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const T* uc = u + col * wsr;
+    const T* zc = z ? z + col * wsr : nullptr;
+    const int64_t base = (int64_t)blockIdx.x * NT * PK + threadIdx.x;
+    typename O::P uv[PK], zv[PK];
+#pragma unroll
+    for (int p = 0; p < PK; ++p) {
+        int64_t i = base + p * NT;
+        uv[p] = i < npk ? O::ld(uc, i) : O::zero();
+        zv[p] = (zc && i < npk) ? O::ld(zc, i) : O::zero();
+    }
+    const T* vb = V.base + col * V.sr;
+    for (int l = 0; l < J; ++l) {
+        const T* vl = vb + l * V.sj;
+        double2 as, at;
+        if constexpr (O::CPX == 2) {
+            float sx = 0.f, sy = 0.f, tx = 0.f, ty = 0.f;  // FP32 chunks of PK packs
+#pragma unroll
+            for (int p = 0; p < PK; ++p) {
+                int64_t i = base + p * NT;
+                if (i < npk) {
+                    typename O::P q = O::ld_ro(vl, i);
+                    double2 d1 = O::dot(q, uv[p]);
+                    sx += (float)d1.x;
+                    sy += (float)d1.y;
+                    if (zc) {
+                        double2 d2 = O::dot(q, zv[p]);
+                        tx += (float)d2.x;
+                        ty += (float)d2.y;
+                    }
+                }
+            }
+            as = make_double2(sx, sy);
+            at = make_double2(tx, ty);
+        } else {
+            as = make_double2(0, 0);
+            at = make_double2(0, 0);
+#pragma unroll
+            for (int p = 0; p < PK; ++p) {
+                int64_t i = base + p * NT;
+                if (i < npk) {
+                    typename O::P q = O::ld_ro(vl, i);
+                    as = cadd(as, O::dot(q, uv[p]));
+                    if (zc) at = cadd(at, O::dot(q, zv[p]));
+                }
+            }
+        }
+        as = warp_sum(as);
+        if (lane == 0) sm[l][warp] = as;
+        if (zc) {
+            at = warp_sum(at);
+            if (lane == 0) sm[J + l][warp] = at;
+        }
+    }
+    {
+        double a = 0;
+        double2 bz = make_double2(0, 0);
+        double g = 0;
+#pragma unroll
+        for (int p = 0; p < PK; ++p) {
+            a += O::nrm2(uv[p]);
+            if (zc) {
+                bz = cadd(bz, O::dot(uv[p], zv[p]));
+                g += O::nrm2(zv[p]);
+            }
+        }
+        const int base_slot = zc ? 2 * J : J;
+        double2 r = warp_sum(make_double2(a, 0));
+        if (lane == 0) sm[base_slot][warp] = r;
+        if (zc) {
+            r = warp_sum(bz);
+            if (lane == 0) sm[base_slot + 1][warp] = r;
+            r = warp_sum(make_double2(g, 0));
+            if (lane == 0) sm[base_slot + 2][warp] = r;
+        }
+    }
+    flush_partials(sm, zc ? 2 * J + 3 : J + 1, rd, col);
+}
+
+// Delayed CGS2, update of step j:  q_j = (u - Q s) / rho  (written over u), and
+// the next candidate  u_{j+1} = z / rho - Q c - d q_j  (when next != null).
+// Coefficients per column: [0,J) s, [J,2J) c, 2J: (1/rho, 0), 2J+1: d.
+template <class T>
+__global__ void __launch_bounds__(NT) k_dcgs_update(Basis<T> V, int J, const double2* __restrict__ coef,
+                                                    int cstride, T* u, const T* __restrict__ z, T* next,
+                                                    int64_t wsr, int64_t npk, const int* __restrict__ skip) {
+    using O = Ops<T>;
+    const int col = blockIdx.y;
+    if (skip && skip[col]) return;
+    __shared__ typename O::C cs[MAXSLOT], cc[MAXSLOT];
+    __shared__ double ex[2][2];
+    const double2* cf = coef + (int64_t)col * cstride;
+    for (int l = threadIdx.x; l < J; l += NT) {
+        cs[l] = O::coef(cf[l]);
+        cc[l] = O::coef(cf[J + l]);
+    }
+    if (threadIdx.x == 0) {
+        ex[0][0] = cf[2 * J].x;
+        ex[1][0] = cf[2 * J + 1].x;
+        ex[1][1] = cf[2 * J + 1].y;
+    }
+    __syncthreads();
+    const double inv_rho = ex[0][0];
+    const typename O::C dd = O::coef(make_double2(ex[1][0], ex[1][1]));
+    T* uc = u + col * wsr;
+    const T* zc = next ? z + col * wsr : nullptr;
+    T* nc = next ? next + col * wsr : nullptr;
+    const T* vb = V.base + col * V.sr;
+    const int64_t base = (int64_t)blockIdx.x * NT * PK + threadIdx.x;
+#pragma unroll
+    for (int p = 0; p < PK; ++p) {
+        int64_t i = base + p * NT;
+        if (i >= npk) break;
+        typename O::P qs = O::zero(), qc = O::zero();
+        for (int l = 0; l < J; ++l) {
+            typename O::P q = O::ld_ro(vb + l * V.sj, i);
+            O::add_cv(qs, cs[l], q);
+            if (nc) O::add_cv(qc, cc[l], q);
+        }
+        typename O::P uv = O::ld(uc, i);
+        // q_j = (u - qs) / rho
+        typename O::C one;
+        if constexpr (O::CPX == 1) {
+            one = make_double2(1.0, 0.0);
+        } else {
+            one = make_float2(1.0f, 0.0f);
+        }
+        O::sub_cv(uv, one, qs);
+        typename O::P qj = O::scal(uv, inv_rho);
+        O::st(uc, i, qj);
+        if (nc) {
+            typename O::P nv = O::scal(O::ld(zc, i), inv_rho);
+            O::sub_cv(nv, one, qc);
+            O::sub_cv(nv, dd, qj);
+            O::st(nc, i, nv);
+        }
+    }
+}
+
 // Second stage of every reduction plus the scalar bookkeeping that consumes it.
 __global__ void __launch_bounds__(NT) k_reduce(Reduce rd, int nslot, int mode, int colidx, DevState S,
                                                const double2* __restrict__ lambda) {
@@ -400,6 +551,7 @@ __global__ void __launch_bounds__(NT) k_reduce(Reduce rd, int nslot, int mode, i
     // broke down in this cycle; every other mode is column work proper.
     if (mode == RM_BETA_RESTART && S.done[col]) return;
     if (mode != RM_BETA_FIRST && mode != RM_BETA_RESTART && S.skip[col]) return;
+    __shared__ double2 gsh[MAXSLOT];
     __shared__ double2 sums[MAXSLOT];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int j = warp; j < nslot; j += NWARP) {
@@ -446,6 +598,87 @@ __global__ void __launch_bounds__(NT) k_reduce(Reduce rd, int nslot, int mode, i
                 } else {
                     S.scale[col] = 1.0 / hn;
                 }
+            }
+            break;
+        }
+        case RM_DCGS:
+        case RM_DCGS_FINAL: {
+            // Delayed CGS2 bookkeeping of step j = colidx (see k_dcgs_dots for the slots).
+            const int j = colidx;
+            const bool fin = mode == RM_DCGS_FINAL;
+            const int64_t hb = (int64_t)col * (S.kmax + 1) * S.kmax;
+            const int km = S.kmax;
+            double2* H = S.H + hb;
+            const double2 alpha = sums[fin ? j : 2 * j];
+            __shared__ double rho_sh;
+            __shared__ int broke_sh;
+            if (threadIdx.x == 0) {
+                double s2 = 0;
+                for (int l = 0; l < j; ++l) s2 += cabs2(sums[l]);
+                double r2 = alpha.x - s2;
+                double rho = r2 > 0 ? sqrt(r2) : 0.0;
+                int broke = 0;
+                if (j == 0) {
+                    S.beta[col] = rho;
+                    broke = !(rho > 0);
+                } else {
+                    broke = !(rho > S.bd_tol * S.norm0[col]);
+                    H[(int64_t)j * km + (j - 1)] = make_double2(rho, 0);
+                }
+                if (!isfinite(r2)) {
+                    atomicOr(S.err, 2);
+                    broke = 1;
+                }
+                rho_sh = rho;
+                broke_sh = broke;
+            }
+            __syncthreads();
+            // correct column j-1: H[0:j, j-1] += s
+            for (int l = threadIdx.x; l < j; l += NT) {
+                double2 h = H[(int64_t)l * km + (j - 1)];
+                H[(int64_t)l * km + (j - 1)] = cadd(h, sums[l]);
+            }
+            __syncthreads();
+            const double rho = rho_sh;
+            const int64_t cr = (int64_t)col * S.rstride;
+            if (fin) {
+                // closing pass: q_k = (u - Q s) / rho; an invariant Krylov space (rho ~ 0)
+                // leaves q_k = 0, so the restart norm is 0 and the column converges
+                for (int l = threadIdx.x; l < j; l += NT) S.red[cr + l] = sums[l];
+                if (threadIdx.x == 0) S.red[cr + 2 * j] = make_double2(broke_sh ? 0.0 : 1.0 / rho, 0);
+                break;
+            }
+            if (broke_sh) {  // the Krylov space is invariant: FOM on its j columns is exact
+                if (threadIdx.x == 0) {
+                    S.kk[col] = j;
+                    S.skip[col] = 1;
+                }
+                break;
+            }
+            for (int l = threadIdx.x; l < j; l += NT) S.red[cr + l] = sums[l];  // s
+            // g = Hbar s, Hbar = H[0:j+1, 0:j]
+            for (int i = threadIdx.x; i <= j; i += NT) {
+                double2 g = make_double2(0, 0);
+                for (int l = (i > 0 ? i - 1 : 0); l < j; ++l) g = cadd(g, cmul(H[(int64_t)i * km + l], sums[l]));
+                gsh[i] = g;
+            }
+            __syncthreads();
+            const double ir = 1.0 / rho;
+            for (int i = threadIdx.x; i < j; i += NT) {
+                double2 t = sums[j + i];
+                double2 hp = make_double2((t.x - gsh[i].x) * ir, (t.y - gsh[i].y) * ir);
+                H[(int64_t)i * km + j] = hp;                                             // tentative column j
+                S.red[cr + j + i] = make_double2(gsh[i].x * ir + hp.x, gsh[i].y * ir + hp.y);  // c
+            }
+            if (threadIdx.x == 0) {
+                double2 st = make_double2(0, 0);
+                for (int l = 0; l < j; ++l) st = cadd(st, cconjmul(sums[l], sums[j + l]));
+                double2 beta = sums[2 * j + 1];
+                double2 hjj = make_double2(((beta.x - st.x) * ir - gsh[j].x) * ir, ((beta.y - st.y) * ir - gsh[j].y) * ir);
+                H[(int64_t)j * km + j] = hjj;
+                S.red[cr + 2 * j] = make_double2(ir, 0);
+                S.red[cr + 2 * j + 1] = make_double2(gsh[j].x * ir + hjj.x, gsh[j].y * ir + hjj.y);  // d
+                S.norm0[col] = sqrt(sums[2 * j + 2].x) * ir;  // ~ ||A^2 q_j|| for the next breakdown test
             }
             break;
         }
@@ -683,6 +916,37 @@ cudaError_t update_shifts(Basis<T> V, int J, const double2* y, int s, int kmax, 
     count_launch();
     return cudaGetLastError();
 }
+
+template <class T>
+cudaError_t dcgs_dots(Basis<T> V, int J, const T* u, const T* z, int64_t wsr, int64_t n, int ncol, const Reduce& rd,
+                      const int* skip, cudaStream_t st) {
+    if (2 * J + 3 > MAXSLOT) return cudaErrorInvalidValue;
+    int64_t npk = n / Ops<T>::CPX;
+    dim3 grid(rd.nblk, ncol);
+    k_dcgs_dots<T><<<grid, NT, 0, st>>>(V, J, u, z, wsr, npk, rd, skip);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t dcgs_update(Basis<T> V, int J, const double2* coef, int cstride, T* u, const T* z, T* next, int64_t wsr,
+                        int64_t n, int ncol, const int* skip, cudaStream_t st) {
+    if (J > MAXSLOT) return cudaErrorInvalidValue;
+    int64_t npk = n / Ops<T>::CPX;
+    dim3 grid(reduce_blocks<T>(n), ncol);
+    k_dcgs_update<T><<<grid, NT, 0, st>>>(V, J, coef, cstride, u, z, next, wsr, npk, skip);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template cudaError_t dcgs_dots<double2>(Basis<double2>, int, const double2*, const double2*, int64_t, int64_t, int,
+                                        const Reduce&, const int*, cudaStream_t);
+template cudaError_t dcgs_dots<float2>(Basis<float2>, int, const float2*, const float2*, int64_t, int64_t, int,
+                                       const Reduce&, const int*, cudaStream_t);
+template cudaError_t dcgs_update<double2>(Basis<double2>, int, const double2*, int, double2*, const double2*,
+                                          double2*, int64_t, int64_t, int, const int*, cudaStream_t);
+template cudaError_t dcgs_update<float2>(Basis<float2>, int, const double2*, int, float2*, const float2*, float2*,
+                                         int64_t, int64_t, int, const int*, cudaStream_t);
 
 template <class T>
 cudaError_t axpby3(T* out, double a, const T* x, double b, const T* y, double c, const T* z, int64_t count,

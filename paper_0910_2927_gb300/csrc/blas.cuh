@@ -39,7 +39,9 @@ enum ReduceMode {
     RM_P2 = 2,           // second CGS pass: Hessenberg column, h_{j+1,j}, breakdown, scale
     RM_BETA_FIRST = 3,   // bnorm = beta = sqrt(sum_0), rho = 1, scale = 1/beta
     RM_BETA_RESTART = 4, // beta = sqrt(sum_0), residual estimate, convergence, scale = 1/beta
-    RM_SIGNED = 5        // red[col][j] = sign(Re lambda_j) * sum_j (x_P coefficients)
+    RM_SIGNED = 5,       // red[col][j] = sign(Re lambda_j) * sum_j (x_P coefficients)
+    RM_DCGS = 6,         // delayed CGS2 step j: rho, column j-1 correction, tentative column j, update coefficients
+    RM_DCGS_FINAL = 7    // delayed CGS2 closing pass of a cycle (no new candidate)
 };
 
 template <class T>
@@ -59,6 +61,14 @@ cudaError_t update_x(Basis<T> V, int J, const double2* coef, int cstride, double
 template <class T>
 cudaError_t update_shifts(Basis<T> V, int J, const double2* y, int s, int kmax, double2* xs, int64_t xs_shift,
                           int64_t xs_col, int64_t n, int ncol, const int* skip, const int* kk, cudaStream_t st);
+
+// Delayed CGS2 (one fused reduction and one fused update per Arnoldi step).
+template <class T>
+cudaError_t dcgs_dots(Basis<T> V, int J, const T* u, const T* z, int64_t wsr, int64_t n, int ncol, const Reduce& rd,
+                      const int* skip, cudaStream_t st);
+template <class T>
+cudaError_t dcgs_update(Basis<T> V, int J, const double2* coef, int cstride, T* u, const T* z, T* next, int64_t wsr,
+                        int64_t n, int ncol, const int* skip, cudaStream_t st);
 
 // out = a x + b y + c z over `count` complex elements (z may be null).
 template <class T>

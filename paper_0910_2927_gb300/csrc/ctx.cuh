@@ -49,6 +49,9 @@ struct Engine {
     cudaGraphExec_t graph = nullptr;
     uint64_t graph_key = 0;
     long long graph_kernels = 0;  // kernel nodes of the captured cycle
+    // kernel timing: event pairs recorded inside the cycle (class, algorithmic bytes)
+    std::vector<cudaEvent_t> tev;
+    std::vector<std::pair<int, double>> tmarks;
 };
 
 }  // namespace sgn
@@ -96,6 +99,11 @@ struct sgn_ctx {
     size_t io_bytes = 0;
     double2* h_pinned = nullptr;
     size_t h_pinned_bytes = 0;
+    // kernel timing totals per class (stencil, Gram-Schmidt reduction, Gram-Schmidt update)
+    int timing = 0;
+    double t_ms[3] = {0, 0, 0};
+    long long t_launches[3] = {0, 0, 0};
+    double t_bytes[3] = {0, 0, 0};
 };
 
 namespace sgn {

@@ -14,7 +14,9 @@
 #include "ctx.cuh"
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
+#include <string>
 
 namespace sgn {
 
@@ -150,12 +152,111 @@ uint64_t cycle_key(const sgn_ctx* c, const Engine& E, const CycleArgs& a) {
     mixd(c->mass);
     for (int d = 0; d < 4; ++d) h = mix(h, c->ap[d]);
     mixd(E.S.tol);
+    h = mix(h, c->timing);
     return h;
 }
 
-// One restart cycle of Algorithm 1 for all columns.
+// Event pair around one launch of a timed kernel class (only while capturing a
+// cycle with timing on); the pair is replayed with the graph.
+struct Timer {
+    const sgn_ctx* c;
+    Engine& E;
+    cudaStream_t st;
+    int idx = -1;
+    Timer(const sgn_ctx* c_, Engine& E_, cudaStream_t st_) : c(c_), E(E_), st(st_) {}
+    cudaError_t begin(int cls, double bytes) {
+        if (!c->timing) return cudaSuccess;
+        idx = (int)E.tmarks.size();
+        while ((int)E.tev.size() < 2 * (idx + 1)) {
+            cudaEvent_t ev;
+            cudaError_t e = cudaEventCreate(&ev);
+            if (e != cudaSuccess) return e;
+            E.tev.push_back(ev);
+        }
+        E.tmarks.emplace_back(cls, bytes);
+        return cudaEventRecord(E.tev[2 * idx], st);
+    }
+    cudaError_t end() {
+        if (!c->timing) return cudaSuccess;
+        return cudaEventRecord(E.tev[2 * idx + 1], st);
+    }
+};
+
+bool use_cgs2() {
+    static const bool v = [] {
+        const char* s = getenv("SGN_ORTHO");
+        return s && std::string(s) == "cgs2";
+    }();
+    return v;
+}
+
+// One restart cycle of Algorithm 1, Arnoldi by delayed CGS2: the second
+// projection of each new basis vector is done in the next step's single fused
+// reduction, so every step reads the basis twice (one reduction sweep, one
+// update sweep) instead of three times.  On entry V[0] holds the unnormalised
+// restart vector; step 0 normalises it and records beta.
+template <class T>
+cudaError_t cycle_dcgs(const sgn_ctx* c, Engine& E, const CycleArgs& a, cudaStream_t st) {
+    const int64_t n = E.n;
+    const int ncol = E.ncol, k = E.k;
+    T* V = reinterpret_cast<T*>(E.V);
+    T* w = reinterpret_cast<T*>(E.w);
+    T* t = reinterpret_cast<T*>(E.t);
+    const int64_t sj = (int64_t)ncol * n, sr = n;
+    const Reduce rd{E.partial, E.nblk, E.rstride};
+    const DevState& S = E.S;
+    const Basis<T> VB{V, sj, sr};
+    const double fb = (double)n * sizeof(T) * ncol;            // one field per column
+    const double stb = (double)c->vol * 4 * 9 * sizeof(T) + 2 * fb;  // links once, in and out once
+    Timer tm(c, E, st);
+    for (int j = 0; j < k; ++j) {
+        // z = A^2 u_j (u_j: candidate for v_j, once orthogonalised)
+        CU(tm.begin(0, stb));
+        CU(apply_hw<T>(c, t, V + j * sj, ncol, a.adjoint, S.skip, st));
+        CU(tm.end());
+        CU(tm.begin(0, stb));
+        CU(apply_hw<T>(c, w, t, ncol, a.adjoint, S.skip, st));
+        CU(tm.end());
+        CU(tm.begin(1, (j + 2) * fb));
+        CU(dcgs_dots<T>(VB, j, V + j * sj, w, sr, n, ncol, rd, S.skip, st));
+        CU(tm.end());
+        CU(reduce(rd, 2 * j + 3, ncol, RM_DCGS, j, S, nullptr, st));
+        CU(tm.begin(2, (j + 4) * fb));
+        CU(dcgs_update<T>(VB, j, S.red, S.rstride, V + j * sj, w, V + (j + 1) * sj, sr, n, ncol, S.skip, st));
+        CU(tm.end());
+    }
+    // closing pass: second projection of v_k
+    CU(tm.begin(1, (k + 1) * fb));
+    CU(dcgs_dots<T>(VB, k, V + k * sj, nullptr, sr, n, ncol, rd, S.skip, st));
+    CU(tm.end());
+    CU(reduce(rd, k + 1, ncol, RM_DCGS_FINAL, k, S, nullptr, st));
+    CU(tm.begin(2, (k + 2) * fb));
+    CU(dcgs_update<T>(VB, k, S.red, S.rstride, V + k * sj, nullptr, nullptr, sr, n, ncol, S.skip, st));
+    CU(tm.end());
+    CU(shifted_solves(S, ncol, st));
+    CU(combine_shifts(S, ncol, st));
+    if (a.xacc) CU(update_x<T>(VB, k, S.coef, S.rstride, a.xacc, a.xsr, n, ncol, S.done, S.kk, st));
+    if (a.xs) CU(update_shifts<T>(VB, k, S.y, E.s, k, a.xs, a.xs_shift, a.xs_col, n, ncol, S.done, S.kk, st));
+    T* Vk = V + k * sj;
+    if (a.project && a.m > 0) {
+        const Basis<T> LB{reinterpret_cast<const T*>(a.L), n, 0};
+        const Basis<T> RB{reinterpret_cast<const T*>(a.R), n, 0};
+        CU(mdot<T>(LB, a.m, Vk, sr, n, ncol, rd, 0, S.skip, st));
+        CU(reduce(rd, a.m, ncol, RM_STORE, 0, S, nullptr, st));
+        CU(maxpy_scale<T>(RB, a.m, S.red, S.rstride, Vk, sr, Vk, sr, nullptr, n, ncol, S.skip, st));
+    }
+    // convergence test on ||r||; r (unnormalised) becomes the next cycle's V[0]
+    CU(mdot<T>(VB, 0, Vk, sr, n, ncol, rd, 1, S.skip, st));
+    CU(reduce(rd, 1, ncol, RM_BETA_RESTART, 0, S, nullptr, st));
+    CU(maxpy_scale<T>(VB, 0, S.red, S.rstride, Vk, sr, V, sr, nullptr, n, ncol, S.skip, st));
+    return cudaSuccess;
+}
+
+// One restart cycle of Algorithm 1 for all columns, Arnoldi by CGS2 in three
+// passes per step (kept for comparison; SGN_ORTHO=cgs2).
 template <class T>
 cudaError_t cycle(const sgn_ctx* c, Engine& E, const CycleArgs& a, cudaStream_t st) {
+    if (!use_cgs2()) return cycle_dcgs<T>(c, E, a, st);
     const int64_t n = E.n;
     const int ncol = E.ncol, k = E.k;
     T* V = reinterpret_cast<T*>(E.V);
@@ -215,7 +316,7 @@ int get_engine(sgn_ctx* c, int ncol, int k, int s, int prec, Engine** out) {
     E->n = c->n;
     const size_t esz = prec == SGN_PREC_FP64 ? sizeof(double2) : sizeof(float2);
     E->nblk = prec == SGN_PREC_FP64 ? reduce_blocks<double2>(c->n) : reduce_blocks<float2>(c->n);
-    int rs = std::max(k + 2, c->m + 1);
+    int rs = std::max(2 * k + 4, c->m + 1);
     E->rstride = (rs + 7) & ~7;
     const size_t nc = (size_t)ncol;
     const size_t field = (size_t)c->n * esz;
@@ -289,6 +390,7 @@ void release_engines(sgn_ctx* c) {
     for (auto& kv : c->engines) {
         Engine& E = *kv.second;
         if (E.graph) cudaGraphExecDestroy(E.graph);
+        for (cudaEvent_t ev : E.tev) cudaEventDestroy(ev);
         dev_free(c, E.arena);
         if (E.h_done) cudaFreeHost(E.h_done);
         if (E.h_resest) cudaFreeHost(E.h_resest);
@@ -326,7 +428,8 @@ int run_engine(sgn_ctx* c, Engine& E, const CycleArgs& a, double tol, int max_cy
     // beta = ||b~||, rho_i = 1, v_1 = b~ / beta
     SGN_CUDA(mdot<T>(VB, 0, V, n, n, ncol, rd, 1, nullptr, st));
     SGN_CUDA(reduce(rd, 1, ncol, RM_BETA_FIRST, 0, E.S, nullptr, st));
-    SGN_CUDA(maxpy_scale<T>(VB, 0, E.S.red, E.S.rstride, V, n, V, n, E.S.scale, n, ncol, E.S.skip, st));
+    if (use_cgs2())  // delayed CGS2 normalises the restart vector in its first step
+        SGN_CUDA(maxpy_scale<T>(VB, 0, E.S.red, E.S.rstride, V, n, V, n, E.S.scale, n, ncol, E.S.skip, st));
 
     const uint64_t key = cycle_key(c, E, a);
     if (E.graph && E.graph_key != key) {
@@ -339,6 +442,7 @@ int run_engine(sgn_ctx* c, Engine& E, const CycleArgs& a, double tol, int max_cy
     }();
     if (!E.graph && !no_graph) {
         cudaGraph_t g = nullptr;
+        E.tmarks.clear();
         SGN_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         const long long before = g_launches;
         cudaError_t ce = cycle<T>(c, E, a, st);
@@ -367,11 +471,21 @@ int run_engine(sgn_ctx* c, Engine& E, const CycleArgs& a, double tol, int max_cy
             SGN_CUDA(cudaGraphLaunch(E.graph, st));
             count_launch(E.graph_kernels);
         } else {
+            E.tmarks.clear();
             SGN_CUDA(cycle<T>(c, E, a, st));
         }
         SGN_CUDA(cudaMemcpyAsync(E.h_done, E.S.done, ncol * sizeof(int), cudaMemcpyDeviceToHost, st));
         SGN_CUDA(cudaMemcpyAsync(E.h_err, E.S.err, sizeof(int), cudaMemcpyDeviceToHost, st));
         SGN_CUDA(cudaStreamSynchronize(st));
+        if (c->timing)
+            for (size_t i = 0; i < E.tmarks.size(); ++i) {
+                float ms = 0;
+                SGN_CUDA(cudaEventElapsedTime(&ms, E.tev[2 * i], E.tev[2 * i + 1]));
+                const int cls = E.tmarks[i].first;
+                c->t_ms[cls] += ms;
+                c->t_launches[cls] += 1;
+                c->t_bytes[cls] += E.tmarks[i].second;
+            }
         if (*E.h_err) break;
         all_done = true;
         for (int i = 0; i < ncol; ++i) all_done = all_done && E.h_done[i];
@@ -437,7 +551,7 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
     SGN_CHECK(get_engine(c, ncol, k, s, SGN_PREC_MIXED, &E));
     // refinement batch: one shifted system per column, bounded by memory
     const size_t per_col = (size_t)(k + 4) * n * sizeof(float2) + (size_t)n * sizeof(double2);
-    int B = (int)std::min<size_t>((size_t)s * ncol, std::max<size_t>(1, kRefineBudgetBytes / per_col));
+    int B = (int)std::min<size_t>({(size_t)s * ncol, (size_t)4 * ncol, std::max<size_t>(1, kRefineBudgetBytes / per_col)});
     Engine* E1 = nullptr;
     SGN_CHECK(get_engine(c, B, k, 1, SGN_PREC_MIXED, &E1));
 
