@@ -83,6 +83,8 @@ SGN_API int sgn_create(sgn_ctx** out, const int dims[4], sgn_alloc_fn alloc, sgn
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev_t0);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev_t1);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev_k0);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev_k1);
     if (e == cudaSuccess) e = prepare_small_kernels();
     if (e != cudaSuccess) {
         set_error(std::string("sgn_create: ") + cudaGetErrorString(e));
@@ -114,6 +116,8 @@ SGN_API int sgn_destroy(sgn_ctx* c) {
     if (c->ev_out) cudaEventDestroy(c->ev_out);
     if (c->ev_t0) cudaEventDestroy(c->ev_t0);
     if (c->ev_t1) cudaEventDestroy(c->ev_t1);
+    if (c->ev_k0) cudaEventDestroy(c->ev_k0);
+    if (c->ev_k1) cudaEventDestroy(c->ev_k1);
     if (c->work) cudaStreamDestroy(c->work);
     delete c;
     return SGN_OK;

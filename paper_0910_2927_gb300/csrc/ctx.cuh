@@ -64,6 +64,7 @@ struct sgn_ctx {
     cudaStream_t user_stream = nullptr;
     cudaStream_t work = nullptr;  // internal stream (capturable); ordered against user_stream by events
     cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+    cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;  // autotuner timing
     sgn_alloc_fn alloc = nullptr;
     sgn_free_fn free_ = nullptr;
     void* user = nullptr;
@@ -99,6 +100,8 @@ struct sgn_ctx {
     size_t io_bytes = 0;
     double2* h_pinned = nullptr;
     size_t h_pinned_bytes = 0;
+    // tuned stencil launch shapes, keyed by precision * 4096 + columns
+    std::map<int, sgn::StencilShape> shapes;
     // kernel timing totals per class (stencil, Gram-Schmidt reduction, Gram-Schmidt update)
     int timing = 0;
     double t_ms[3] = {0, 0, 0};
@@ -117,6 +120,9 @@ cudaError_t apply_hw32(const sgn_ctx* c, float2* out, const float2* in, int ncol
 
 int solve(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int ncol, bool adjoint, bool no_a,
           sgn_report* rep);
+// Pick the fastest stencil launch shape for (precision, ncol) by timing candidates
+// on the given buffers (ncol fields each); cached in the context.  Not during capture.
+int tune_stencil(sgn_ctx* c, int prec, int ncol, void* in, void* out);
 // Dot products <a_c, b_c> of ncol pairs of FP64 fields (host result, FP64 reductions).
 int field_dots(sgn_ctx* c, const double2* a, const double2* b, int ncol, std::vector<std::complex<double>>& out);
 int build_deflation(sgn_ctx* c, int m, int extra, double eig_tol, double* lambda_out);

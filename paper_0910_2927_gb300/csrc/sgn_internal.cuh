@@ -58,12 +58,18 @@ struct StencilParams {
 // ---------------------------------------------------------- kernel entry --
 // Stencil: out = H_W in for nrhs fields.  Real = double or float; links in
 // double, float or bf16 (Link).  skip: per-field flags (non-zero: skip), may be null.
+// Launch shape: sx sites (x fastest) by rb fields per CTA; {0, 0} picks the default.
+struct StencilShape {
+    int sx = 0;
+    int rb = 0;
+};
 cudaError_t launch_hw_f64(double2* out, const double2* in, const double2* U, int nrhs,
-                          const StencilParams& p, const int* skip, cudaStream_t st);
+                          const StencilParams& p, const int* skip, cudaStream_t st, StencilShape sh = {});
 cudaError_t launch_hw_f32(float2* out, const float2* in, const float2* U, int nrhs,
-                          const StencilParams& p, const int* skip, cudaStream_t st);
+                          const StencilParams& p, const int* skip, cudaStream_t st, StencilShape sh = {});
 cudaError_t launch_hw_f32_bf16links(float2* out, const float2* in, const __nv_bfloat162* U, int nrhs,
-                                    const StencilParams& p, const int* skip, cudaStream_t st);
+                                    const StencilParams& p, const int* skip, cudaStream_t st,
+                                    StencilShape sh = {});
 
 // ------------------------------------------------------------ vector ops --
 // A "basis" is J fields per column: element e of vector j of column r lives at

@@ -14,6 +14,7 @@
 #include "ctx.cuh"
 
 #include <algorithm>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <string>
@@ -71,18 +72,77 @@ StencilParams stencil_params(const sgn_ctx* c, bool adjoint) {
     return p;
 }
 
+namespace {
+StencilShape shape_for(const sgn_ctx* c, int prec, int ncol) {
+    auto it = c->shapes.find(prec * 4096 + ncol);
+    return it == c->shapes.end() ? StencilShape{} : it->second;
+}
+}  // namespace
+
 cudaError_t apply_hw64(const sgn_ctx* c, double2* out, const double2* in, int ncol, bool adjoint, const int* skip,
                        cudaStream_t st) {
     return launch_hw_f64(out, in, reinterpret_cast<const double2*>(c->U64.p), ncol, stencil_params(c, adjoint), skip,
-                         st);
+                         st, shape_for(c, 0, ncol));
 }
 
 cudaError_t apply_hw32(const sgn_ctx* c, float2* out, const float2* in, int ncol, bool adjoint, const int* skip,
                        cudaStream_t st) {
     StencilParams p = stencil_params(c, adjoint);
+    const int prec = c->link_storage == SGN_LINKS_BF16 ? 2 : 1;
     if (c->link_storage == SGN_LINKS_BF16)
-        return launch_hw_f32_bf16links(out, in, reinterpret_cast<const __nv_bfloat162*>(c->U16.p), ncol, p, skip, st);
-    return launch_hw_f32(out, in, reinterpret_cast<const float2*>(c->U32.p), ncol, p, skip, st);
+        return launch_hw_f32_bf16links(out, in, reinterpret_cast<const __nv_bfloat162*>(c->U16.p), ncol, p, skip, st,
+                                       shape_for(c, prec, ncol));
+    return launch_hw_f32(out, in, reinterpret_cast<const float2*>(c->U32.p), ncol, p, skip, st,
+                         shape_for(c, prec, ncol));
+}
+
+int tune_stencil(sgn_ctx* c, int prec, int ncol, void* in, void* out) {
+    const int key = prec * 4096 + ncol;
+    if (c->shapes.count(key)) return SGN_OK;
+    cudaStream_t st = c->work;
+    const StencilParams p = stencil_params(c, false);
+    std::vector<StencilShape> cands;
+    for (int rb : {1, 2, 3, 4, 6, 8, 12, 16}) {
+        if (rb > ncol) continue;
+        for (int sx : {32, 64, 128, 256})
+            if (sx * rb <= 384 && sx * rb >= 64) cands.push_back({sx, rb});
+    }
+    if (cands.empty()) cands.push_back({});
+    auto run = [&](StencilShape sh) -> cudaError_t {
+        if (prec == 0)
+            return launch_hw_f64(reinterpret_cast<double2*>(out), reinterpret_cast<const double2*>(in),
+                                 reinterpret_cast<const double2*>(c->U64.p), ncol, p, nullptr, st, sh);
+        if (prec == 2)
+            return launch_hw_f32_bf16links(reinterpret_cast<float2*>(out), reinterpret_cast<const float2*>(in),
+                                           reinterpret_cast<const __nv_bfloat162*>(c->U16.p), ncol, p, nullptr, st,
+                                           sh);
+        return launch_hw_f32(reinterpret_cast<float2*>(out), reinterpret_cast<const float2*>(in),
+                             reinterpret_cast<const float2*>(c->U32.p), ncol, p, nullptr, st, sh);
+    };
+    float best = 1e30f;
+    StencilShape pick{};
+    const long long l0 = g_launches;
+    for (const StencilShape& sh : cands) {
+        for (int w = 0; w < 2; ++w) SGN_CUDA(run(sh));
+        SGN_CUDA(cudaEventRecord(c->ev_k0, st));
+        for (int r = 0; r < 3; ++r) SGN_CUDA(run(sh));
+        SGN_CUDA(cudaEventRecord(c->ev_k1, st));
+        SGN_CUDA(cudaEventSynchronize(c->ev_k1));
+        float ms = 0;
+        SGN_CUDA(cudaEventElapsedTime(&ms, c->ev_k0, c->ev_k1));
+        if (ms < best) {
+            best = ms;
+            pick = sh;
+        }
+    }
+    g_launches = l0;  // tuning launches are not part of the solve
+    c->shapes[key] = pick;
+    static const bool dbg = [] {
+        const char* s = getenv("SGN_DEBUG");
+        return s && s[0] == '1';
+    }();
+    if (dbg) fprintf(stderr, "[sgn tune] stencil prec %d ncol %d -> sx %d rb %d (%.3f ms / 3)\n", prec, ncol, pick.sx, pick.rb, best);
+    return SGN_OK;
 }
 
 namespace {
@@ -174,11 +234,13 @@ struct Timer {
             E.tev.push_back(ev);
         }
         E.tmarks.emplace_back(cls, bytes);
-        return cudaEventRecord(E.tev[2 * idx], st);
+        // external: recorded as an event node of the captured graph (a plain record
+        // inside a capture only orders the stream and records nothing)
+        return cudaEventRecordWithFlags(E.tev[2 * idx], st, cudaEventRecordExternal);
     }
     cudaError_t end() {
         if (!c->timing) return cudaSuccess;
-        return cudaEventRecord(E.tev[2 * idx + 1], st);
+        return cudaEventRecordWithFlags(E.tev[2 * idx + 1], st, cudaEventRecordExternal);
     }
 };
 
@@ -626,6 +688,10 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
     else
         SGN_CUDA(apply_hw64(c, bt, rstart, ncol, adjoint, nullptr, st));  // b~ in FP64
     SGN_CUDA(convert_f64_to_f32(bt, reinterpret_cast<float2*>(E->V), (int64_t)ncol * n, st));
+    const int p32 = c->link_storage == SGN_LINKS_BF16 ? 2 : 1;
+    SGN_CHECK(tune_stencil(c, p32, ncol, E->V, E->t));
+    SGN_CHECK(tune_stencil(c, p32, B, E1->V, E1->t));
+    SGN_CHECK(tune_stencil(c, 0, ncol, bt, t64));
 
     CycleArgs a;
     a.adjoint = adjoint;
@@ -819,6 +885,7 @@ int solve(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int ncol, 
     else
         SGN_CUDA(apply_hw64(c, reinterpret_cast<double2*>(E->V), rstart, ncol, adjoint, nullptr, st));
 
+    SGN_CHECK(tune_stencil(c, 0, ncol, E->V, E->t));
     CycleArgs a;
     a.adjoint = adjoint;
     a.L = Lb;

@@ -239,12 +239,16 @@ __global__ void __launch_bounds__(384) k_hw(typename Field<R>::T* __restrict__ o
 
 template <class R, class LinkT>
 cudaError_t launch(typename Field<R>::T* out, const typename Field<R>::T* in, const LinkT* U, int nrhs,
-                   const StencilParams& p, const int* skip, cudaStream_t st) {
+                   const StencilParams& p, const int* skip, cudaStream_t st, StencilShape sh) {
     if (nrhs <= 0 || p.vol <= 0) return cudaSuccess;
     int rb = nrhs <= 12 ? nrhs : 8;
     int sx = 256 / rb;
     sx = sx < 32 ? 32 : (sx / 32) * 32;
     if (sx * rb > 384) sx = 32;
+    if (sh.sx > 0 && sh.rb > 0 && sh.sx % 32 == 0 && sh.sx * sh.rb <= 384) {
+        sx = sh.sx;
+        rb = sh.rb;
+    }
     dim3 block(sx, rb);
     dim3 grid((unsigned)((p.vol + sx - 1) / sx), (unsigned)((nrhs + rb - 1) / rb));
     k_hw<R, LinkT><<<grid, block, 0, st>>>(out, in, U, nrhs, p, skip);
@@ -255,16 +259,16 @@ cudaError_t launch(typename Field<R>::T* out, const typename Field<R>::T* in, co
 }  // namespace
 
 cudaError_t launch_hw_f64(double2* out, const double2* in, const double2* U, int nrhs, const StencilParams& p,
-                          const int* skip, cudaStream_t st) {
-    return launch<double, double2>(out, in, U, nrhs, p, skip, st);
+                          const int* skip, cudaStream_t st, StencilShape sh) {
+    return launch<double, double2>(out, in, U, nrhs, p, skip, st, sh);
 }
 cudaError_t launch_hw_f32(float2* out, const float2* in, const float2* U, int nrhs, const StencilParams& p,
-                          const int* skip, cudaStream_t st) {
-    return launch<float, float2>(out, in, U, nrhs, p, skip, st);
+                          const int* skip, cudaStream_t st, StencilShape sh) {
+    return launch<float, float2>(out, in, U, nrhs, p, skip, st, sh);
 }
 cudaError_t launch_hw_f32_bf16links(float2* out, const float2* in, const __nv_bfloat162* U, int nrhs,
-                                    const StencilParams& p, const int* skip, cudaStream_t st) {
-    return launch<float, __nv_bfloat162>(out, in, U, nrhs, p, skip, st);
+                                    const StencilParams& p, const int* skip, cudaStream_t st, StencilShape sh) {
+    return launch<float, __nv_bfloat162>(out, in, U, nrhs, p, skip, st, sh);
 }
 
 }  // namespace sgn
