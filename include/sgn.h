@@ -195,6 +195,25 @@ SGN_API int sgn_hw_apply(sgn_ctx* ctx, const void* in, void* out, int nrhs, int 
  * the context's allocator and is kept for later calls. */
 SGN_API int sgn_inner_products(sgn_ctx* ctx, const double* V, int J, const double* w, int nrhs, double* out);
 
+/* The inner products of sgn_inner_products, for callers that cannot allocate
+ * device memory: code running while its stream is being captured into a CUDA
+ * graph, host callbacks, or frameworks that own every device allocation.  (The
+ * paper has no counterpart; this is a deployment variant of the Gram-Schmidt
+ * and projection inner products above.)
+ *   V: J complex128 device fields of n complex numbers each, back to back;
+ *   w: nrhs complex128 device fields; out: DEVICE array of nrhs*J complex128,
+ *   out[c*J + j] = V_j^dag w_c.  n even, 1 <= J <= 64, 1 <= nrhs <= 512.
+ * No context and no allocation: the per-block partial sums live in one fixed
+ * 8 MiB device array inside the library (held on every device that loads the
+ * library until the process exits).  The call is rejected (SGN_ERR_ARG) when
+ * nrhs * J * ceil(n / 1024) * 16 bytes exceeds 8 MiB.  The first call on a device
+ * looks up the array's device address; make that first call before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU (other
+ * streams or threads) race and must be serialised by the caller.  Work is
+ * queued on `stream` (a cudaStream_t); the call does not synchronise. */
+SGN_API int sgn_inner_products_noalloc(const double* V, int J, const double* w, long long n, int nrhs, double* out,
+                                       void* stream);
+
 /* dH_W/dmu applied to nrhs complex128 device fields: out = gamma5 dD_W/dmu in,
  * dD_W/dmu psi(x) = -1/2 [(1 - gamma_t) e^{+mu} U_t(x) psi(x+t) - (1 + gamma_t) e^{-mu} U_t(x-t)^dag psi(x-t)]
  * (only the time hops of D_W(mu) depend on mu, Sec. 1). */

@@ -50,6 +50,7 @@ SIGNATURES = {
     "sgn_apply_shifts": (C.c_int, [P, P, P, P, C.c_int, C.c_int, C.POINTER(Report)]),
     "sgn_hw_apply": (C.c_int, [P, P, P, C.c_int, C.c_int, C.c_int]),
     "sgn_inner_products": (C.c_int, [P, P, C.c_int, P, C.c_int, P]),
+    "sgn_inner_products_noalloc": (C.c_int, [P, C.c_int, P, C.c_longlong, C.c_int, P, P]),
     "sgn_dhw_dmu_apply": (C.c_int, [P, P, P, C.c_int]),
     "sgn_grad_mu": (C.c_int, [P, P, P, C.c_int, P]),
     "sgn_set_kernel_timing": (C.c_int, [P, C.c_int]),
