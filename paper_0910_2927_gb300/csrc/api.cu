@@ -66,6 +66,8 @@ SGN_API int sgn_create(sgn_ctx** out, const int dims[4], sgn_alloc_fn alloc, sgn
     *out = nullptr;
     for (int d = 0; d < 4; ++d)
         if (dims[d] < 2) return fail(SGN_ERR_ARG, "sgn_create: every lattice extent must be >= 2");
+    if ((int64_t)dims[0] * dims[1] * dims[2] * dims[3] >= (int64_t(1) << 27))
+        return fail(SGN_ERR_ARG, "sgn_create: the lattice volume must be below 2^27 sites");
     if ((alloc == nullptr) != (free_ == nullptr))
         return fail(SGN_ERR_ARG, "sgn_create: give both allocator callbacks or neither");
     sgn_ctx* c = new (std::nothrow) sgn_ctx();

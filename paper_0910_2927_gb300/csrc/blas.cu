@@ -94,6 +94,24 @@ struct Ops<float2> {
         a = fmaf(w.w, w.w, a);
         return a;
     }
+    // FP32 results: no FP64 instruction in the inner loops (FP64 runs at 1/64 rate)
+    static __device__ __forceinline__ void dot_acc(float& re, float& im, P v, P w) {
+        re = fmaf(v.x, w.x, re);
+        re = fmaf(v.y, w.y, re);
+        re = fmaf(v.z, w.z, re);
+        re = fmaf(v.w, w.w, re);
+        im = fmaf(v.x, w.y, im);
+        im = fmaf(-v.y, w.x, im);
+        im = fmaf(v.z, w.w, im);
+        im = fmaf(-v.w, w.z, im);
+    }
+    static __device__ __forceinline__ void nrm2_acc(float& a, P w) {
+        a = fmaf(w.x, w.x, a);
+        a = fmaf(w.y, w.y, a);
+        a = fmaf(w.z, w.z, a);
+        a = fmaf(w.w, w.w, a);
+    }
+    static __device__ __forceinline__ P scalf(P v, float f) { return make_float4(v.x * f, v.y * f, v.z * f, v.w * f); }
     static __device__ __forceinline__ void sub_cv(P& w, C c, P v) {
         w.x = fmaf(-c.x, v.x, w.x);
         w.x = fmaf(c.y, v.y, w.x);
@@ -144,6 +162,32 @@ __device__ __forceinline__ double2 warp_sum(double2 v) {
     return v;
 }
 
+// Sum over the 32 lanes of an FP32 value kept as an unevaluated pair (hi, lo)
+// (error-free TwoSum at every level): about FP64 accuracy for the tree at FP32
+// instruction rates (FP64 runs at 1/64 of the FP32 rate on this part).
+__device__ __forceinline__ float2 warp_sum_pair(float v) {
+    float hi = v, lo = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float olo = __shfl_xor_sync(0xffffffffu, lo, o);
+        const float s = __fadd_rn(hi, ohi);
+        const float bp = __fadd_rn(s, -hi);
+        const float e = __fadd_rn(__fadd_rn(hi, -__fadd_rn(s, -bp)), __fadd_rn(ohi, -bp));
+        const float t = __fadd_rn(e, __fadd_rn(lo, olo));
+        hi = __fadd_rn(s, t);
+        lo = __fadd_rn(t, -__fadd_rn(hi, s));
+    }
+    return make_float2(hi, lo);
+}
+// Warp sums of a per-thread FP32 complex partial (re, im); lane 0 stores the
+// FP64 result in sm[slot][warp].
+__device__ __forceinline__ void warp_store_f(double2 (*sm)[NWARP], int slot, float re, float im, int lane, int warp) {
+    const float2 r = warp_sum_pair(re);
+    const float2 i = warp_sum_pair(im);
+    if (lane == 0) sm[slot][warp] = make_double2((double)r.x + (double)r.y, (double)i.x + (double)i.y);
+}
+
 // Store the per-warp values sm[slot][warp] summed over warps into the partials.
 __device__ __forceinline__ void flush_partials(double2 (*sm)[NWARP], int nslot, const Reduce& rd, int col) {
     __syncthreads();
@@ -177,36 +221,38 @@ __global__ void __launch_bounds__(NT) k_mdot(Basis<T> V, int J, const T* __restr
     const T* vb = V.base + col * V.sr;
     for (int j = 0; j < J; ++j) {
         const T* vj = vb + j * V.sj;
-        double2 acc;
         if constexpr (O::CPX == 2) {
-            float ax = 0.f, ay = 0.f;  // FP32 chunk of PK packs
+            float ax = 0.f, ay = 0.f;  // FP32 chunk of PK packs (8 complex products)
 #pragma unroll
             for (int p = 0; p < PK; ++p) {
                 int64_t i = base + p * NT;
-                if (i < npk) {
-                    double2 d = O::dot(O::ld_ro(vj, i), wv[p]);
-                    ax += (float)d.x;
-                    ay += (float)d.y;
-                }
+                if (i < npk) O::dot_acc(ax, ay, O::ld_ro(vj, i), wv[p]);
             }
-            acc = make_double2(ax, ay);
+            warp_store_f(sm, j, ax, ay, lane, warp);
         } else {
-            acc = make_double2(0, 0);
+            double2 acc = make_double2(0, 0);
 #pragma unroll
             for (int p = 0; p < PK; ++p) {
                 int64_t i = base + p * NT;
                 if (i < npk) acc = cadd(acc, O::dot(O::ld_ro(vj, i), wv[p]));
             }
+            acc = warp_sum(acc);
+            if (lane == 0) sm[j][warp] = acc;
         }
-        acc = warp_sum(acc);
-        if (lane == 0) sm[j][warp] = acc;
     }
     if (with_norm) {
-        double a = 0;
+        if constexpr (O::CPX == 2) {
+            float a = 0.f;
 #pragma unroll
-        for (int p = 0; p < PK; ++p) a += O::nrm2(wv[p]);
-        double2 acc = warp_sum(make_double2(a, 0));
-        if (lane == 0) sm[J][warp] = acc;
+            for (int p = 0; p < PK; ++p) O::nrm2_acc(a, wv[p]);
+            warp_store_f(sm, J, a, 0.f, lane, warp);
+        } else {
+            double a = 0;
+#pragma unroll
+            for (int p = 0; p < PK; ++p) a += O::nrm2(wv[p]);
+            double2 acc = warp_sum(make_double2(a, 0));
+            if (lane == 0) sm[J][warp] = acc;
+        }
     }
     flush_partials(sm, J + (with_norm ? 1 : 0), rd, col);
 }
@@ -249,31 +295,31 @@ __global__ void __launch_bounds__(NT) k_maxpy_mdot(Basis<T> V, int J, const doub
     }
     for (int j = 0; j < J; ++j) {
         const T* vj = vb + j * V.sj;
-        double2 acc;
         if constexpr (O::CPX == 2) {
             float ax = 0.f, ay = 0.f;
 #pragma unroll
             for (int p = 0; p < PK; ++p) {
                 int64_t i = base + p * NT;
-                if (i < npk) {
-                    double2 d = O::dot(O::ld_ro(vj, i), wv[p]);
-                    ax += (float)d.x;
-                    ay += (float)d.y;
-                }
+                if (i < npk) O::dot_acc(ax, ay, O::ld_ro(vj, i), wv[p]);
             }
-            acc = make_double2(ax, ay);
+            warp_store_f(sm, j, ax, ay, lane, warp);
         } else {
-            acc = make_double2(0, 0);
+            double2 acc = make_double2(0, 0);
 #pragma unroll
             for (int p = 0; p < PK; ++p) {
                 int64_t i = base + p * NT;
                 if (i < npk) acc = cadd(acc, O::dot(O::ld_ro(vj, i), wv[p]));
             }
+            acc = warp_sum(acc);
+            if (lane == 0) sm[j][warp] = acc;
         }
-        acc = warp_sum(acc);
-        if (lane == 0) sm[j][warp] = acc;
     }
-    {
+    if constexpr (O::CPX == 2) {
+        float a = 0.f;
+#pragma unroll
+        for (int p = 0; p < PK; ++p) O::nrm2_acc(a, wv[p]);
+        warp_store_f(sm, J, a, 0.f, lane, warp);
+    } else {
         double a = 0;
 #pragma unroll
         for (int p = 0; p < PK; ++p) a += O::nrm2(wv[p]);
@@ -315,10 +361,19 @@ __global__ void __launch_bounds__(NT) k_maxpy_scale(Basis<T> V, int J, const dou
             if (i < npk) O::sub_cv(wv[p], c, O::ld_ro(vj, i));
         }
     }
+    if constexpr (O::CPX == 2) {
+        const float scf = (float)sc;
 #pragma unroll
-    for (int p = 0; p < PK; ++p) {
-        int64_t i = base + p * NT;
-        if (i < npk) O::st(oc, i, O::scal(wv[p], sc));
+        for (int p = 0; p < PK; ++p) {
+            int64_t i = base + p * NT;
+            if (i < npk) O::st(oc, i, O::scalf(wv[p], scf));
+        }
+    } else {
+#pragma unroll
+        for (int p = 0; p < PK; ++p) {
+            int64_t i = base + p * NT;
+            if (i < npk) O::st(oc, i, O::scal(wv[p], sc));
+        }
     }
 }
 
@@ -418,7 +473,6 @@ __global__ void __launch_bounds__(NT) k_dcgs_dots(Basis<T> V, int J, const T* __
     const T* vb = V.base + col * V.sr;
     for (int l = 0; l < J; ++l) {
         const T* vl = vb + l * V.sj;
-        double2 as, at;
         if constexpr (O::CPX == 2) {
             float sx = 0.f, sy = 0.f, tx = 0.f, ty = 0.f;  // FP32 chunks of PK packs
 #pragma unroll
@@ -426,21 +480,14 @@ __global__ void __launch_bounds__(NT) k_dcgs_dots(Basis<T> V, int J, const T* __
                 int64_t i = base + p * NT;
                 if (i < npk) {
                     typename O::P q = O::ld_ro(vl, i);
-                    double2 d1 = O::dot(q, uv[p]);
-                    sx += (float)d1.x;
-                    sy += (float)d1.y;
-                    if (zc) {
-                        double2 d2 = O::dot(q, zv[p]);
-                        tx += (float)d2.x;
-                        ty += (float)d2.y;
-                    }
+                    O::dot_acc(sx, sy, q, uv[p]);
+                    if (zc) O::dot_acc(tx, ty, q, zv[p]);
                 }
             }
-            as = make_double2(sx, sy);
-            at = make_double2(tx, ty);
+            warp_store_f(sm, l, sx, sy, lane, warp);
+            if (zc) warp_store_f(sm, J + l, tx, ty, lane, warp);
         } else {
-            as = make_double2(0, 0);
-            at = make_double2(0, 0);
+            double2 as = make_double2(0, 0), at = make_double2(0, 0);
 #pragma unroll
             for (int p = 0; p < PK; ++p) {
                 int64_t i = base + p * NT;
@@ -450,34 +497,51 @@ __global__ void __launch_bounds__(NT) k_dcgs_dots(Basis<T> V, int J, const T* __
                     if (zc) at = cadd(at, O::dot(q, zv[p]));
                 }
             }
-        }
-        as = warp_sum(as);
-        if (lane == 0) sm[l][warp] = as;
-        if (zc) {
-            at = warp_sum(at);
-            if (lane == 0) sm[J + l][warp] = at;
+            as = warp_sum(as);
+            if (lane == 0) sm[l][warp] = as;
+            if (zc) {
+                at = warp_sum(at);
+                if (lane == 0) sm[J + l][warp] = at;
+            }
         }
     }
     {
-        double a = 0;
-        double2 bz = make_double2(0, 0);
-        double g = 0;
-#pragma unroll
-        for (int p = 0; p < PK; ++p) {
-            a += O::nrm2(uv[p]);
-            if (zc) {
-                bz = cadd(bz, O::dot(uv[p], zv[p]));
-                g += O::nrm2(zv[p]);
-            }
-        }
         const int base_slot = zc ? 2 * J : J;
-        double2 r = warp_sum(make_double2(a, 0));
-        if (lane == 0) sm[base_slot][warp] = r;
-        if (zc) {
-            r = warp_sum(bz);
-            if (lane == 0) sm[base_slot + 1][warp] = r;
-            r = warp_sum(make_double2(g, 0));
-            if (lane == 0) sm[base_slot + 2][warp] = r;
+        if constexpr (O::CPX == 2) {
+            float a = 0.f, bx = 0.f, by = 0.f, g = 0.f;
+#pragma unroll
+            for (int p = 0; p < PK; ++p) {
+                O::nrm2_acc(a, uv[p]);
+                if (zc) {
+                    O::dot_acc(bx, by, uv[p], zv[p]);
+                    O::nrm2_acc(g, zv[p]);
+                }
+            }
+            warp_store_f(sm, base_slot, a, 0.f, lane, warp);
+            if (zc) {
+                warp_store_f(sm, base_slot + 1, bx, by, lane, warp);
+                warp_store_f(sm, base_slot + 2, g, 0.f, lane, warp);
+            }
+        } else {
+            double a = 0;
+            double2 bz = make_double2(0, 0);
+            double g = 0;
+#pragma unroll
+            for (int p = 0; p < PK; ++p) {
+                a += O::nrm2(uv[p]);
+                if (zc) {
+                    bz = cadd(bz, O::dot(uv[p], zv[p]));
+                    g += O::nrm2(zv[p]);
+                }
+            }
+            double2 r = warp_sum(make_double2(a, 0));
+            if (lane == 0) sm[base_slot][warp] = r;
+            if (zc) {
+                r = warp_sum(bz);
+                if (lane == 0) sm[base_slot + 1][warp] = r;
+                r = warp_sum(make_double2(g, 0));
+                if (lane == 0) sm[base_slot + 2][warp] = r;
+            }
         }
     }
     flush_partials(sm, zc ? 2 * J + 3 : J + 1, rd, col);
@@ -507,6 +571,7 @@ __global__ void __launch_bounds__(NT) k_dcgs_update(Basis<T> V, int J, const dou
     }
     __syncthreads();
     const double inv_rho = ex[0][0];
+    const float inv_rho_f = (float)inv_rho;
     const typename O::C dd = O::coef(make_double2(ex[1][0], ex[1][1]));
     T* uc = u + col * wsr;
     const T* zc = next ? z + col * wsr : nullptr;
@@ -532,10 +597,20 @@ __global__ void __launch_bounds__(NT) k_dcgs_update(Basis<T> V, int J, const dou
             one = make_float2(1.0f, 0.0f);
         }
         O::sub_cv(uv, one, qs);
-        typename O::P qj = O::scal(uv, inv_rho);
+        typename O::P qj;
+        if constexpr (O::CPX == 2) {
+            qj = O::scalf(uv, inv_rho_f);
+        } else {
+            qj = O::scal(uv, inv_rho);
+        }
         O::st(uc, i, qj);
         if (nc) {
-            typename O::P nv = O::scal(O::ld(zc, i), inv_rho);
+            typename O::P nv;
+            if constexpr (O::CPX == 2) {
+                nv = O::scalf(O::ld(zc, i), inv_rho_f);
+            } else {
+                nv = O::scal(O::ld(zc, i), inv_rho);
+            }
             O::sub_cv(nv, one, qc);
             O::sub_cv(nv, dd, qj);
             O::st(nc, i, nv);
@@ -743,20 +818,23 @@ __global__ void __launch_bounds__(NT) k_axpby3(T* __restrict__ out, double a, co
                                                const T* __restrict__ y, double c, const T* __restrict__ z,
                                                int64_t npk) {
     using O = Ops<T>;
+    const float af = (float)a, bf = (float)b, cf = (float)c;  // FP32 path: convert once
     for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < npk; i += (int64_t)gridDim.x * NT) {
-        typename O::P v = O::scal(O::ld(x, i), a);
-        typename O::P w = O::scal(O::ld(y, i), b);
         typename O::P r;
         if constexpr (O::CPX == 1) {
+            typename O::P v = O::scal(O::ld(x, i), a);
+            typename O::P w = O::scal(O::ld(y, i), b);
             r = make_double2(v.x + w.x, v.y + w.y);
-        } else {
-            r = make_float4(v.x + w.x, v.y + w.y, v.z + w.z, v.w + w.w);
-        }
-        if (z) {
-            typename O::P u = O::scal(O::ld(z, i), c);
-            if constexpr (O::CPX == 1) {
+            if (z) {
+                typename O::P u = O::scal(O::ld(z, i), c);
                 r = make_double2(r.x + u.x, r.y + u.y);
-            } else {
+            }
+        } else {
+            typename O::P v = O::scalf(O::ld(x, i), af);
+            typename O::P w = O::scalf(O::ld(y, i), bf);
+            r = make_float4(v.x + w.x, v.y + w.y, v.z + w.z, v.w + w.w);
+            if (z) {
+                typename O::P u = O::scalf(O::ld(z, i), cf);
                 r = make_float4(r.x + u.x, r.y + u.y, r.z + u.z, r.w + u.w);
             }
         }

@@ -112,6 +112,7 @@ struct sgn_ctx {
 namespace sgn {
 
 StencilParams stencil_params(const sgn_ctx* c, bool adjoint);
+void fill_fp32_coefficients(StencilParams& p);
 // H_W applied in FP64 / FP32 to ncol fields (skip may be null).
 cudaError_t apply_hw64(const sgn_ctx* c, double2* out, const double2* in, int ncol, bool adjoint, const int* skip,
                        cudaStream_t st);

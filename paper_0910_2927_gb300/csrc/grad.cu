@@ -18,6 +18,7 @@ cudaError_t apply_dhw_dmu64(const sgn_ctx* c, double2* out, const double2* in, i
     }
     p.cf[3] = -0.5 * std::exp(c->mu);  // d/dmu of -1/2 e^{+mu}
     p.cb[3] = 0.5 * std::exp(-c->mu);  // d/dmu of -1/2 e^{-mu}
+    fill_fp32_coefficients(p);
     return launch_hw_f64(out, in, reinterpret_cast<const double2*>(c->U64.p), ncol, p, nullptr, st);
 }
 

@@ -44,6 +44,23 @@ __host__ __device__ inline double2 cadd(double2 a, double2 b) { return make_doub
 __host__ __device__ inline double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __host__ __device__ inline double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
 
+// Exact division of n < 2^27 by a fixed d >= 1 with one 64-bit multiply and a
+// shift: M = floor(2^(32+s) / d) + 1, 2^s >= d.  The error n (M - 2^(32+s)/d) /
+// 2^(32+s) < 2^27 / 2^(32+s) <= 1/(32 d) never crosses an integer.
+struct FastDiv {
+    uint32_t d = 1;
+    int sh = 32;
+    uint64_t M = (uint64_t(1) << 32) + 1;
+    FastDiv() = default;
+    explicit FastDiv(uint32_t div) : d(div) {
+        int s = 0;
+        while ((1u << s) < div) ++s;
+        sh = 32 + s;
+        M = (uint64_t(1) << sh) / div + 1;
+    }
+    __host__ __device__ __forceinline__ uint32_t div(uint32_t n) const { return (uint32_t)(((uint64_t)n * M) >> sh); }
+};
+
 // Lattice geometry and operator parameters passed by value to the stencil.
 struct StencilParams {
     int L[4];          // Lx, Ly, Lz, Lt
@@ -53,6 +70,11 @@ struct StencilParams {
     double cf[4];      // forward hop coefficient -1/2 e^{+mu d_nu,t}
     double cb[4];      // backward hop coefficient -1/2 e^{-mu d_nu,t}
     int ap[4];         // antiperiodic flags
+    // the same coefficients in FP32 for the FP32 stencil (no FP64 conversion in the kernel)
+    float diag32;
+    float cf32[4];
+    float cb32[4];
+    FastDiv div[3];    // by Lx, Ly, Lz (site < 2^27)
 };
 
 // ---------------------------------------------------------- kernel entry --

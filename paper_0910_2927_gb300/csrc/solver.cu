@@ -55,6 +55,15 @@ void dev_free(sgn_ctx* c, DevBuf& b) {
     b.bytes = 0;
 }
 
+void fill_fp32_coefficients(StencilParams& p) {
+    for (int d = 0; d < 3; ++d) p.div[d] = FastDiv((uint32_t)p.L[d]);
+    p.diag32 = (float)p.diag;
+    for (int d = 0; d < 4; ++d) {
+        p.cf32[d] = (float)p.cf[d];
+        p.cb32[d] = (float)p.cb[d];
+    }
+}
+
 StencilParams stencil_params(const sgn_ctx* c, bool adjoint) {
     StencilParams p{};
     for (int d = 0; d < 4; ++d) {
@@ -69,6 +78,7 @@ StencilParams stencil_params(const sgn_ctx* c, bool adjoint) {
     p.vol = c->vol;
     p.stride_rhs = c->n;
     p.diag = 4.0 + c->mass;
+    fill_fp32_coefficients(p);
     return p;
 }
 
@@ -631,10 +641,12 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
     size_t o_r0 = take(field * ncol), o_bt = take(field * ncol), o_xp = take(field * ncol);
     size_t o_t = take(field * ncol), o_u = take(field * ncol);
     size_t o_d = take(field * B);
+    size_t o_rs = take(field * ncol * s);
+    const int ncmax = std::max({ncol, B, s * ncol});
     size_t o_om = take(sizeof(double2) * ncol * rs64);
-    size_t o_red = take(sizeof(double2) * ncol * rs64);
-    size_t o_part = take(sizeof(double2) * (size_t)std::max(ncol, B) * rs64 * nblk64);
-    size_t o_flags = take(sizeof(int) * 2 * std::max(ncol, B));
+    size_t o_red = take(sizeof(double2) * ncmax * rs64);
+    size_t o_part = take(sizeof(double2) * (size_t)ncmax * rs64 * nblk64);
+    size_t o_flags = take(sizeof(int) * 2 * ncmax);
     SGN_CHECK(ensure_io(c, off));
     char* io = reinterpret_cast<char*>(c->io.p);
     double2* xs = reinterpret_cast<double2*>(io + o_xs);
@@ -644,15 +656,16 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
     double2* t64 = reinterpret_cast<double2*>(io + o_t);
     double2* u64 = reinterpret_cast<double2*>(io + o_u);
     double2* d = reinterpret_cast<double2*>(io + o_d);
+    double2* rsd = reinterpret_cast<double2*>(io + o_rs);  // true residuals r_i, [i][col][n]
     double2* omtab = reinterpret_cast<double2*>(io + o_om);
     // FP64 reductions use their own partials and state (the FP32 engines size theirs for float packs)
     DevState S64{};
     S64.red = reinterpret_cast<double2*>(io + o_red);
     S64.skip = reinterpret_cast<int*>(io + o_flags);
-    S64.done = S64.skip + std::max(ncol, B);
+    S64.done = S64.skip + ncmax;
     S64.rstride = rs64;
     const Reduce rd64{reinterpret_cast<double2*>(io + o_part), nblk64, rs64};
-    SGN_CUDA(cudaMemsetAsync(S64.skip, 0, sizeof(int) * 2 * std::max(ncol, B), st));
+    SGN_CUDA(cudaMemsetAsync(S64.skip, 0, sizeof(int) * 2 * ncmax, st));
 
     std::vector<double> sig_cols((size_t)ncol * s), om_cols((size_t)ncol * s);
     std::vector<double2> omh((size_t)ncol * rs64, make_double2(0, 0));
@@ -731,25 +744,28 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
     a1.xs_shift = (int64_t)B * n;
     a1.xs_col = n;
     const int max_rounds = 8;
-    std::vector<double2> hres((size_t)ncol * rs64);
     std::vector<double> sig1(B), om1(B, 1.0);
+    const int nall = s * ncol;  // every (shift, column) pair as one column of [i][col][n]
+    std::vector<double2> hall((size_t)nall * rs64);
     for (int round = 0; round <= max_rounds; ++round) {
-        // true residuals r_i = b~ - (A^2 - sigma_i) x_i, projected, in xs-shaped staging one shift at a time
-        std::vector<std::pair<int, int>> todo;  // (shift, column)
-        worst = 0;
+        // true residuals r_i = b~ - (A^2 - sigma_i) x_i of every shifted system (FP64)
         for (int i = 0; i < s; ++i) {
             double2* xi = xs + (size_t)i * ncol * n;
             SGN_CUDA(apply_hw64(c, t64, xi, ncol, adjoint, nullptr, st));
             SGN_CUDA(apply_hw64(c, u64, t64, ncol, adjoint, nullptr, st));
-            // t64 <- b~ - u + sigma_i x_i
-            SGN_CUDA(axpby3<double2>(t64, 1.0, bt, -1.0, u64, c->sigma[i], xi, (int64_t)ncol * n, st));
-            SGN_CUDA(mdot<double2>(Basis<double2>{t64, 0, n}, 0, t64, n, n, ncol, rd64, 1, nullptr, st));
-            SGN_CUDA(reduce(rd64, 1, ncol, RM_STORE, 0, S64, nullptr, st));
-            SGN_CUDA(cudaMemcpyAsync(hres.data(), S64.red, sizeof(double2) * hres.size(), cudaMemcpyDeviceToHost,
-                                     st));
-            SGN_CUDA(cudaStreamSynchronize(st));
+            SGN_CUDA(axpby3<double2>(rsd + (size_t)i * ncol * n, 1.0, bt, -1.0, u64, c->sigma[i], xi,
+                                     (int64_t)ncol * n, st));
+        }
+        SGN_CUDA(mdot<double2>(Basis<double2>{rsd, 0, n}, 0, rsd, n, n, nall, rd64, 1, nullptr, st));
+        SGN_CUDA(reduce(rd64, 1, nall, RM_STORE, 0, S64, nullptr, st));
+        SGN_CUDA(cudaMemcpyAsync(hall.data(), S64.red, sizeof(double2) * hall.size(), cudaMemcpyDeviceToHost, st));
+        SGN_CUDA(cudaStreamSynchronize(st));
+        std::vector<std::pair<int, int>> todo;  // (shift, column)
+        worst = 0;
+        for (int i = 0; i < s; ++i)
             for (int col = 0; col < ncol; ++col) {
-                double rel = bnorm[col] > 0 ? std::sqrt(hres[(size_t)col * rs64].x) / bnorm[col] : 0.0;
+                const double r2 = hall[((size_t)i * ncol + col) * rs64].x;
+                const double rel = bnorm[col] > 0 ? std::sqrt(r2) / bnorm[col] : 0.0;
                 if (!std::isfinite(rel)) {
                     set_error("non-finite true residual in refinement");
                     return SGN_ERR_NONFINITE;
@@ -757,10 +773,30 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
                 worst = std::max(worst, rel);
                 if (rel > c->tol) todo.emplace_back(i, col);
             }
-        }
         if (todo.empty() || round == max_rounds) break;
         ++ref_rounds;
-        // correction solves, B systems at a time
+        if (m > 0) {
+            // the range(P) part of each residual is solved exactly in the eigenbasis,
+            // (A^2 - sigma)^{-1} R = R (Lambda^2 - sigma)^{-1}:  x_i += R (Lambda^2 - sigma_i)^{-1} L^dag r_i,
+            // and the Krylov corrections work on (I - P) r_i.  One launch each for all pairs.
+            SGN_CUDA(mdot<double2>(LB, m, rsd, n, n, nall, rd64, 0, nullptr, st));
+            SGN_CUDA(reduce(rd64, m, nall, RM_STORE, 0, S64, nullptr, st));
+            SGN_CUDA(maxpy_scale<double2>(RB, m, S64.red, rs64, rsd, n, rsd, n, nullptr, n, nall, nullptr, st));
+            SGN_CUDA(cudaMemcpyAsync(hall.data(), S64.red, sizeof(double2) * hall.size(), cudaMemcpyDeviceToHost, st));
+            SGN_CUDA(cudaStreamSynchronize(st));
+            for (int i = 0; i < s; ++i)
+                for (int col = 0; col < ncol; ++col)
+                    for (int l = 0; l < m; ++l) {
+                        double2& v = hall[((size_t)i * ncol + col) * rs64 + l];
+                        const std::complex<double> lj = adjoint ? std::conj(c->lam[l]) : c->lam[l];
+                        const std::complex<double> q = std::complex<double>(v.x, v.y) / (lj * lj - c->sigma[i]);
+                        v = make_double2(q.real(), q.imag());
+                    }
+            SGN_CUDA(cudaMemcpyAsync(S64.red, hall.data(), sizeof(double2) * hall.size(), cudaMemcpyHostToDevice, st));
+            SGN_CUDA(update_x<double2>(RB, m, S64.red, rs64, xs, n, n, nall, nullptr, nullptr, st));
+            SGN_CUDA(cudaStreamSynchronize(st));
+        }
+        // correction solves, B systems at a time, one system per column
         for (size_t t0 = 0; t0 < todo.size(); t0 += B) {
             const int nb = (int)std::min<size_t>(B, todo.size() - t0);
             float2* V0 = reinterpret_cast<float2*>(E1->V);
@@ -769,30 +805,7 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
             SGN_CHECK(fill_shift_tables(c, *E1, sig1.data(), om1.data()));
             for (int j = 0; j < nb; ++j) {
                 const int i = todo[t0 + j].first, col = todo[t0 + j].second;
-                double2* xi = xs + ((size_t)i * ncol + col) * n;
-                SGN_CUDA(apply_hw64(c, t64, xi, 1, adjoint, nullptr, st));
-                SGN_CUDA(apply_hw64(c, u64, t64, 1, adjoint, nullptr, st));
-                SGN_CUDA(axpby3<double2>(t64, 1.0, bt + (size_t)col * n, -1.0, u64, c->sigma[i], xi, n, st));
-                if (m > 0) {
-                    // the range(P) part of the residual is solved exactly in the eigenbasis,
-                    // (A^2 - sigma)^{-1} R = R (Lambda^2 - sigma)^{-1}: x_i += R (Lambda^2 - sigma_i)^{-1} L^dag r_i;
-                    // the Krylov correction then works on (I - P) r_i
-                    SGN_CUDA(mdot<double2>(LB, m, t64, n, n, 1, rd64, 0, nullptr, st));
-                    SGN_CUDA(reduce(rd64, m, 1, RM_STORE, 0, S64, nullptr, st));
-                    SGN_CUDA(maxpy_scale<double2>(RB, m, S64.red, rs64, t64, n, t64, n, nullptr, n, 1, nullptr, st));
-                    std::vector<double2> cp(m);
-                    SGN_CUDA(cudaMemcpyAsync(cp.data(), S64.red, sizeof(double2) * m, cudaMemcpyDeviceToHost, st));
-                    SGN_CUDA(cudaStreamSynchronize(st));
-                    for (int l = 0; l < m; ++l) {
-                        std::complex<double> lj = adjoint ? std::conj(c->lam[l]) : c->lam[l];
-                        std::complex<double> q = std::complex<double>(cp[l].x, cp[l].y) / (lj * lj - c->sigma[i]);
-                        cp[l] = make_double2(q.real(), q.imag());
-                    }
-                    SGN_CUDA(cudaMemcpyAsync(S64.red, cp.data(), sizeof(double2) * m, cudaMemcpyHostToDevice, st));
-                    SGN_CUDA(update_x<double2>(RB, m, S64.red, rs64, xi, n, n, 1, nullptr, nullptr, st));
-                    SGN_CUDA(cudaStreamSynchronize(st));
-                }
-                SGN_CUDA(convert_f64_to_f32(t64, V0 + (size_t)j * n, n, st));
+                SGN_CUDA(convert_f64_to_f32(rsd + ((size_t)i * ncol + col) * n, V0 + (size_t)j * n, n, st));
             }
             SGN_CUDA(cudaMemsetAsync(d, 0, field * B, st));
             RunResult r1;

@@ -175,6 +175,19 @@ __device__ __forceinline__ void hop(Cx<R> acc[12], const typename Field<R>::T* _
     }
 }
 
+template <class R>
+__device__ __forceinline__ R cf_of(const StencilParams& P, int nu) {
+    if constexpr (sizeof(R) == 4) return P.cf32[nu]; else return P.cf[nu];
+}
+template <class R>
+__device__ __forceinline__ R cb_of(const StencilParams& P, int nu) {
+    if constexpr (sizeof(R) == 4) return P.cb32[nu]; else return P.cb[nu];
+}
+template <class R>
+__device__ __forceinline__ R diag_of(const StencilParams& P) {
+    if constexpr (sizeof(R) == 4) return P.diag32; else return P.diag;
+}
+
 template <class R, class LinkT, int NU>
 __device__ __forceinline__ void both_hops(Cx<R> acc[12], const typename Field<R>::T* __restrict__ in,
                                           const LinkT* __restrict__ U, int64_t site, const int co[4],
@@ -185,13 +198,13 @@ __device__ __forceinline__ void both_hops(Cx<R> acc[12], const typename Field<R>
     const int L = P.L[NU];
     // forward neighbour
     int64_t fw = site + stride;
-    R cf = R(P.cf[NU]);
+    R cf = cf_of<R>(P, NU);
     if (co[NU] == L - 1) {
         fw = site - (int64_t)(L - 1) * stride;
         if (P.ap[NU]) cf = -cf;
     }
     int64_t bw = site - stride;
-    R cb = R(P.cb[NU]);
+    R cb = cb_of<R>(P, NU);
     if (co[NU] == 0) {
         bw = site + (int64_t)(L - 1) * stride;
         if (P.ap[NU]) cb = -cb;
@@ -212,18 +225,20 @@ __global__ void __launch_bounds__(384) k_hw(typename Field<R>::T* __restrict__ o
     const typename Field<R>::T* fin = in + rhs * P.stride_rhs;
     int co[4];
     {
-        int64_t r = site;
-        co[0] = (int)(r % P.L[0]);
-        r /= P.L[0];
-        co[1] = (int)(r % P.L[1]);
-        r /= P.L[1];
-        co[2] = (int)(r % P.L[2]);
-        co[3] = (int)(r / P.L[2]);
+        // coordinates by exact multiply-shift division (no 64-bit integer division)
+        const uint32_t s0 = (uint32_t)site;
+        const uint32_t q0 = P.div[0].div(s0);
+        co[0] = (int)(s0 - q0 * (uint32_t)P.L[0]);
+        const uint32_t q1 = P.div[1].div(q0);
+        co[1] = (int)(q0 - q1 * (uint32_t)P.L[1]);
+        const uint32_t q2 = P.div[2].div(q1);
+        co[2] = (int)(q1 - q2 * (uint32_t)P.L[2]);
+        co[3] = (int)q2;
     }
     Cx<R> acc[12];
     {
         Field<R>::load(fin, site, acc);
-        const R d = R(P.diag);
+        const R d = diag_of<R>(P);
 #pragma unroll
         for (int k = 0; k < 12; ++k) acc[k] = scale(acc[k], d);
     }
