@@ -171,15 +171,49 @@ __device__ __forceinline__ float2 warp_sum_pair(float v) {
     for (int o = 16; o > 0; o >>= 1) {
         const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
         const float olo = __shfl_xor_sync(0xffffffffu, lo, o);
+        // TwoSum(hi, ohi) = (s, e) exactly, then FastTwoSum(s, e + lo + olo).  Written
+        // with __fsub_rn: the same algebra spelled as __fadd_rn(x, -__fadd_rn(..))
+        // was measured to lose the error term on this toolchain.
         const float s = __fadd_rn(hi, ohi);
-        const float bp = __fadd_rn(s, -hi);
-        const float e = __fadd_rn(__fadd_rn(hi, -__fadd_rn(s, -bp)), __fadd_rn(ohi, -bp));
+        const float bp = __fsub_rn(s, hi);
+        const float ap = __fsub_rn(s, bp);
+        const float e = __fadd_rn(__fsub_rn(hi, ap), __fsub_rn(ohi, bp));
         const float t = __fadd_rn(e, __fadd_rn(lo, olo));
-        hi = __fadd_rn(s, t);
-        lo = __fadd_rn(t, -__fadd_rn(hi, s));
+        const float nh = __fadd_rn(s, t);
+        lo = __fsub_rn(t, __fsub_rn(nh, s));
+        hi = nh;
     }
     return make_float2(hi, lo);
 }
+// Double-float sum of the 256 FP32 values st[0..255] (one per thread of the CTA)
+// by one warp: 8 values per lane with TwoSum, then the lane butterfly.
+__device__ __forceinline__ double cta_sum_df(const float* st, int lane) {
+    float hi = 0.f, lo = 0.f;
+#pragma unroll
+    for (int q = 0; q < NT / 32; ++q) {
+        const float v = st[lane + 32 * q];
+        const float s = __fadd_rn(hi, v);
+        const float bp = __fsub_rn(s, hi);
+        const float ap = __fsub_rn(s, bp);
+        lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, ap), __fsub_rn(v, bp)));
+        hi = s;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float olo = __shfl_xor_sync(0xffffffffu, lo, o);
+        const float s = __fadd_rn(hi, ohi);
+        const float bp = __fsub_rn(s, hi);
+        const float ap = __fsub_rn(s, bp);
+        const float e = __fadd_rn(__fsub_rn(hi, ap), __fsub_rn(ohi, bp));
+        const float t = __fadd_rn(e, __fadd_rn(lo, olo));
+        const float nh = __fadd_rn(s, t);
+        lo = __fsub_rn(t, __fsub_rn(nh, s));
+        hi = nh;
+    }
+    return (double)hi + (double)lo;
+}
+
 // Warp sums of a per-thread FP32 complex partial (re, im); lane 0 stores the
 // FP64 result in sm[slot][warp].
 __device__ __forceinline__ void warp_store_f(double2 (*sm)[NWARP], int slot, float re, float im, int lane, int warp) {
@@ -458,7 +492,6 @@ __global__ void __launch_bounds__(NT) k_dcgs_dots(Basis<T> V, int J, const T* __
     using O = Ops<T>;
     const int col = blockIdx.y;
     if (skip && skip[col]) return;
-    __shared__ double2 sm[MAXSLOT][NWARP];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const T* uc = u + col * wsr;
     const T* zc = z ? z + col * wsr : nullptr;
@@ -471,22 +504,83 @@ __global__ void __launch_bounds__(NT) k_dcgs_dots(Basis<T> V, int J, const T* __
         zv[p] = (zc && i < npk) ? O::ld(zc, i) : O::zero();
     }
     const T* vb = V.base + col * V.sr;
-    for (int l = 0; l < J; ++l) {
-        const T* vl = vb + l * V.sj;
-        if constexpr (O::CPX == 2) {
-            float sx = 0.f, sy = 0.f, tx = 0.f, ty = 0.f;  // FP32 chunks of PK packs
+    if constexpr (O::CPX == 2) {
+        // FP32 storage: per-thread FP32 chunk partials are staged in shared memory
+        // for a tile of TL basis vectors; each (vector, component) slot is then summed
+        // over the whole CTA by one warp in double-float and written as this CTA's
+        // FP64 partial.  Four values per vector: Re/Im of q^dag u and of q^dag z.
+        constexpr int TL = 8;
+        __shared__ float st[TL * 4][NT];
+        double* pd = reinterpret_cast<double*>(rd.partial);
+        auto put = [&](int slot, int comp, double v) {
+            pd[2 * (((int64_t)col * rd.stride + slot) * rd.nblk + blockIdx.x) + comp] = v;
+        };
+        const int nv = zc ? 4 : 2;
+        for (int l0 = 0; l0 < J; l0 += TL) {
+            const int tl = (J - l0) < TL ? (J - l0) : TL;
+            for (int g = 0; g < tl; ++g) {
+                const T* vl = vb + (l0 + g) * V.sj;
+                float sx = 0.f, sy = 0.f, tx = 0.f, ty = 0.f;
 #pragma unroll
-            for (int p = 0; p < PK; ++p) {
-                int64_t i = base + p * NT;
-                if (i < npk) {
-                    typename O::P q = O::ld_ro(vl, i);
-                    O::dot_acc(sx, sy, q, uv[p]);
-                    if (zc) O::dot_acc(tx, ty, q, zv[p]);
+                for (int p = 0; p < PK; ++p) {
+                    int64_t i = base + p * NT;
+                    if (i < npk) {
+                        typename O::P q = O::ld_ro(vl, i);
+                        O::dot_acc(sx, sy, q, uv[p]);
+                        if (zc) O::dot_acc(tx, ty, q, zv[p]);
+                    }
+                }
+                st[g * 4 + 0][threadIdx.x] = sx;
+                st[g * 4 + 1][threadIdx.x] = sy;
+                st[g * 4 + 2][threadIdx.x] = tx;
+                st[g * 4 + 3][threadIdx.x] = ty;
+            }
+            __syncthreads();
+            for (int sl = warp; sl < tl * 4; sl += NWARP) {
+                const int g = sl >> 2, v = sl & 3;
+                if (v >= nv) continue;
+                const double r = cta_sum_df(st[sl], lane);
+                if (lane == 0) put(v < 2 ? l0 + g : J + l0 + g, v & 1, r);
+            }
+            __syncthreads();
+        }
+        // norms and u^dag z
+        float a = 0.f, bx = 0.f, by = 0.f, gz = 0.f;
+#pragma unroll
+        for (int p = 0; p < PK; ++p) {
+            O::nrm2_acc(a, uv[p]);
+            if (zc) {
+                O::dot_acc(bx, by, uv[p], zv[p]);
+                O::nrm2_acc(gz, zv[p]);
+            }
+        }
+        st[0][threadIdx.x] = a;
+        st[1][threadIdx.x] = bx;
+        st[2][threadIdx.x] = by;
+        st[3][threadIdx.x] = gz;
+        __syncthreads();
+        const int bs = zc ? 2 * J : J;
+        if (warp < (zc ? 4 : 1)) {
+            const double r = cta_sum_df(st[warp], lane);
+            if (lane == 0) {
+                if (warp == 0) {
+                    put(bs, 0, r);
+                    put(bs, 1, 0.0);
+                } else if (warp == 1) {
+                    put(bs + 1, 0, r);
+                } else if (warp == 2) {
+                    put(bs + 1, 1, r);
+                } else {
+                    put(bs + 2, 0, r);
+                    put(bs + 2, 1, 0.0);
                 }
             }
-            warp_store_f(sm, l, sx, sy, lane, warp);
-            if (zc) warp_store_f(sm, J + l, tx, ty, lane, warp);
-        } else {
+        }
+        return;
+    } else {
+        __shared__ double2 sm[MAXSLOT][NWARP];
+        for (int l = 0; l < J; ++l) {
+            const T* vl = vb + l * V.sj;
             double2 as = make_double2(0, 0), at = make_double2(0, 0);
 #pragma unroll
             for (int p = 0; p < PK; ++p) {
@@ -504,47 +598,28 @@ __global__ void __launch_bounds__(NT) k_dcgs_dots(Basis<T> V, int J, const T* __
                 if (lane == 0) sm[J + l][warp] = at;
             }
         }
-    }
-    {
         const int base_slot = zc ? 2 * J : J;
-        if constexpr (O::CPX == 2) {
-            float a = 0.f, bx = 0.f, by = 0.f, g = 0.f;
+        double a = 0;
+        double2 bz = make_double2(0, 0);
+        double g = 0;
 #pragma unroll
-            for (int p = 0; p < PK; ++p) {
-                O::nrm2_acc(a, uv[p]);
-                if (zc) {
-                    O::dot_acc(bx, by, uv[p], zv[p]);
-                    O::nrm2_acc(g, zv[p]);
-                }
-            }
-            warp_store_f(sm, base_slot, a, 0.f, lane, warp);
+        for (int p = 0; p < PK; ++p) {
+            a += O::nrm2(uv[p]);
             if (zc) {
-                warp_store_f(sm, base_slot + 1, bx, by, lane, warp);
-                warp_store_f(sm, base_slot + 2, g, 0.f, lane, warp);
-            }
-        } else {
-            double a = 0;
-            double2 bz = make_double2(0, 0);
-            double g = 0;
-#pragma unroll
-            for (int p = 0; p < PK; ++p) {
-                a += O::nrm2(uv[p]);
-                if (zc) {
-                    bz = cadd(bz, O::dot(uv[p], zv[p]));
-                    g += O::nrm2(zv[p]);
-                }
-            }
-            double2 r = warp_sum(make_double2(a, 0));
-            if (lane == 0) sm[base_slot][warp] = r;
-            if (zc) {
-                r = warp_sum(bz);
-                if (lane == 0) sm[base_slot + 1][warp] = r;
-                r = warp_sum(make_double2(g, 0));
-                if (lane == 0) sm[base_slot + 2][warp] = r;
+                bz = cadd(bz, O::dot(uv[p], zv[p]));
+                g += O::nrm2(zv[p]);
             }
         }
+        double2 r = warp_sum(make_double2(a, 0));
+        if (lane == 0) sm[base_slot][warp] = r;
+        if (zc) {
+            r = warp_sum(bz);
+            if (lane == 0) sm[base_slot + 1][warp] = r;
+            r = warp_sum(make_double2(g, 0));
+            if (lane == 0) sm[base_slot + 2][warp] = r;
+        }
+        flush_partials(sm, zc ? 2 * J + 3 : J + 1, rd, col);
     }
-    flush_partials(sm, zc ? 2 * J + 3 : J + 1, rd, col);
 }
 
 // Delayed CGS2, update of step j:  q_j = (u - Q s) / rho  (written over u), and

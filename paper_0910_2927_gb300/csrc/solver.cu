@@ -109,6 +109,14 @@ cudaError_t apply_hw32(const sgn_ctx* c, float2* out, const float2* in, int ncol
 int tune_stencil(sgn_ctx* c, int prec, int ncol, void* in, void* out) {
     const int key = prec * 4096 + ncol;
     if (c->shapes.count(key)) return SGN_OK;
+    static const bool off = [] {
+        const char* s = getenv("SGN_NO_TUNE");
+        return s && s[0] == '1';
+    }();
+    if (off) {
+        c->shapes[key] = StencilShape{};
+        return SGN_OK;
+    }
     cudaStream_t st = c->work;
     const StencilParams p = stencil_params(c, false);
     std::vector<StencilShape> cands;
@@ -253,6 +261,14 @@ struct Timer {
         return cudaEventRecordWithFlags(E.tev[2 * idx + 1], st, cudaEventRecordExternal);
     }
 };
+
+bool debug_log() {
+    static const bool v = [] {
+        const char* s = getenv("SGN_DEBUG");
+        return s && s[0] == '1';
+    }();
+    return v;
+}
 
 bool use_cgs2() {
     static const bool v = [] {
@@ -558,6 +574,12 @@ int run_engine(sgn_ctx* c, Engine& E, const CycleArgs& a, double tol, int max_cy
                 c->t_launches[cls] += 1;
                 c->t_bytes[cls] += E.tmarks[i].second;
             }
+        if (debug_log() && (cyc < 30 || cyc % 50 == 0)) {
+            SGN_CUDA(cudaMemcpy(E.h_resest, E.S.resest, ncol * sizeof(double), cudaMemcpyDeviceToHost));
+            double mx = 0;
+            for (int i = 0; i < ncol; ++i) mx = std::max(mx, E.h_resest[i]);
+            fprintf(stderr, "[sgn cycle] %d resmax %.3e\n", cyc, mx);
+        }
         if (*E.h_err) break;
         all_done = true;
         for (int i = 0; i < ncol; ++i) all_done = all_done && E.h_done[i];
@@ -718,6 +740,9 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
     const double tol_inner = std::max(c->tol, 1e-6);
     RunResult rr;
     int status = run_engine<float2>(c, *E, a, tol_inner, c->max_cycles, &rr);
+    if (debug_log())
+        fprintf(stderr, "[sgn mixed] multishift phase: status %d cycles %d converged %d resmax %.3e err %d\n", status,
+                rr.cycles, rr.converged, rr.resmax, rr.err);
     if (status != SGN_OK) return status;
     const int ms_cycles = rr.cycles;
     int ref_rounds = 0, ref_cycles = 0;
@@ -773,6 +798,9 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
                 worst = std::max(worst, rel);
                 if (rel > c->tol) todo.emplace_back(i, col);
             }
+        if (debug_log())
+            fprintf(stderr, "[sgn mixed] round %d: worst true residual %.3e, %zu of %d systems above tol\n", round,
+                    worst, todo.size(), nall);
         if (todo.empty() || round == max_rounds) break;
         ++ref_rounds;
         if (m > 0) {
@@ -810,6 +838,9 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
             SGN_CUDA(cudaMemsetAsync(d, 0, field * B, st));
             RunResult r1;
             int st1 = run_engine<float2>(c, *E1, a1, std::max(c->tol, 1e-5), c->max_cycles, &r1);
+            if (debug_log())
+                fprintf(stderr, "[sgn mixed]   batch at %zu (%d systems): status %d cycles %d resmax %.3e\n", t0, nb,
+                        st1, r1.cycles, r1.resmax);
             if (st1 != SGN_OK) return st1;
             ref_cycles += r1.cycles;
             for (int j = 0; j < nb; ++j) {
