@@ -4,8 +4,14 @@
 //
 // Right eigenvectors: the m + extra eigenvalues of smallest |lambda|.  They are
 // the eigenvalues of A^2 of smallest modulus, i.e. the low end of the
-// spectrum of A^2, which a Chebyshev polynomial in A^2 on [a, b] amplifies
-// (b bounds |lambda|^2 from above, a is the top of the current block).  Block
+// spectrum of A^2, which a Chebyshev polynomial in A^2 amplifies.  For mu > 0
+// A is not Hermitian and the eigenvalues of A^2 leave the real axis (|Im| of
+// order 2 |lambda| |Im lambda|, about 1 at mu = 0.3), so the polynomial is the
+// Chebyshev polynomial of an ellipse rather than of the interval [a, b]: real
+// semi-axis (b - a)/2 from a (the top of the current block) to b (a bound of
+// |lambda|^2), imaginary semi-axis beta from a short Arnoldi run on A^2.  On
+// the interval alone the off-axis eigenvalues outgrow the wanted edge once the
+// gap above it is small.  Block
 // subspace iteration with that filter, SVQB orthonormalisation (Gram matrix,
 // Hermitian eigendecomposition, rank-safe inverse square root) and
 // Rayleigh-Ritz with A^2, where the wanted eigenvalues are extremal (with the
@@ -55,6 +61,7 @@ struct Work {
     double2* Cdev = nullptr;   // q x q coefficients
     double2* coef = nullptr;   // q x rstride per-column coefficients
     std::vector<double2> hred;
+    double beta = 0;           // imaginary semi-axis of the filter ellipse
 };
 
 int setup(Work& W, sgn_ctx* c, int q, size_t esz, int nblk) {
@@ -172,7 +179,28 @@ int svqb(Work& W, T* Y, int q, T* tmp, double eps, int* deficient = nullptr) {
     return SGN_OK;
 }
 
-// Chebyshev filter T_d(s(A^2)) Y, s(t) = (2t - (a+b)) / (b - a), in place.
+// Ellipse geometry of the filter: centre c0 = (a + b)/2, real semi-axis
+// al = (b - a)/2, imaginary semi-axis beta < al, foci c0 -+ d, d = sqrt(al^2 - beta^2).
+// The Chebyshev polynomial T_j((z - c0)/d) has modulus about r^j / 2 on the
+// ellipse, r = (al + beta)/d, and grows as exp(j acosh((c0 - t)/d)) at a real t < a.
+struct Ellipse {
+    double c0, al, d, r;
+    Ellipse(double a, double b, double beta) {
+        c0 = 0.5 * (a + b);
+        al = 0.5 * (b - a);
+        d = std::sqrt(al * al - beta * beta);
+        r = (al + beta) / d;
+    }
+    // growth exponent per degree at the real point t, relative to the ellipse
+    double net(double t) const {
+        const double x = (c0 - t) / d;
+        return (x > 1.0 ? std::acosh(x) : 0.0) - std::log(r);
+    }
+};
+
+// Chebyshev filter T_deg((A^2 - c0)/d) Y / r^deg, in place: the scaled
+// recurrence y_{j+1} = (2/r) s y_j - y_{j-1}/r^2, s = (A^2 - c0)/d, keeps the
+// components on the ellipse at O(1) and the wanted ones below the cap `amp`.
 template <class T>
 int filter(Work& W, bool adj, T* Y, double a, double b, int deg) {
     cudaStream_t st = W.c->work;
@@ -182,9 +210,10 @@ int filter(Work& W, bool adj, T* Y, double a, double b, int deg) {
     T* Yn = reinterpret_cast<T*>(W.blk[2]);
     T* T1 = reinterpret_cast<T*>(W.blk[3]);
     T* T2 = reinterpret_cast<T*>(W.blk[4]);
-    const double al = 2.0 / (b - a), be = -(a + b) / (b - a);
+    const Ellipse e(a, b, W.beta);
+    const double al = 1.0 / (e.d * e.r), be = -e.c0 / (e.d * e.r);
     T* cur = Y;
-    // Y1 = s(A^2) Y0
+    // Y1 = s(A^2) Y0 / r
     SGN_CUDA(hw<T>(W.c, T1, cur, q, adj, st));
     SGN_CUDA(hw<T>(W.c, T2, T1, q, adj, st));
     SGN_CUDA(cudaMemcpyAsync(Yp, cur, sizeof(T) * cnt, cudaMemcpyDeviceToDevice, st));
@@ -192,16 +221,74 @@ int filter(Work& W, bool adj, T* Y, double a, double b, int deg) {
     T* prev = Yp;
     T* now = Yn;
     T* spare = cur;
+    const double rr2 = 1.0 / (e.r * e.r);
     for (int j = 1; j < deg; ++j) {
         SGN_CUDA(hw<T>(W.c, T1, now, q, adj, st));
         SGN_CUDA(hw<T>(W.c, T2, T1, q, adj, st));
-        SGN_CUDA(axpby3<T>(spare, 2 * al, T2, 2 * be, now, -1.0, prev, cnt, st));
+        SGN_CUDA(axpby3<T>(spare, 2 * al, T2, 2 * be, now, -rr2, prev, cnt, st));
         T* t = prev;
         prev = now;
         now = spare;
         spare = t;
     }
     if (now != Y) SGN_CUDA(cudaMemcpyAsync(Y, now, sizeof(T) * cnt, cudaMemcpyDeviceToDevice, st));
+    return SGN_OK;
+}
+
+// Largest |Im theta| over the Ritz values of K Arnoldi steps on A^2 (CGS2,
+// one random start field): an estimate of the imaginary extent of the
+// spectrum of A^2, whose outer boundary Arnoldi resolves first.  Scratch:
+// blocks 1 (the K + 1 basis fields), 3 and 4.
+template <class T>
+int spectrum_height2(Work& W, bool adj, int K, uint64_t seed, double* height) {
+    cudaStream_t st = W.c->work;
+    const int64_t n = W.n;
+    K = std::min(K, W.q - 1);
+    T* V = reinterpret_cast<T*>(W.blk[1]);
+    T* w = reinterpret_cast<T*>(W.blk[3]);
+    T* t = reinterpret_cast<T*>(W.blk[4]);
+    std::vector<cd> Hh((size_t)K * K, 0.0), G;
+    SGN_CUDA(random_fill<T>(V, n, seed, st));
+    SGN_CHECK(gram<T>(W, V, 1, V, 1, G));
+    SGN_CUDA(axpby3<T>(V, 1.0 / std::sqrt(G[0].real()), V, 0.0, V, 0.0, nullptr, n, st));
+    int k = K;
+    for (int j = 0; j < K; ++j) {
+        T* vj = V + (size_t)j * n;
+        T* vn = V + (size_t)(j + 1) * n;
+        SGN_CUDA(hw<T>(W.c, t, vj, 1, adj, st));
+        SGN_CUDA(hw<T>(W.c, w, t, 1, adj, st));
+        // two classical Gram-Schmidt passes against v_0..v_j
+        std::vector<cd> h;
+        SGN_CHECK(gram<T>(W, V, j + 1, w, 1, h));
+        SGN_CHECK(combine<T>(W, V, j + 1, h, 1, t));
+        SGN_CUDA(axpby3<T>(vn, 1.0, w, -1.0, t, 0.0, nullptr, n, st));
+        std::vector<cd> h2;
+        SGN_CHECK(gram<T>(W, V, j + 1, vn, 1, h2));
+        SGN_CHECK(combine<T>(W, V, j + 1, h2, 1, t));
+        SGN_CUDA(axpby3<T>(w, 1.0, vn, -1.0, t, 0.0, nullptr, n, st));
+        for (int i = 0; i <= j; ++i) Hh[(size_t)i * K + j] = h[i] + h2[i];
+        SGN_CHECK(gram<T>(W, w, 1, w, 1, G));
+        const double nrm = std::sqrt(std::max(G[0].real(), 0.0));
+        double hn = 0;
+        for (int i = 0; i <= j; ++i) hn += std::norm(Hh[(size_t)i * K + j]);
+        if (!(nrm > 1e-10 * std::sqrt(hn))) {  // invariant subspace: the Ritz values are exact
+            k = j + 1;
+            break;
+        }
+        if (j + 1 < K) Hh[(size_t)(j + 1) * K + j] = nrm;
+        SGN_CUDA(axpby3<T>(vn, 1.0 / nrm, w, 0.0, w, 0.0, nullptr, n, st));
+    }
+    std::vector<cd> Hk((size_t)k * k);
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) Hk[(size_t)i * k + j] = Hh[(size_t)i * K + j];
+    std::vector<cd> th, X;
+    if (dense_eig(k, Hk, th, X)) {
+        set_error("deflation set-up: Arnoldi eigendecomposition failed");
+        return SGN_ERR_DEFLATION;
+    }
+    double hmax = 0;
+    for (const cd& z : th) hmax = std::max(hmax, std::abs(z.imag()));
+    *height = hmax;
     return SGN_OK;
 }
 
@@ -288,11 +375,10 @@ double spectral_bound2(const sgn_ctx* c) {
     return nb * nb * 1.0001;
 }
 
-int degree_for(double t_want, double a, double b, double amp, int dmax) {
-    double sw = std::abs((2 * t_want - b - a) / (b - a));
-    if (!(sw > 1.0 + 1e-12)) return dmax;
-    double d = std::acosh(amp) / std::acosh(sw);
-    int di = (int)std::ceil(d);
+int degree_for(const Ellipse& e, double t, double amp, int dmax) {
+    const double g = e.net(t);
+    if (!(g > 1e-12)) return dmax;
+    const int di = (int)std::ceil(std::acosh(amp) / g);
     return std::min(dmax, std::max(4, di));
 }
 
@@ -328,9 +414,10 @@ int iterate(Work& W, bool adj, T* Y, int want, double tol, int max_it, Ritz& rz,
         double worst = 0;
         for (int j = 0; j < want; ++j) worst = std::max(worst, rz.res[j]);
         if (debug_on())
-            fprintf(stderr, "[sgn eig %s %s] it %d worst %.3e theta_min %.4e theta_want %.4e theta_top %.4e\n",
+            fprintf(stderr,
+                    "[sgn eig %s %s] it %d worst %.3e theta_min %.4e theta_want %.4e theta_top %.4e beta %.3f\n",
                     adj ? "left" : "right", f64 ? "fp64" : "fp32", it, worst, std::abs(rz.theta[0]),
-                    std::abs(rz.theta[want - 1]), std::abs(rz.theta[q - 1]));
+                    std::abs(rz.theta[want - 1]), std::abs(rz.theta[q - 1]), W.beta);
         if (worst <= tol) {
             *its = it;
             return SGN_OK;
@@ -352,11 +439,12 @@ int iterate(Work& W, bool adj, T* Y, int want, double tol, int max_it, Ritz& rz,
         const double tmin = std::abs(rz.theta[0]);
         double a = std::abs(rz.theta[q - 1]);
         a = std::max(a, 1.02 * tw);
-        a = std::min(a, 0.9 * b);
+        a = std::min(a, std::min(0.9 * b, b - 4.0 * W.beta));  // keeps beta below half the real semi-axis
         const int dmax = f64 ? 400 : 800;
         const double amp = f64 ? 1e6 : 1e3;  // squared stays inside the Gram resolution above
-        const int d_conv = degree_for(tw, a, b, amp, dmax);
-        const int d_safe = degree_for(tmin, a, b, amp, dmax);
+        const Ellipse e(a, b, W.beta);
+        const int d_conv = degree_for(e, tw, amp, dmax);
+        const int d_safe = degree_for(e, tmin, amp, dmax);
         const int deg = std::max(4, std::min(d_conv, d_safe));
         SGN_CHECK(filter<T>(W, adj, Y, a, b, deg));
         int bad = 0;
@@ -370,8 +458,10 @@ int iterate(Work& W, bool adj, T* Y, int want, double tol, int max_it, Ritz& rz,
     for (int j = 0; j < want; ++j) worst = std::max(worst, rz.res[j]);
     *its = max_it;
     if (worst <= tol || stop_on_stall) return SGN_OK;
-    set_error("deflation set-up: eigenpairs did not converge (worst relative residual " + std::to_string(worst) +
-              ")");
+    char msg[160];
+    snprintf(msg, sizeof msg, "deflation set-up: eigenpairs did not converge in %d iterations (worst relative residual %.3e, tolerance %.3e)",
+             max_it, worst, tol);
+    set_error(msg);
     return SGN_ERR_DEFLATION;
 }
 
@@ -392,9 +482,19 @@ int eig_side(sgn_ctx* c, bool adj, int want, int q, double tol, uint64_t seed, d
     Work W;
     SGN_CHECK(setup(W, c, q, sizeof(float2), reduce_blocks<float2>(c->n)));
     float2* Y = reinterpret_cast<float2*>(W.blk[0]);
+    // imaginary extent of the spectrum of A^2, widened by 15 % (Arnoldi Ritz
+    // values approach the outer boundary of the spectrum from inside)
+    double height = 0;
+    int rc = spectrum_height2<float2>(W, adj, 40, seed ^ 0xa5a5ULL, &height);
+    if (rc != SGN_OK) {
+        dev_free(c, W.buf);
+        return rc;
+    }
+    W.beta = 1.15 * height;
+    if (debug_on()) fprintf(stderr, "[sgn eig] spectrum of A^2: max |Im| %.4f (Arnoldi)\n", height);
     SGN_CUDA(random_fill<float2>(Y, (int64_t)q * c->n, seed, st));
     // FP32 filter until the A^2 residuals reach their FP32 floor (or tol)
-    int rc = iterate<float2>(W, adj, Y, want, std::max(tol, 1e-6), 80, rz, true, true, &its);
+    rc = iterate<float2>(W, adj, Y, want, std::max(tol, 1e-6), 80, rz, true, true, &its);
     if (rc != SGN_OK) {
         dev_free(c, W.buf);
         return rc;
@@ -405,6 +505,7 @@ int eig_side(sgn_ctx* c, bool adj, int want, int q, double tol, uint64_t seed, d
         dev_free(c, W.buf);
         return rc;
     }
+    W64.beta = W.beta;
     double2* Y64 = reinterpret_cast<double2*>(W64.blk[0]);
     SGN_CUDA(convert_f32_to_f64(Y, Y64, (int64_t)q * c->n, st));
     SGN_CUDA(cudaStreamSynchronize(st));
@@ -412,7 +513,7 @@ int eig_side(sgn_ctx* c, bool adj, int want, int q, double tol, uint64_t seed, d
     // FP64: converge the A^2 subspace, then split it with one Rayleigh-Ritz step on A
     double tol2 = tol / 10;
     for (int attempt = 0; attempt < 4 && rc == SGN_OK; ++attempt) {
-        rc = iterate<double2>(W64, adj, Y64, want, tol2, 30, rz, attempt == 0, false, &its);
+        rc = iterate<double2>(W64, adj, Y64, want, tol2, 40, rz, attempt == 0, false, &its);
         if (rc != SGN_OK) break;
         double2* F = reinterpret_cast<double2*>(W64.blk[4]);
         SGN_CUDA(cudaMemcpyAsync(F, Y64, sizeof(double2) * want * c->n, cudaMemcpyDeviceToDevice, st));
