@@ -51,7 +51,8 @@ EXTRA = 4              # eigenpairs beyond m, to place the scale c in the gap
 # Restart cycles one solve of the default workload takes in the FP64 form (the
 # oracle runs the same algorithm and the same cycle count); used only to turn
 # the reference arm's bounded sample into solves/s.
-CYCLES_PER_SOLVE = {"24^4": 40, "16^4": 40, "10^4": 40, "8^4": 40, "4^4": 8}
+# (10^4 and 8^4: 9 cycles measured on a GB300 at tol 1e-10; the others are estimates.)
+CYCLES_PER_SOLVE = {"24^4": 40, "16^4": 40, "10^4": 9, "8^4": 9, "4^4": 8}
 
 
 def workload_name(w, name):
@@ -385,9 +386,16 @@ def run_ours(args, w, name):
     D.close()
 
 
+# DRAM bytes (read + write) per algorithmic byte of a kernel, from one ncu capture of the
+# kernel as it stands (profiles/k_dcgs_dots_10x4_mixed.md: 372.4 MB for 368.6 MB at J = 30).
+# An entry must be removed when its kernel changes.
+DRAM_PER_ALGORITHMIC_BYTE = {"k_dcgs_dots<float2>": 372.4 / 368.6}
+
+
 def roofline(kt, hbm, peak_src, t_timed):
     """Dominant kernel of the timed steps (largest summed event time): algorithmic
-    bytes per launch / average launch duration, against the measured HBM copy rate."""
+    bytes per launch / average launch duration, against the measured HBM copy rate;
+    traffic = the measured DRAM-to-algorithmic ratio times the average launch's bytes."""
     name = max(kt, key=lambda k: kt[k]["ms"])
     d = kt[name]
     if not d["launches"]:
@@ -395,8 +403,10 @@ def roofline(kt, hbm, peak_src, t_timed):
     per_launch_bytes = d["bytes"] / d["launches"]
     per_launch_s = d["ms"] / 1000.0 / d["launches"]
     achieved = per_launch_bytes / per_launch_s / 1e9
+    ratio = DRAM_PER_ALGORITHMIC_BYTE.get(name)
     return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": None, "kernel": name, "launches": d["launches"],
+            "traffic": ratio * per_launch_bytes if ratio else None, "kernel": name, "launches": d["launches"],
+            "bytes_per_launch": per_launch_bytes,
             "share_of_timed": d["ms"] / 1000.0 / t_timed, "peak_source": peak_src + " hbm_gbs"}
 
 
@@ -410,19 +420,25 @@ def stencil_hbm(pkg, torch, args):
         sc.load_gauge(torch.from_numpy(U).cuda())
         del U
         sc.set_precision(pkg.PREC_MIXED, 1e-8, pkg.LINKS_FP32)
-        b32 = torch.from_numpy(si.point_sources(dims, nrhs)).cuda().to(torch.complex64)
+        # the library's internal (packed) layout, so that one call is one stencil launch
+        b32 = sc.pack(torch.from_numpy(si.point_sources(dims, nrhs)).cuda().to(torch.complex64),
+                      pkg.PREC_MIXED)
         out = torch.empty_like(b32)
         lib = pkg.lib()
         stream = torch.cuda.current_stream()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         for _ in range(3):
-            lib.sgn_hw_apply(sc._h, C.c_void_p(b32.data_ptr()), C.c_void_p(out.data_ptr()), nrhs, 1, 0)
+            lib.sgn_hw_apply(sc._h, C.c_void_p(b32.data_ptr()), C.c_void_p(out.data_ptr()), nrhs, 1,
+                             pkg.HW_PACKED)
         torch.cuda.synchronize()
         reps = 20
+        torch.cuda.nvtx.range_push("stencil")
         ev[0].record(stream)
         for _ in range(reps):
-            lib.sgn_hw_apply(sc._h, C.c_void_p(b32.data_ptr()), C.c_void_p(out.data_ptr()), nrhs, 1, 0)
+            lib.sgn_hw_apply(sc._h, C.c_void_p(b32.data_ptr()), C.c_void_p(out.data_ptr()), nrhs, 1,
+                             pkg.HW_PACKED)
         ev[1].record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         t = ev[0].elapsed_time(ev[1]) / 1000.0 / reps
     byts = (288 + 192 * nrhs) * vol   # links once, each spinor read once and written once
@@ -443,9 +459,16 @@ def main():
                     help="stopping tolerance on the shifted-system residuals, both forms")
     ap.add_argument("--skip-fp64-form", action="store_true", help="do not time the plain FP64 form")
     ap.add_argument("--no-stencil-24", action="store_true", help="do not time the 24^4 stencil")
+    ap.add_argument("--stencil-only", action="store_true",
+                    help="time only the 12-column FP32 stencil at 24^4 and print its numbers")
     args = ap.parse_args()
     TOL = args.tol
     w = WORKLOADS[args.workload]
+    if args.stencil_only:
+        import torch
+        import paper_0910_2927_gb300 as pkg
+        print(json.dumps({"stencil_24^4": stencil_hbm(pkg, torch, args)}))
+        return
     if args.impl == "reference":
         reference_arm(args, w, args.workload)
     else:

@@ -180,11 +180,30 @@ SGN_API int sgn_apply(sgn_ctx* ctx, const double* b, double* x, int nrhs, int fl
 SGN_API int sgn_apply_shifts(sgn_ctx* ctx, const double* b, double* x, double* x_shift, int nrhs,
                              int flags, sgn_report* rep);
 
-/* The Wilson kernel alone: out = H_W(mu) in (or H_W(-mu) with adjoint = 1) for
- * nrhs fields.  precision SGN_PREC_FP64: complex128 fields; SGN_PREC_MIXED:
- * complex64 fields with the FP32 (or BF16, see sgn_set_precision) links.
- * Device pointers; in and out must not overlap. */
-SGN_API int sgn_hw_apply(sgn_ctx* ctx, const void* in, void* out, int nrhs, int precision, int adjoint);
+/* Flags of sgn_hw_apply. */
+#define SGN_HW_ADJOINT 1 /* apply H_W(mu)^dag = H_W(-mu) */
+#define SGN_HW_PACKED 2  /* in and out are in the packed layout (sgn_pack_fields) */
+
+/* The Wilson kernel alone (Sec. 1): out = H_W(mu) in (or H_W(-mu) with
+ * SGN_HW_ADJOINT) for nrhs fields.  precision SGN_PREC_FP64: complex128 fields;
+ * SGN_PREC_MIXED: complex64 fields with the FP32 (or BF16, see
+ * sgn_set_precision) links.  Device pointers; in and out must not overlap.
+ * Natural-order fields are packed into a staging buffer, the stencil runs on
+ * the packed copy and the result is unpacked; with SGN_HW_PACKED the stencil
+ * runs on the caller's packed fields directly (no staging, one kernel).
+ * Errors: SGN_ERR_ARG (unknown precision or flag), SGN_ERR_STATE (no gauge). */
+SGN_API int sgn_hw_apply(sgn_ctx* ctx, const void* in, void* out, int nrhs, int precision, int flags);
+
+/* Layout conversion of nfield fields between the natural order
+ * [site][spin][colour] and the packed order the library keeps internally:
+ * complex entry k = 3 spin + colour of site s at (k/2) * 2V + 2s + (k mod 2)
+ * within its field (six planes of two entries per site, so a warp's loads of
+ * consecutive sites are contiguous).  Device pointers, in != out;
+ * precision SGN_PREC_FP64 (complex128) or SGN_PREC_MIXED (complex64);
+ * 1 <= nfield <= 65535.  Every other call of this interface takes and returns
+ * natural-order fields. */
+SGN_API int sgn_pack_fields(sgn_ctx* ctx, const void* in, void* out, int nfield, int precision);
+SGN_API int sgn_unpack_fields(sgn_ctx* ctx, const void* in, void* out, int nfield, int precision);
 
 /* Inner products out[c*J + j] = <V_j, w_c> = V_j^dag w_c of J fields V (one basis
  * shared by every column) with nrhs fields w -- the coefficients of classical

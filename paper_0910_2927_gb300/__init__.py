@@ -11,11 +11,11 @@ import ctypes as C
 import numpy as np
 
 from . import _abi
-from ._abi import (APPLY_ADJOINT, APPLY_HOST_BUFFERS, LINKS_BF16, LINKS_FP32, PREC_FP64, PREC_MIXED, Report,
-                   SignError, check, lib)
+from ._abi import (APPLY_ADJOINT, APPLY_HOST_BUFFERS, HW_ADJOINT, HW_PACKED, LINKS_BF16, LINKS_FP32, PREC_FP64,
+                   PREC_MIXED, Report, SignError, check, lib)
 
 __all__ = ["SignContext", "kenney_laub", "SignError", "PREC_FP64", "PREC_MIXED", "LINKS_FP32", "LINKS_BF16",
-           "sign_apply", "SignApply"]
+           "HW_ADJOINT", "HW_PACKED", "sign_apply", "SignApply"]
 
 
 def kenney_laub(s: int, c: float = 1.0):
@@ -228,16 +228,35 @@ class SignContext:
                                        wc.shape[0], out.ctypes.data))
         return out
 
-    def hw(self, psi, precision=PREC_FP64, adjoint=False):
-        """H_W(mu) psi (or H_W(-mu) psi) for CUDA fields of shape (nrhs, n) or (n,)."""
+    def hw(self, psi, precision=PREC_FP64, adjoint=False, packed=False):
+        """H_W(mu) psi (or H_W(-mu) psi) for CUDA fields of shape (nrhs, n) or (n,);
+        packed=True: psi is (and the result stays) in the packed layout of `pack`."""
         torch = _torch()
         dt = torch.complex128 if precision == PREC_FP64 else torch.complex64
         x = psi.to(dt).contiguous()
         out = torch.empty_like(x)
         nrhs = x.numel() // self.n
+        flags = (HW_ADJOINT if adjoint else 0) | (HW_PACKED if packed else 0)
         check(lib().sgn_hw_apply(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()), nrhs,
-                                 int(precision), int(bool(adjoint))))
+                                 int(precision), flags))
         return out
+
+    def _layout(self, fn, psi, precision):
+        torch = _torch()
+        dt = torch.complex128 if precision == PREC_FP64 else torch.complex64
+        x = psi.to(dt).contiguous()
+        out = torch.empty_like(x)
+        check(fn(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()), x.numel() // self.n,
+                 int(precision)))
+        return out
+
+    def pack(self, psi, precision=PREC_FP64):
+        """Natural [site][spin][colour] fields -> the library's packed layout."""
+        return self._layout(lib().sgn_pack_fields, psi, precision)
+
+    def unpack(self, psi, precision=PREC_FP64):
+        """Packed fields -> natural [site][spin][colour] order."""
+        return self._layout(lib().sgn_unpack_fields, psi, precision)
 
 
 def sign_apply(ctx: SignContext, b, adjoint=False):

@@ -14,6 +14,7 @@ STATUS = {0: "SGN_OK", 1: "SGN_ERR_ARG", 2: "SGN_ERR_CUDA", 3: "SGN_ERR_NOT_CONV
 PREC_FP64, PREC_MIXED = 0, 1
 LINKS_FP32, LINKS_BF16 = 0, 1
 APPLY_HOST_BUFFERS, APPLY_ADJOINT, APPLY_NO_A = 1, 2, 4
+HW_ADJOINT, HW_PACKED = 1, 2
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
@@ -49,6 +50,8 @@ SIGNATURES = {
     "sgn_apply": (C.c_int, [P, P, P, C.c_int, C.c_int, C.POINTER(Report)]),
     "sgn_apply_shifts": (C.c_int, [P, P, P, P, C.c_int, C.c_int, C.POINTER(Report)]),
     "sgn_hw_apply": (C.c_int, [P, P, P, C.c_int, C.c_int, C.c_int]),
+    "sgn_pack_fields": (C.c_int, [P, P, P, C.c_int, C.c_int]),
+    "sgn_unpack_fields": (C.c_int, [P, P, P, C.c_int, C.c_int]),
     "sgn_inner_products": (C.c_int, [P, P, C.c_int, P, C.c_int, P]),
     "sgn_inner_products_noalloc": (C.c_int, [P, C.c_int, P, C.c_longlong, C.c_int, P, P]),
     "sgn_dhw_dmu_apply": (C.c_int, [P, P, P, C.c_int]),

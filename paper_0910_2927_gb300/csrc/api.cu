@@ -51,6 +51,20 @@ int copy_in(sgn_ctx* c, void* dst, const void* src, size_t bytes, int on_device)
     return SGN_OK;
 }
 
+// nfield natural-order complex128 fields (device, or host when on_device == 0)
+// into packed device fields; host data pass through the staging buffer.
+int fields_in(sgn_ctx* c, double2* packed, const double* src, int nfield, int on_device) {
+    const double2* nat = reinterpret_cast<const double2*>(src);
+    if (!on_device) {
+        const size_t bytes = (size_t)c->n * nfield * sizeof(double2);
+        SGN_CHECK(dev_alloc(c, c->stage, bytes));
+        SGN_CUDA(cudaMemcpyAsync(c->stage.p, src, bytes, cudaMemcpyHostToDevice, c->work));
+        nat = as<double2>(c->stage);
+    }
+    SGN_CUDA(pack_fields<double2>(nat, packed, c->vol, nfield, c->work));
+    return SGN_OK;
+}
+
 }  // namespace
 }  // namespace sgn
 
@@ -140,7 +154,13 @@ SGN_API int sgn_load_gauge(sgn_ctx* c, const double* links, int on_device) {
     SGN_CHECK(dev_alloc(c, c->U64, count * sizeof(double2)));
     SGN_CHECK(dev_alloc(c, c->U32, count * sizeof(float2)));
     SGN_CHECK(dev_alloc(c, c->U16, count * sizeof(__nv_bfloat162)));
-    SGN_CHECK(copy_in(c, c->U64.p, links, count * sizeof(double2), on_device));
+    const double2* nat = reinterpret_cast<const double2*>(links);
+    if (!on_device) {
+        SGN_CHECK(dev_alloc(c, c->stage, count * sizeof(double2)));
+        SGN_CHECK(copy_in(c, c->stage.p, links, count * sizeof(double2), 0));
+        nat = as<double2>(c->stage);
+    }
+    SGN_CUDA(pack_links(nat, as<double2>(c->U64), c->vol, c->work));
     SGN_CUDA(convert_f64_to_f32(as<double2>(c->U64), as<float2>(c->U32), (int64_t)count, c->work));
     SGN_CUDA(links_f64_to_bf16(as<double2>(c->U64), as<__nv_bfloat162>(c->U16), (int64_t)count, c->work));
     SGN_CUDA(cudaStreamSynchronize(c->work));
@@ -243,8 +263,8 @@ SGN_API int sgn_set_deflation(sgn_ctx* c, int m, const double* R, const double* 
     SGN_CHECK(dev_alloc(c, c->L32, cnt * sizeof(float2)));
     SGN_CHECK(dev_alloc(c, c->lam_dev, (size_t)m * sizeof(double2)));
     SGN_CHECK(dev_alloc(c, c->lamc_dev, (size_t)m * sizeof(double2)));
-    SGN_CHECK(copy_in(c, c->R64.p, R, cnt * sizeof(double2), on_device));
-    SGN_CHECK(copy_in(c, c->L64.p, L, cnt * sizeof(double2), on_device));
+    SGN_CHECK(fields_in(c, as<double2>(c->R64), R, m, on_device));
+    SGN_CHECK(fields_in(c, as<double2>(c->L64), L, m, on_device));
     SGN_CUDA(convert_f64_to_f32(as<double2>(c->R64), as<float2>(c->R32), (int64_t)cnt, c->work));
     SGN_CUDA(convert_f64_to_f32(as<double2>(c->L64), as<float2>(c->L32), (int64_t)cnt, c->work));
     std::vector<double> lamc(lam);
@@ -264,9 +284,17 @@ SGN_API int sgn_get_deflation(sgn_ctx* c, int* m, double* R, double* L, double* 
     if (m) *m = c->m;
     if (c->m == 0) return SGN_OK;
     const size_t cnt = (size_t)c->n * c->m;
-    SGN_CUDA(cudaStreamSynchronize(c->work));
-    if (R) SGN_CUDA(cudaMemcpy(R, c->R64.p, cnt * sizeof(double2), cudaMemcpyDeviceToHost));
-    if (L) SGN_CUDA(cudaMemcpy(L, c->L64.p, cnt * sizeof(double2), cudaMemcpyDeviceToHost));
+    SGN_CHECK(enter(c));
+    SGN_CHECK(dev_alloc(c, c->stage, cnt * sizeof(double2)));
+    for (int side = 0; side < 2; ++side) {
+        double* dst = side == 0 ? R : L;
+        if (!dst) continue;
+        SGN_CUDA(unpack_fields<double2>(as<double2>(side == 0 ? c->R64 : c->L64), as<double2>(c->stage), c->vol,
+                                        c->m, c->work));
+        SGN_CUDA(cudaMemcpyAsync(dst, c->stage.p, cnt * sizeof(double2), cudaMemcpyDeviceToHost, c->work));
+        SGN_CUDA(cudaStreamSynchronize(c->work));
+    }
+    SGN_CHECK(leave(c));
     if (lambda)
         for (int j = 0; j < c->m; ++j) {
             lambda[2 * j] = c->lam[j].real();
@@ -301,19 +329,32 @@ int apply_common(sgn_ctx* c, const double* b, double* x, double* x_shift, int nr
     SGN_CHECK(enter(c));
     const long long launches0 = g_launches;
     SGN_CUDA(cudaEventRecord(c->ev_t0, c->work));
-    const double2* bd = reinterpret_cast<const double2*>(b);
-    double2* xd = reinterpret_cast<double2*>(x);
-    if (host) {
-        SGN_CHECK(dev_alloc(c, c->stage, 2 * fbytes));
-        double2* sb = as<double2>(c->stage);
-        SGN_CUDA(cudaMemcpyAsync(sb, b, fbytes, cudaMemcpyHostToDevice, c->work));
-        bd = sb;
-        xd = sb + (size_t)c->n * nrhs;
+    // staging: [b packed][x packed][x_shift packed]
+    const size_t nn = (size_t)c->n * nrhs;
+    const int s = (int)c->sigma.size();
+    SGN_CHECK(dev_alloc(c, c->stage, (2 + (x_shift ? s : 0)) * fbytes));
+    double2* bp = as<double2>(c->stage);
+    double2* xp = bp + nn;
+    double2* xsp = x_shift ? xp + nn : nullptr;
+    if (host) {  // natural b lands in the x slot, is packed into the b slot
+        SGN_CUDA(cudaMemcpyAsync(xp, b, fbytes, cudaMemcpyHostToDevice, c->work));
+        SGN_CUDA(pack_fields<double2>(xp, bp, c->vol, nrhs, c->work));
+    } else {
+        SGN_CUDA(pack_fields<double2>(reinterpret_cast<const double2*>(b), bp, c->vol, nrhs, c->work));
     }
     const bool no_a = flags & SGN_APPLY_NO_A;
-    int status = solve(c, bd, xd, reinterpret_cast<double2*>(x_shift), nrhs, adjoint, no_a, rep);
-    if (host && (status == SGN_OK || status == SGN_ERR_NOT_CONVERGED))
-        SGN_CUDA(cudaMemcpyAsync(x, xd, fbytes, cudaMemcpyDeviceToHost, c->work));
+    int status = solve(c, bp, xp, xsp, nrhs, adjoint, no_a, rep);
+    if (status == SGN_OK || status == SGN_ERR_NOT_CONVERGED) {
+        if (host) {  // natural x goes out through the b slot
+            SGN_CUDA(unpack_fields<double2>(xp, bp, c->vol, nrhs, c->work));
+            SGN_CUDA(cudaMemcpyAsync(x, bp, fbytes, cudaMemcpyDeviceToHost, c->work));
+        } else {
+            SGN_CUDA(unpack_fields<double2>(xp, reinterpret_cast<double2*>(x), c->vol, nrhs, c->work));
+            if (xsp)
+                SGN_CUDA(unpack_fields<double2>(xsp, reinterpret_cast<double2*>(x_shift), c->vol, s * nrhs,
+                                                c->work));
+        }
+    }
     SGN_CUDA(cudaEventRecord(c->ev_t1, c->work));
     SGN_CUDA(cudaEventSynchronize(c->ev_t1));
     if (rep) {
@@ -338,20 +379,79 @@ SGN_API int sgn_apply_shifts(sgn_ctx* c, const double* b, double* x, double* x_s
     return apply_common(c, b, x, x_shift, nrhs, flags, rep);
 }
 
-SGN_API int sgn_hw_apply(sgn_ctx* c, const void* in, void* out, int nrhs, int precision, int adjoint) {
+SGN_API int sgn_hw_apply(sgn_ctx* c, const void* in, void* out, int nrhs, int precision, int flags) {
     if (!c || !in || !out || nrhs < 1) return fail(SGN_ERR_ARG, "sgn_hw_apply: bad argument");
     if (in == out) return fail(SGN_ERR_ARG, "sgn_hw_apply: in and out must differ");
     if (!c->have_gauge) return fail(SGN_ERR_STATE, "sgn_hw_apply: load the gauge field first");
-    SGN_CHECK(enter(c));
-    if (precision == SGN_PREC_FP64) {
-        SGN_CUDA(apply_hw64(c, reinterpret_cast<double2*>(out), reinterpret_cast<const double2*>(in), nrhs,
-                            adjoint != 0, nullptr, c->work));
-    } else if (precision == SGN_PREC_MIXED) {
-        SGN_CUDA(apply_hw32(c, reinterpret_cast<float2*>(out), reinterpret_cast<const float2*>(in), nrhs,
-                            adjoint != 0, nullptr, c->work));
-    } else {
+    if (precision != SGN_PREC_FP64 && precision != SGN_PREC_MIXED)
         return fail(SGN_ERR_ARG, "sgn_hw_apply: unknown precision");
+    if (flags & ~(SGN_HW_ADJOINT | SGN_HW_PACKED)) return fail(SGN_ERR_ARG, "sgn_hw_apply: unknown flag");
+    const bool adjoint = flags & SGN_HW_ADJOINT;
+    const bool packed = flags & SGN_HW_PACKED;
+    SGN_CHECK(enter(c));
+    const size_t nn = (size_t)c->n * nrhs;
+    if (precision == SGN_PREC_FP64) {
+        const double2* pi = reinterpret_cast<const double2*>(in);
+        double2* po = reinterpret_cast<double2*>(out);
+        if (!packed) {
+            SGN_CHECK(dev_alloc(c, c->stage, 2 * nn * sizeof(double2)));
+            double2* t = as<double2>(c->stage);
+            SGN_CUDA(pack_fields<double2>(pi, t, c->vol, nrhs, c->work));
+            pi = t;
+            po = t + nn;
+        }
+        SGN_CHECK(tune_stencil(c, 0, nrhs, const_cast<double2*>(pi), po));
+        SGN_CUDA(apply_hw64(c, po, pi, nrhs, adjoint, nullptr, c->work));
+        if (!packed)
+            SGN_CUDA(unpack_fields<double2>(po, reinterpret_cast<double2*>(out), c->vol, nrhs, c->work));
+    } else {
+        const float2* pi = reinterpret_cast<const float2*>(in);
+        float2* po = reinterpret_cast<float2*>(out);
+        if (!packed) {
+            SGN_CHECK(dev_alloc(c, c->stage, 2 * nn * sizeof(float2)));
+            float2* t = as<float2>(c->stage);
+            SGN_CUDA(pack_fields<float2>(pi, t, c->vol, nrhs, c->work));
+            pi = t;
+            po = t + nn;
+        }
+        SGN_CHECK(tune_stencil(c, c->link_storage == SGN_LINKS_BF16 ? 2 : 1, nrhs, const_cast<float2*>(pi), po));
+        SGN_CUDA(apply_hw32(c, po, pi, nrhs, adjoint, nullptr, c->work));
+        if (!packed)
+            SGN_CUDA(unpack_fields<float2>(po, reinterpret_cast<float2*>(out), c->vol, nrhs, c->work));
     }
+    SGN_CHECK(leave(c));
+    return SGN_OK;
+}
+
+SGN_API int sgn_pack_fields(sgn_ctx* c, const void* in, void* out, int nfield, int precision) {
+    if (!c || !in || !out || nfield < 1 || nfield > 65535) return fail(SGN_ERR_ARG, "sgn_pack_fields: bad argument");
+    if (in == out) return fail(SGN_ERR_ARG, "sgn_pack_fields: in and out must differ");
+    if (precision != SGN_PREC_FP64 && precision != SGN_PREC_MIXED)
+        return fail(SGN_ERR_ARG, "sgn_pack_fields: unknown precision");
+    SGN_CHECK(enter(c));
+    if (precision == SGN_PREC_FP64)
+        SGN_CUDA(pack_fields<double2>(reinterpret_cast<const double2*>(in), reinterpret_cast<double2*>(out), c->vol,
+                                      nfield, c->work));
+    else
+        SGN_CUDA(pack_fields<float2>(reinterpret_cast<const float2*>(in), reinterpret_cast<float2*>(out), c->vol,
+                                     nfield, c->work));
+    SGN_CHECK(leave(c));
+    return SGN_OK;
+}
+
+SGN_API int sgn_unpack_fields(sgn_ctx* c, const void* in, void* out, int nfield, int precision) {
+    if (!c || !in || !out || nfield < 1 || nfield > 65535)
+        return fail(SGN_ERR_ARG, "sgn_unpack_fields: bad argument");
+    if (in == out) return fail(SGN_ERR_ARG, "sgn_unpack_fields: in and out must differ");
+    if (precision != SGN_PREC_FP64 && precision != SGN_PREC_MIXED)
+        return fail(SGN_ERR_ARG, "sgn_unpack_fields: unknown precision");
+    SGN_CHECK(enter(c));
+    if (precision == SGN_PREC_FP64)
+        SGN_CUDA(unpack_fields<double2>(reinterpret_cast<const double2*>(in), reinterpret_cast<double2*>(out),
+                                        c->vol, nfield, c->work));
+    else
+        SGN_CUDA(unpack_fields<float2>(reinterpret_cast<const float2*>(in), reinterpret_cast<float2*>(out), c->vol,
+                                       nfield, c->work));
     SGN_CHECK(leave(c));
     return SGN_OK;
 }
@@ -361,7 +461,12 @@ SGN_API int sgn_dhw_dmu_apply(sgn_ctx* c, const double* in, double* out, int nrh
     if (in == out) return fail(SGN_ERR_ARG, "sgn_dhw_dmu_apply: in and out must differ");
     if (!c->have_gauge) return fail(SGN_ERR_STATE, "sgn_dhw_dmu_apply: load the gauge field first");
     SGN_CHECK(enter(c));
-    SGN_CUDA(apply_dhw_dmu64(c, reinterpret_cast<double2*>(out), reinterpret_cast<const double2*>(in), nrhs, c->work));
+    const size_t nn = (size_t)c->n * nrhs;
+    SGN_CHECK(dev_alloc(c, c->stage, 2 * nn * sizeof(double2)));
+    double2* t = as<double2>(c->stage);
+    SGN_CUDA(pack_fields<double2>(reinterpret_cast<const double2*>(in), t, c->vol, nrhs, c->work));
+    SGN_CUDA(apply_dhw_dmu64(c, t + nn, t, nrhs, c->work));
+    SGN_CUDA(unpack_fields<double2>(t + nn, reinterpret_cast<double2*>(out), c->vol, nrhs, c->work));
     SGN_CHECK(leave(c));
     return SGN_OK;
 }
@@ -371,7 +476,12 @@ SGN_API int sgn_grad_mu(sgn_ctx* c, const double* b, const double* g, int nrhs, 
     if (!c->have_gauge || c->sigma.empty()) return fail(SGN_ERR_STATE, "sgn_grad_mu: gauge field and rational function needed");
     if (c->m > 0) return fail(SGN_ERR_STATE, "sgn_grad_mu: defined for the undeflated function (m = 0) only");
     SGN_CHECK(enter(c));
-    int st = grad_mu(c, reinterpret_cast<const double2*>(b), reinterpret_cast<const double2*>(g), nrhs, dmu);
+    const size_t nn = (size_t)c->n * nrhs;
+    SGN_CHECK(dev_alloc(c, c->stage, 2 * nn * sizeof(double2)));
+    double2* t = as<double2>(c->stage);
+    SGN_CUDA(pack_fields<double2>(reinterpret_cast<const double2*>(b), t, c->vol, nrhs, c->work));
+    SGN_CUDA(pack_fields<double2>(reinterpret_cast<const double2*>(g), t + nn, c->vol, nrhs, c->work));
+    int st = grad_mu(c, t, t + nn, nrhs, dmu);
     SGN_CHECK(leave(c));
     return st;
 }

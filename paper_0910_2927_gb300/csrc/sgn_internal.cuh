@@ -77,13 +77,29 @@ struct StencilParams {
     FastDiv div[3];    // by Lx, Ly, Lz (site < 2^27)
 };
 
+// ---------------------------------------------------------- field layout --
+// Inside the library every field is kept "packed": the complex entry k = 3 spin
+// + colour of site s of a field of vol sites sits at (k/2) * 2 vol + 2 s + k%2,
+// i.e. six planes that each hold two consecutive spin-colour entries per site.
+// A warp of 32 consecutive sites then reads 32 x 16 contiguous bytes per plane
+// (FP32), where the natural [site][12] order reads every 96th-byte chunk.
+// Links are packed as [dir][row 3][col 3][site].  Dot products and vector
+// updates do not depend on the order; only the stencil and the boundary do.
+template <class T>
+cudaError_t pack_fields(const T* natural, T* packed, int64_t vol, int nfield, cudaStream_t st);
+template <class T>
+cudaError_t unpack_fields(const T* packed, T* natural, int64_t vol, int nfield, cudaStream_t st);
+cudaError_t pack_links(const double2* natural, double2* packed, int64_t vol, cudaStream_t st);
+
 // ---------------------------------------------------------- kernel entry --
-// Stencil: out = H_W in for nrhs fields.  Real = double or float; links in
+// Stencil: out = H_W in for nrhs fields (packed layout).  Real = double or float; links in
 // double, float or bf16 (Link).  skip: per-field flags (non-zero: skip), may be null.
-// Launch shape: sx sites (x fastest) by rb fields per CTA; {0, 0} picks the default.
+// Launch shape: sx sites (x fastest) by rb threads per CTA, each thread nr
+// fields of its site (nr <= 3 FP32, 1 FP64); {0, 0, 1} picks the default.
 struct StencilShape {
     int sx = 0;
     int rb = 0;
+    int nr = 1;
 };
 cudaError_t launch_hw_f64(double2* out, const double2* in, const double2* U, int nrhs,
                           const StencilParams& p, const int* skip, cudaStream_t st, StencilShape sh = {});

@@ -117,13 +117,26 @@ int tune_stencil(sgn_ctx* c, int prec, int ncol, void* in, void* out) {
         c->shapes[key] = StencilShape{};
         return SGN_OK;
     }
+    // SGN_STENCIL_SHAPE="sx,rb,nr" fixes the shape of every stencil launch (checked at launch)
+    if (const char* fix = getenv("SGN_STENCIL_SHAPE")) {
+        StencilShape sh;
+        if (sscanf(fix, "%d,%d,%d", &sh.sx, &sh.rb, &sh.nr) == 3) {
+            c->shapes[key] = sh;
+            return SGN_OK;
+        }
+    }
     cudaStream_t st = c->work;
     const StencilParams p = stencil_params(c, false);
     std::vector<StencilShape> cands;
-    for (int rb : {1, 2, 3, 4, 6, 8, 12, 16}) {
-        if (rb > ncol) continue;
-        for (int sx : {32, 64, 128, 256})
-            if (sx * rb <= 384 && sx * rb >= 64) cands.push_back({sx, rb});
+    for (int nr : {1, 2, 3}) {
+        if (nr > ncol || (prec == 0 && nr > 1)) continue;
+        const int groups = (ncol + nr - 1) / nr;
+        const int maxt = nr == 1 ? 384 : 256;
+        for (int rb : {1, 2, 3, 4, 6, 8, 12, 16}) {
+            if (rb > groups) continue;
+            for (int sx : {32, 64, 128, 256})
+                if (sx * rb <= maxt && sx * rb >= 64) cands.push_back({sx, rb, nr});
+        }
     }
     if (cands.empty()) cands.push_back({});
     auto run = [&](StencilShape sh) -> cudaError_t {
@@ -159,7 +172,9 @@ int tune_stencil(sgn_ctx* c, int prec, int ncol, void* in, void* out) {
         const char* s = getenv("SGN_DEBUG");
         return s && s[0] == '1';
     }();
-    if (dbg) fprintf(stderr, "[sgn tune] stencil prec %d ncol %d -> sx %d rb %d (%.3f ms / 3)\n", prec, ncol, pick.sx, pick.rb, best);
+    if (dbg)
+        fprintf(stderr, "[sgn tune] stencil prec %d ncol %d -> sx %d rb %d nr %d (%.3f ms / 3)\n", prec, ncol, pick.sx,
+                pick.rb, pick.nr, best);
     return SGN_OK;
 }
 

@@ -5,6 +5,8 @@
 // sites (x fastest) for RB fields, so the RB warps that share a site tile
 // read the same links back to back and the link bytes come from L1 after the
 // first field: with 12 fields the links cost 1/12 of their bytes per field.
+// Fields and links are in the packed layout (planes over sites), so every
+// load of a warp covers 32 consecutive sites of one plane.
 // Each hop uses the rank-2 spin projector (1 -/+ gamma_nu): two colour
 // vectors are multiplied by the link instead of four, and gamma5 is folded
 // into the write (spins 2, 3 negated).
@@ -45,41 +47,53 @@ __device__ __forceinline__ void cmac_conj(Cx<R>& acc, Cx<R> u, Cx<R> v) {
 }
 
 // ---- loads -----------------------------------------------------------------
+// Packed field: plane p (entries 2p, 2p+1) of site s at complex offset p * vol2 + 2 s.
 template <class R>
 struct Field;
 template <>
 struct Field<double> {
     using T = double2;
-    static __device__ __forceinline__ void load(const double2* __restrict__ f, int64_t site, Cx<double> p[12]) {
-        const double2* s = f + site * 12;
+    static __device__ __forceinline__ void load(const double2* __restrict__ f, int64_t site, int64_t vol2,
+                                                Cx<double> p[12]) {
+        const double2* s = f + 2 * site;
 #pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            double2 v = __ldg(s + k);
-            p[k] = {v.x, v.y};
+        for (int k = 0; k < 6; ++k) {
+            const double2 a = __ldg(s + k * vol2);
+            const double2 b = __ldg(s + k * vol2 + 1);
+            p[2 * k] = {a.x, a.y};
+            p[2 * k + 1] = {b.x, b.y};
         }
     }
-    static __device__ __forceinline__ void store(double2* __restrict__ f, int64_t site, const Cx<double> p[12]) {
-        double2* s = f + site * 12;
+    static __device__ __forceinline__ void store(double2* __restrict__ f, int64_t site, int64_t vol2,
+                                                 const Cx<double> p[12]) {
+        double2* s = f + 2 * site;
 #pragma unroll
-        for (int k = 0; k < 12; ++k) s[k] = make_double2(p[k].x, p[k].y);
+        for (int k = 0; k < 6; ++k) {
+            s[k * vol2] = make_double2(p[2 * k].x, p[2 * k].y);
+            s[k * vol2 + 1] = make_double2(p[2 * k + 1].x, p[2 * k + 1].y);
+        }
     }
 };
 template <>
 struct Field<float> {
     using T = float2;
-    static __device__ __forceinline__ void load(const float2* __restrict__ f, int64_t site, Cx<float> p[12]) {
-        const float4* s = reinterpret_cast<const float4*>(f + site * 12);
+    static __device__ __forceinline__ void load(const float2* __restrict__ f, int64_t site, int64_t vol2,
+                                                Cx<float> p[12]) {
+        const float2* s = f + 2 * site;
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            float4 v = __ldg(s + k);
+            const float4 v = __ldg(reinterpret_cast<const float4*>(s + k * vol2));
             p[2 * k] = {v.x, v.y};
             p[2 * k + 1] = {v.z, v.w};
         }
     }
-    static __device__ __forceinline__ void store(float2* __restrict__ f, int64_t site, const Cx<float> p[12]) {
-        float4* s = reinterpret_cast<float4*>(f + site * 12);
+    static __device__ __forceinline__ void store(float2* __restrict__ f, int64_t site, int64_t vol2,
+                                                 const Cx<float> p[12]) {
+        float2* s = f + 2 * site;
 #pragma unroll
-        for (int k = 0; k < 6; ++k) s[k] = make_float4(p[2 * k].x, p[2 * k].y, p[2 * k + 1].x, p[2 * k + 1].y);
+        for (int k = 0; k < 6; ++k)
+            *reinterpret_cast<float4*>(s + k * vol2) =
+                make_float4(p[2 * k].x, p[2 * k].y, p[2 * k + 1].x, p[2 * k + 1].y);
     }
 };
 
@@ -107,70 +121,91 @@ struct Link<float, __nv_bfloat162> {
     }
 };
 
-// One hop: acc += coef * (1 + S gamma_NU) W psi(nb), W = U_NU(site) (forward,
-// S = -1) or U_NU(nb)^dag (backward, S = +1).  Spin index a*3 + colour c.
+// One hop for NR fields: acc[i] += coef * (1 + S gamma_NU) W psi_i(nb), W =
+// U_NU(site) (forward, S = -1) or U_NU(nb)^dag (backward, S = +1).  Spin
+// index a*3 + colour c.
 //   (1 + S gamma) psi = [h ; S B^dag h],  h = psi_up + S B psi_dn,
 //   gamma_NU = [[0, B], [B^dag, 0]]:  B = -i sigma_{x,y,z}, or 1 for t.
-template <class R, class LinkT, int NU, int S>
-__device__ __forceinline__ void hop(Cx<R> acc[12], const typename Field<R>::T* __restrict__ in,
-                                    const LinkT* __restrict__ U, int64_t link_site, int64_t nb, R coef) {
-    Cx<R> p[12];
-    Field<R>::load(in, nb, p);
-    Cx<R> h0[3], h1[3];
+// Each link entry is loaded once and applied to the NR fields.
+template <class R, class LinkT, int NU, int S, int NR>
+__device__ __forceinline__ void hop(Cx<R> (&acc)[NR][12], const typename Field<R>::T* __restrict__ in,
+                                    int64_t stride_rhs, const bool (&act)[NR], const LinkT* __restrict__ U,
+                                    int64_t link_site, int64_t nb, R coef, int64_t vol) {
     const R s = R(S);
+    Cx<R> h0[NR][3], h1[NR][3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        Cx<R> p0 = p[c], p1 = p[3 + c], p2 = p[6 + c], p3 = p[9 + c];
-        if constexpr (NU == 0) {  // B psi_dn = (-i p3, -i p2)
-            h0[c] = p0 + scale(mul_mi(p3), s);
-            h1[c] = p1 + scale(mul_mi(p2), s);
-        } else if constexpr (NU == 1) {  // (-p3, p2)
-            h0[c] = p0 - scale(p3, s);
-            h1[c] = p1 + scale(p2, s);
-        } else if constexpr (NU == 2) {  // (-i p2, i p3)
-            h0[c] = p0 + scale(mul_mi(p2), s);
-            h1[c] = p1 + scale(mul_i(p3), s);
-        } else {  // (p2, p3)
-            h0[c] = p0 + scale(p2, s);
-            h1[c] = p1 + scale(p3, s);
+    for (int i = 0; i < NR; ++i) {
+        Cx<R> p[12];
+        if (act[i]) {
+            Field<R>::load(in + i * stride_rhs, nb, 2 * vol, p);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) p[k] = {R(0), R(0)};
         }
-    }
-    const int64_t lb = (link_site * 4 + NU) * 9;
-    Cx<R> g0[3], g1[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        g0[a] = {R(0), R(0)};
-        g1[a] = {R(0), R(0)};
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            if constexpr (S < 0) {  // U(site) h
-                Cx<R> u = Link<R, LinkT>::ld(U, lb + a * 3 + b);
-                cmac(g0[a], u, h0[b]);
-                cmac(g1[a], u, h1[b]);
-            } else {  // U(nb)^dag h: (U^dag)_{ab} = conj(U_{ba})
-                Cx<R> u = Link<R, LinkT>::ld(U, lb + b * 3 + a);
-                cmac_conj(g0[a], u, h0[b]);
-                cmac_conj(g1[a], u, h1[b]);
+        for (int c = 0; c < 3; ++c) {
+            Cx<R> p0 = p[c], p1 = p[3 + c], p2 = p[6 + c], p3 = p[9 + c];
+            if constexpr (NU == 0) {  // B psi_dn = (-i p3, -i p2)
+                h0[i][c] = p0 + scale(mul_mi(p3), s);
+                h1[i][c] = p1 + scale(mul_mi(p2), s);
+            } else if constexpr (NU == 1) {  // (-p3, p2)
+                h0[i][c] = p0 - scale(p3, s);
+                h1[i][c] = p1 + scale(p2, s);
+            } else if constexpr (NU == 2) {  // (-i p2, i p3)
+                h0[i][c] = p0 + scale(mul_mi(p2), s);
+                h1[i][c] = p1 + scale(mul_i(p3), s);
+            } else {  // (p2, p3)
+                h0[i][c] = p0 + scale(p2, s);
+                h1[i][c] = p1 + scale(p3, s);
             }
         }
     }
+    // packed links: entry (row, col) of U_NU(site) at ((NU * 9 + 3 row + col) * vol + site)
+    const LinkT* lb = U + (int64_t)NU * 9 * vol + link_site;
     const R cs = coef * s;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        acc[c] = acc[c] + scale(g0[c], coef);
-        acc[3 + c] = acc[3 + c] + scale(g1[c], coef);
-        if constexpr (NU == 0) {  // B^dag g = (i g1, i g0)
-            acc[6 + c] = acc[6 + c] + scale(mul_i(g1[c]), cs);
-            acc[9 + c] = acc[9 + c] + scale(mul_i(g0[c]), cs);
-        } else if constexpr (NU == 1) {  // (g1, -g0)
-            acc[6 + c] = acc[6 + c] + scale(g1[c], cs);
-            acc[9 + c] = acc[9 + c] - scale(g0[c], cs);
-        } else if constexpr (NU == 2) {  // (i g0, -i g1)
-            acc[6 + c] = acc[6 + c] + scale(mul_i(g0[c]), cs);
-            acc[9 + c] = acc[9 + c] + scale(mul_mi(g1[c]), cs);
-        } else {  // (g0, g1)
-            acc[6 + c] = acc[6 + c] + scale(g0[c], cs);
-            acc[9 + c] = acc[9 + c] + scale(g1[c], cs);
+    for (int a = 0; a < 3; ++a) {
+        Cx<R> g0[NR], g1[NR];
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            g0[i] = {R(0), R(0)};
+            g1[i] = {R(0), R(0)};
+        }
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            if constexpr (S < 0) {  // U(site) h
+                const Cx<R> u = Link<R, LinkT>::ld(lb, (a * 3 + b) * vol);
+#pragma unroll
+                for (int i = 0; i < NR; ++i) {
+                    cmac(g0[i], u, h0[i][b]);
+                    cmac(g1[i], u, h1[i][b]);
+                }
+            } else {  // U(nb)^dag h: (U^dag)_{ab} = conj(U_{ba})
+                const Cx<R> u = Link<R, LinkT>::ld(lb, (b * 3 + a) * vol);
+#pragma unroll
+                for (int i = 0; i < NR; ++i) {
+                    cmac_conj(g0[i], u, h0[i][b]);
+                    cmac_conj(g1[i], u, h1[i][b]);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            acc[i][a] = acc[i][a] + scale(g0[i], coef);
+            acc[i][3 + a] = acc[i][3 + a] + scale(g1[i], coef);
+            if constexpr (NU == 0) {  // B^dag g = (i g1, i g0)
+                acc[i][6 + a] = acc[i][6 + a] + scale(mul_i(g1[i]), cs);
+                acc[i][9 + a] = acc[i][9 + a] + scale(mul_i(g0[i]), cs);
+            } else if constexpr (NU == 1) {  // (g1, -g0)
+                acc[i][6 + a] = acc[i][6 + a] + scale(g1[i], cs);
+                acc[i][9 + a] = acc[i][9 + a] - scale(g0[i], cs);
+            } else if constexpr (NU == 2) {  // (i g0, -i g1)
+                acc[i][6 + a] = acc[i][6 + a] + scale(mul_i(g0[i]), cs);
+                acc[i][9 + a] = acc[i][9 + a] + scale(mul_mi(g1[i]), cs);
+            } else {  // (g0, g1)
+                acc[i][6 + a] = acc[i][6 + a] + scale(g0[i], cs);
+                acc[i][9 + a] = acc[i][9 + a] + scale(g1[i], cs);
+            }
         }
     }
 }
@@ -188,10 +223,10 @@ __device__ __forceinline__ R diag_of(const StencilParams& P) {
     if constexpr (sizeof(R) == 4) return P.diag32; else return P.diag;
 }
 
-template <class R, class LinkT, int NU>
-__device__ __forceinline__ void both_hops(Cx<R> acc[12], const typename Field<R>::T* __restrict__ in,
-                                          const LinkT* __restrict__ U, int64_t site, const int co[4],
-                                          const StencilParams& P) {
+template <class R, class LinkT, int NU, int NR>
+__device__ __forceinline__ void both_hops(Cx<R> (&acc)[NR][12], const typename Field<R>::T* __restrict__ in,
+                                          const bool (&act)[NR], const LinkT* __restrict__ U, int64_t site,
+                                          const int co[4], const StencilParams& P) {
     int64_t stride = 1;
 #pragma unroll
     for (int d = 0; d < NU; ++d) stride *= P.L[d];
@@ -209,20 +244,27 @@ __device__ __forceinline__ void both_hops(Cx<R> acc[12], const typename Field<R>
         bw = site + (int64_t)(L - 1) * stride;
         if (P.ap[NU]) cb = -cb;
     }
-    hop<R, LinkT, NU, -1>(acc, in, U, site, fw, cf);
-    hop<R, LinkT, NU, +1>(acc, in, U, bw, bw, cb);
+    hop<R, LinkT, NU, -1, NR>(acc, in, P.stride_rhs, act, U, site, fw, cf, P.vol);
+    hop<R, LinkT, NU, +1, NR>(acc, in, P.stride_rhs, act, U, bw, bw, cb, P.vol);
 }
 
-template <class R, class LinkT>
-__global__ void __launch_bounds__(384) k_hw(typename Field<R>::T* __restrict__ out,
-                                            const typename Field<R>::T* __restrict__ in,
-                                            const LinkT* __restrict__ U, int nrhs, StencilParams P,
-                                            const int* __restrict__ skip) {
+// Thread (x, y) of the CTA: site blockIdx.x * SX + x, fields NR (blockIdx.y * RB + y) + 0..NR-1.
+template <class R, class LinkT, int NR>
+__global__ void __launch_bounds__(NR == 1 ? 384 : 256)
+    k_hw(typename Field<R>::T* __restrict__ out, const typename Field<R>::T* __restrict__ in,
+         const LinkT* __restrict__ U, int nrhs, StencilParams P, const int* __restrict__ skip) {
     const int64_t site = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int rhs = blockIdx.y * blockDim.y + threadIdx.y;
-    if (site >= P.vol || rhs >= nrhs) return;
-    if (skip && skip[rhs]) return;
-    const typename Field<R>::T* fin = in + rhs * P.stride_rhs;
+    const int rhs0 = (blockIdx.y * blockDim.y + threadIdx.y) * NR;
+    if (site >= P.vol || rhs0 >= nrhs) return;
+    bool act[NR];
+    bool any = false;
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+        act[i] = rhs0 + i < nrhs && !(skip && skip[rhs0 + i]);
+        any |= act[i];
+    }
+    if (!any) return;
+    const typename Field<R>::T* fin = in + rhs0 * P.stride_rhs;
     int co[4];
     {
         // coordinates by exact multiply-shift division (no 64-bit integer division)
@@ -235,43 +277,130 @@ __global__ void __launch_bounds__(384) k_hw(typename Field<R>::T* __restrict__ o
         co[2] = (int)(q1 - q2 * (uint32_t)P.L[2]);
         co[3] = (int)q2;
     }
-    Cx<R> acc[12];
-    {
-        Field<R>::load(fin, site, acc);
-        const R d = diag_of<R>(P);
+    Cx<R> acc[NR][12];
+    const R d = diag_of<R>(P);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) acc[k] = scale(acc[k], d);
+    for (int i = 0; i < NR; ++i) {
+        if (act[i]) {
+            Field<R>::load(fin + i * P.stride_rhs, site, 2 * P.vol, acc[i]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) acc[i][k] = {R(0), R(0)};
+        }
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[i][k] = scale(acc[i][k], d);
     }
-    both_hops<R, LinkT, 0>(acc, fin, U, site, co, P);
-    both_hops<R, LinkT, 1>(acc, fin, U, site, co, P);
-    both_hops<R, LinkT, 2>(acc, fin, U, site, co, P);
-    both_hops<R, LinkT, 3>(acc, fin, U, site, co, P);
-    // gamma5 = diag(1, 1, -1, -1)
+    both_hops<R, LinkT, 0, NR>(acc, fin, act, U, site, co, P);
+    both_hops<R, LinkT, 1, NR>(acc, fin, act, U, site, co, P);
+    both_hops<R, LinkT, 2, NR>(acc, fin, act, U, site, co, P);
+    both_hops<R, LinkT, 3, NR>(acc, fin, act, U, site, co, P);
 #pragma unroll
-    for (int k = 6; k < 12; ++k) acc[k] = {-acc[k].x, -acc[k].y};
-    Field<R>::store(out + rhs * P.stride_rhs, site, acc);
+    for (int i = 0; i < NR; ++i) {
+        if (!act[i]) continue;
+        // gamma5 = diag(1, 1, -1, -1)
+#pragma unroll
+        for (int k = 6; k < 12; ++k) acc[i][k] = {-acc[i][k].x, -acc[i][k].y};
+        Field<R>::store(out + (rhs0 + i) * P.stride_rhs, site, 2 * P.vol, acc[i]);
+    }
+}
+
+// ---- layout conversions (one thread per site of one field) --------------------
+template <class T>
+__global__ void k_pack(const T* __restrict__ in, T* __restrict__ out, int64_t vol) {
+    const int64_t site = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= vol) return;
+    const int64_t f = (int64_t)blockIdx.y * 12 * vol;
+    const T* src = in + f + site * 12;
+    T* dst = out + f + 2 * site;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        dst[k * 2 * vol] = src[2 * k];
+        dst[k * 2 * vol + 1] = src[2 * k + 1];
+    }
+}
+template <class T>
+__global__ void k_unpack(const T* __restrict__ in, T* __restrict__ out, int64_t vol) {
+    const int64_t site = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= vol) return;
+    const int64_t f = (int64_t)blockIdx.y * 12 * vol;
+    const T* src = in + f + 2 * site;
+    T* dst = out + f + site * 12;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        dst[2 * k] = src[k * 2 * vol];
+        dst[2 * k + 1] = src[k * 2 * vol + 1];
+    }
+}
+__global__ void k_pack_links(const double2* __restrict__ in, double2* __restrict__ out, int64_t vol) {
+    const int64_t site = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= vol) return;
+#pragma unroll 4
+    for (int e = 0; e < 36; ++e) out[e * vol + site] = in[site * 36 + e];
+}
+
+template <class R, class LinkT, int NR>
+cudaError_t launch_nr(typename Field<R>::T* out, const typename Field<R>::T* in, const LinkT* U, int nrhs,
+                      const StencilParams& p, const int* skip, cudaStream_t st, int sx, int rb) {
+    const int groups = (nrhs + NR - 1) / NR;
+    dim3 block(sx, rb);
+    dim3 grid((unsigned)((p.vol + sx - 1) / sx), (unsigned)((groups + rb - 1) / rb));
+    k_hw<R, LinkT, NR><<<grid, block, 0, st>>>(out, in, U, nrhs, p, skip);
+    count_launch();
+    return cudaGetLastError();
 }
 
 template <class R, class LinkT>
 cudaError_t launch(typename Field<R>::T* out, const typename Field<R>::T* in, const LinkT* U, int nrhs,
                    const StencilParams& p, const int* skip, cudaStream_t st, StencilShape sh) {
     if (nrhs <= 0 || p.vol <= 0) return cudaSuccess;
+    if (sh.sx > 0 && sh.rb > 0) {  // a tuned shape: validate it against the kernel's launch bounds
+        const int maxnr = sizeof(R) == 8 ? 1 : 3;  // more fields per thread spill registers
+        if (sh.sx % 32 != 0 || sh.nr < 1 || sh.nr > maxnr || sh.sx * sh.rb > (sh.nr == 1 ? 384 : 256))
+            return cudaErrorInvalidValue;
+        if constexpr (sizeof(R) == 4) {
+            if (sh.nr == 2) return launch_nr<R, LinkT, 2>(out, in, U, nrhs, p, skip, st, sh.sx, sh.rb);
+            if (sh.nr == 3) return launch_nr<R, LinkT, 3>(out, in, U, nrhs, p, skip, st, sh.sx, sh.rb);
+        }
+        return launch_nr<R, LinkT, 1>(out, in, U, nrhs, p, skip, st, sh.sx, sh.rb);
+    }
+    // default: one field per thread, up to 12 fields of a site tile per CTA
     int rb = nrhs <= 12 ? nrhs : 8;
     int sx = 256 / rb;
     sx = sx < 32 ? 32 : (sx / 32) * 32;
     if (sx * rb > 384) sx = 32;
-    if (sh.sx > 0 && sh.rb > 0 && sh.sx % 32 == 0 && sh.sx * sh.rb <= 384) {
-        sx = sh.sx;
-        rb = sh.rb;
-    }
-    dim3 block(sx, rb);
-    dim3 grid((unsigned)((p.vol + sx - 1) / sx), (unsigned)((nrhs + rb - 1) / rb));
-    k_hw<R, LinkT><<<grid, block, 0, st>>>(out, in, U, nrhs, p, skip);
-    count_launch();
-    return cudaGetLastError();
+    return launch_nr<R, LinkT, 1>(out, in, U, nrhs, p, skip, st, sx, rb);
 }
 
 }  // namespace
+
+template <class T>
+cudaError_t pack_fields(const T* natural, T* packed, int64_t vol, int nfield, cudaStream_t st) {
+    if (nfield <= 0 || vol <= 0) return cudaSuccess;
+    if (nfield > 65535) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)((vol + 255) / 256), (unsigned)nfield);
+    k_pack<T><<<grid, 256, 0, st>>>(natural, packed, vol);
+    count_launch();
+    return cudaGetLastError();
+}
+template <class T>
+cudaError_t unpack_fields(const T* packed, T* natural, int64_t vol, int nfield, cudaStream_t st) {
+    if (nfield <= 0 || vol <= 0) return cudaSuccess;
+    if (nfield > 65535) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)((vol + 255) / 256), (unsigned)nfield);
+    k_unpack<T><<<grid, 256, 0, st>>>(packed, natural, vol);
+    count_launch();
+    return cudaGetLastError();
+}
+template cudaError_t pack_fields<double2>(const double2*, double2*, int64_t, int, cudaStream_t);
+template cudaError_t pack_fields<float2>(const float2*, float2*, int64_t, int, cudaStream_t);
+template cudaError_t unpack_fields<double2>(const double2*, double2*, int64_t, int, cudaStream_t);
+template cudaError_t unpack_fields<float2>(const float2*, float2*, int64_t, int, cudaStream_t);
+
+cudaError_t pack_links(const double2* natural, double2* packed, int64_t vol, cudaStream_t st) {
+    k_pack_links<<<(unsigned)((vol + 255) / 256), 256, 0, st>>>(natural, packed, vol);
+    count_launch();
+    return cudaGetLastError();
+}
 
 cudaError_t launch_hw_f64(double2* out, const double2* in, const double2* U, int nrhs, const StencilParams& p,
                           const int* skip, cudaStream_t st, StencilShape sh) {

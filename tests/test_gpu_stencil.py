@@ -77,3 +77,61 @@ def test_inner_products_match_numpy():
         got = ctx.inner_products(torch.from_numpy(V).cuda(), torch.from_numpy(w).cuda())
     ref = w @ V.conj().T
     np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_packed_layout_roundtrip_and_stencil():
+    """pack/unpack invert each other, the packed order is the documented one
+    (entry k of site s at (k/2) 2V + 2s + k%2), and the stencil on packed
+    fields equals the packed result of the stencil on natural fields."""
+    import paper_0910_2927_gb300 as pkg
+    dims, mu = (3, 4, 5, 6), 0.3
+    vol = int(np.prod(dims))
+    U = si.random_su3_links(dims, 0.7, 21)
+    b = si.gaussian_block(dims, 5, 22)
+    # the documented order, written out on the host
+    nat = b.reshape(5, vol, 6, 2)
+    want_packed = np.ascontiguousarray(nat.transpose(0, 2, 1, 3)).reshape(5, -1)
+    with _ctx(dims, U, mu) as ctx:
+        for prec, dt in ((pkg.PREC_FP64, np.complex128), (pkg.PREC_MIXED, np.complex64)):
+            bd = torch.from_numpy(b.astype(dt)).cuda()
+            pk = ctx.pack(bd, prec)
+            assert np.array_equal(pk.cpu().numpy(), want_packed.astype(dt))
+            assert torch.equal(ctx.unpack(pk, prec), bd)
+            for adj in (False, True):
+                direct = ctx.hw(pk, precision=prec, adjoint=adj, packed=True)
+                via = ctx.pack(ctx.hw(bd, precision=prec, adjoint=adj), prec)
+                assert torch.equal(direct, via)
+
+
+@pytest.mark.parametrize("shape", ["32,4,3", "64,2,2", "32,2,3", "64,3,1", "128,1,2"])
+def test_fp32_stencil_launch_shapes(shape, monkeypatch):
+    """Every launch shape (sites per CTA, thread rows, fields per thread) gives
+    the oracle's result, including field counts that leave the last thread's
+    group of fields ragged (5 fields, 3 per thread)."""
+    import paper_0910_2927_gb300 as pkg
+    monkeypatch.setenv("SGN_STENCIL_SHAPE", shape)
+    dims, mu = (5, 2, 3, 7), 0.3
+    U = si.random_su3_links(dims, 0.7, 31)
+    b = si.gaussian_block(dims, 5, 32)
+    with _ctx(dims, U, mu, (1, 1, 0, 1)) as ctx:
+        ctx.set_precision(pkg.PREC_MIXED, 1e-8, pkg.LINKS_FP32)
+        out = ctx.hw(torch.from_numpy(b).cuda(), precision=pkg.PREC_MIXED).cpu().numpy()
+        outa = ctx.hw(torch.from_numpy(b).cuda(), precision=pkg.PREC_MIXED, adjoint=True).cpu().numpy()
+    for r in range(5):
+        ref = O.hw(dims, U, b[r], mu, -1.6, (1, 1, 0, 1))
+        assert np.linalg.norm(out[r] - ref) / np.linalg.norm(ref) < 2e-6
+        refa = O.hw(dims, U, b[r], -mu, -1.6, (1, 1, 0, 1))
+        assert np.linalg.norm(outa[r] - refa) / np.linalg.norm(refa) < 2e-6
+
+
+def test_invalid_launch_shape_is_an_error(monkeypatch):
+    """A shape outside the kernel's limits is refused with an error, not launched."""
+    import paper_0910_2927_gb300 as pkg
+    monkeypatch.setenv("SGN_STENCIL_SHAPE", "32,12,3")  # 384 threads with 3 fields each
+    dims = (4, 4, 4, 4)
+    U = si.random_su3_links(dims, 0.7, 33)
+    b = si.gaussian_block(dims, 12, 34)
+    with _ctx(dims, U, 0.3) as ctx:
+        ctx.set_precision(pkg.PREC_MIXED, 1e-8, pkg.LINKS_FP32)
+        with pytest.raises(pkg.SignError):
+            ctx.hw(torch.from_numpy(b).cuda(), precision=pkg.PREC_MIXED)
