@@ -144,6 +144,13 @@ SGN_API int sgn_set_restart(sgn_ctx* ctx, int k, double tol, int max_cycles, int
  * links for the FP32 stencil. */
 SGN_API int sgn_set_precision(sgn_ctx* ctx, int precision, double target_rel_err, int link_storage);
 
+/* Mixed form only (no counterpart in the paper, which works in FP64): the
+ * restart length of the FP32 correction solves that bring each shifted
+ * system's true FP64 residual below the tolerance (0: min(k, 16)), and how many
+ * shifted systems one correction batch solves side by side (0: up to 4 nrhs,
+ * bounded by memory).  Errors: SGN_ERR_ARG (k_refine > 64, max_batch > 4096). */
+SGN_API int sgn_set_refinement(sgn_ctx* ctx, int k_refine, int max_batch);
+
 /* LR deflation data of Sec. 4 (eq. (4.1)): m right eigenvectors R and left
  * eigenvectors L (each n x m, column j = one field of n = 12 V complex128,
  * columns back to back), eigenvalues lambda (m complex128), normalised so that

@@ -113,6 +113,10 @@ class SignContext:
     def set_precision(self, precision=PREC_FP64, target_rel_err=1e-8, link_storage=LINKS_FP32):
         check(lib().sgn_set_precision(self._h, int(precision), float(target_rel_err), int(link_storage)))
 
+    def set_refinement(self, k_refine=0, max_batch=0):
+        """Mixed form: restart length and batch size of the correction solves (0: defaults)."""
+        check(lib().sgn_set_refinement(self._h, int(k_refine), int(max_batch)))
+
     # -- data ----------------------------------------------------------------
     def _as_c128(self, a):
         torch = _torch()

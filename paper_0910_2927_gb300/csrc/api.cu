@@ -238,6 +238,14 @@ SGN_API int sgn_set_precision(sgn_ctx* c, int precision, double target_rel_err, 
     return SGN_OK;
 }
 
+SGN_API int sgn_set_refinement(sgn_ctx* c, int k_refine, int max_batch) {
+    if (!c || k_refine < 0 || k_refine > 64 || max_batch < 0 || max_batch > 4096)
+        return fail(SGN_ERR_ARG, "sgn_set_refinement: need 0 <= k_refine <= 64, 0 <= max_batch <= 4096");
+    c->k_refine = k_refine;
+    c->refine_batch = max_batch;
+    return SGN_OK;
+}
+
 SGN_API int sgn_set_deflation(sgn_ctx* c, int m, const double* R, const double* L, const double* lambda,
                               int on_device) {
     if (!c || m < 0 || m > 64) return fail(SGN_ERR_ARG, "sgn_set_deflation: need 0 <= m <= 64");

@@ -4,8 +4,10 @@
 // update of Algorithm 1 and the LR projection r -> (I - R L^dag) r (Sec. 4).
 //
 // Element granularity is a 16-byte "pack": one complex128 or two complex64.
-// A thread owns PK packs of one column; a CTA of NT threads owns NT*PK
-// consecutive packs.  Dot products: each thread forms its PK pack products
+// A thread owns PKT packs of one column (PKT = 1, 2 or 4, a template
+// parameter); a CTA of NT threads owns NT*PKT consecutive packs.  The number
+// of CTAs per column is chosen so that the grid fills whole waves of the GPU
+// (wave_blocks), and PKT follows from it.  Dot products: each thread forms its PKT pack products
 // (in FP32 for complex64 storage, i.e. chunks of 8 complex products), promotes
 // them to FP64 and the rest of the reduction -- warp shuffles, the CTA sum and
 // the per-column sum over CTAs -- is FP64 in a fixed order (no atomics).
@@ -16,7 +18,7 @@ namespace {
 
 constexpr int NT = 256;
 constexpr int NWARP = NT / 32;
-constexpr int PK = 4;
+constexpr int PK = 4;  // default packs per thread (reduce_blocks)
 constexpr int MAXSLOT = 136;  // >= 2 kmax + 3 (delayed CGS2), >= deflation size + 1, >= eigensolver block + 1
 
 template <class T>
@@ -236,7 +238,7 @@ __device__ __forceinline__ void flush_partials(double2 (*sm)[NWARP], int nslot, 
 // ---------------------------------------------------------------- kernels --
 
 // partial[j] = sum_e conj(V_j[e]) w[e], j < J; slot J: ||w||^2 if with_norm.
-template <class T>
+template <class T, int PKT>
 __global__ void __launch_bounds__(NT) k_mdot(Basis<T> V, int J, const T* __restrict__ w, int64_t wsr, int64_t npk,
                                              Reduce rd, int with_norm, const int* __restrict__ skip) {
     using O = Ops<T>;
@@ -245,10 +247,10 @@ __global__ void __launch_bounds__(NT) k_mdot(Basis<T> V, int J, const T* __restr
     __shared__ double2 sm[MAXSLOT][NWARP];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const T* wc = w + col * wsr;
-    const int64_t base = (int64_t)blockIdx.x * NT * PK + threadIdx.x;
-    typename O::P wv[PK];
+    const int64_t base = (int64_t)blockIdx.x * NT * PKT + threadIdx.x;
+    typename O::P wv[PKT];
 #pragma unroll
-    for (int p = 0; p < PK; ++p) {
+    for (int p = 0; p < PKT; ++p) {
         int64_t i = base + p * NT;
         wv[p] = i < npk ? O::ld_ro(wc, i) : O::zero();
     }
@@ -256,9 +258,9 @@ __global__ void __launch_bounds__(NT) k_mdot(Basis<T> V, int J, const T* __restr
     for (int j = 0; j < J; ++j) {
         const T* vj = vb + j * V.sj;
         if constexpr (O::CPX == 2) {
-            float ax = 0.f, ay = 0.f;  // FP32 chunk of PK packs (8 complex products)
+            float ax = 0.f, ay = 0.f;  // FP32 chunk of PKT packs (8 complex products)
 #pragma unroll
-            for (int p = 0; p < PK; ++p) {
+            for (int p = 0; p < PKT; ++p) {
                 int64_t i = base + p * NT;
                 if (i < npk) O::dot_acc(ax, ay, O::ld_ro(vj, i), wv[p]);
             }
@@ -266,7 +268,7 @@ __global__ void __launch_bounds__(NT) k_mdot(Basis<T> V, int J, const T* __restr
         } else {
             double2 acc = make_double2(0, 0);
 #pragma unroll
-            for (int p = 0; p < PK; ++p) {
+            for (int p = 0; p < PKT; ++p) {
                 int64_t i = base + p * NT;
                 if (i < npk) acc = cadd(acc, O::dot(O::ld_ro(vj, i), wv[p]));
             }
@@ -278,12 +280,12 @@ __global__ void __launch_bounds__(NT) k_mdot(Basis<T> V, int J, const T* __restr
         if constexpr (O::CPX == 2) {
             float a = 0.f;
 #pragma unroll
-            for (int p = 0; p < PK; ++p) O::nrm2_acc(a, wv[p]);
+            for (int p = 0; p < PKT; ++p) O::nrm2_acc(a, wv[p]);
             warp_store_f(sm, J, a, 0.f, lane, warp);
         } else {
             double a = 0;
 #pragma unroll
-            for (int p = 0; p < PK; ++p) a += O::nrm2(wv[p]);
+            for (int p = 0; p < PKT; ++p) a += O::nrm2(wv[p]);
             double2 acc = warp_sum(make_double2(a, 0));
             if (lane == 0) sm[J][warp] = acc;
         }
@@ -292,7 +294,7 @@ __global__ void __launch_bounds__(NT) k_mdot(Basis<T> V, int J, const T* __restr
 }
 
 // w -= sum_j c_j V_j; then partial[j] = V_j^dag w (j < J) and slot J = ||w||^2.
-template <class T>
+template <class T, int PKT>
 __global__ void __launch_bounds__(NT) k_maxpy_mdot(Basis<T> V, int J, const double2* __restrict__ coef, int cstride,
                                                    T* w, int64_t wsr, int64_t npk, Reduce rd,
                                                    const int* __restrict__ skip) {
@@ -305,10 +307,10 @@ __global__ void __launch_bounds__(NT) k_maxpy_mdot(Basis<T> V, int J, const doub
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     T* wc = w + col * wsr;
-    const int64_t base = (int64_t)blockIdx.x * NT * PK + threadIdx.x;
-    typename O::P wv[PK];
+    const int64_t base = (int64_t)blockIdx.x * NT * PKT + threadIdx.x;
+    typename O::P wv[PKT];
 #pragma unroll
-    for (int p = 0; p < PK; ++p) {
+    for (int p = 0; p < PKT; ++p) {
         int64_t i = base + p * NT;
         wv[p] = i < npk ? O::ld(wc, i) : O::zero();
     }
@@ -317,13 +319,13 @@ __global__ void __launch_bounds__(NT) k_maxpy_mdot(Basis<T> V, int J, const doub
         const T* vj = vb + j * V.sj;
         const typename O::C c = cs[j];
 #pragma unroll
-        for (int p = 0; p < PK; ++p) {
+        for (int p = 0; p < PKT; ++p) {
             int64_t i = base + p * NT;
             if (i < npk) O::sub_cv(wv[p], c, O::ld_ro(vj, i));
         }
     }
 #pragma unroll
-    for (int p = 0; p < PK; ++p) {
+    for (int p = 0; p < PKT; ++p) {
         int64_t i = base + p * NT;
         if (i < npk) O::st(wc, i, wv[p]);
     }
@@ -332,7 +334,7 @@ __global__ void __launch_bounds__(NT) k_maxpy_mdot(Basis<T> V, int J, const doub
         if constexpr (O::CPX == 2) {
             float ax = 0.f, ay = 0.f;
 #pragma unroll
-            for (int p = 0; p < PK; ++p) {
+            for (int p = 0; p < PKT; ++p) {
                 int64_t i = base + p * NT;
                 if (i < npk) O::dot_acc(ax, ay, O::ld_ro(vj, i), wv[p]);
             }
@@ -340,7 +342,7 @@ __global__ void __launch_bounds__(NT) k_maxpy_mdot(Basis<T> V, int J, const doub
         } else {
             double2 acc = make_double2(0, 0);
 #pragma unroll
-            for (int p = 0; p < PK; ++p) {
+            for (int p = 0; p < PKT; ++p) {
                 int64_t i = base + p * NT;
                 if (i < npk) acc = cadd(acc, O::dot(O::ld_ro(vj, i), wv[p]));
             }
@@ -351,12 +353,12 @@ __global__ void __launch_bounds__(NT) k_maxpy_mdot(Basis<T> V, int J, const doub
     if constexpr (O::CPX == 2) {
         float a = 0.f;
 #pragma unroll
-        for (int p = 0; p < PK; ++p) O::nrm2_acc(a, wv[p]);
+        for (int p = 0; p < PKT; ++p) O::nrm2_acc(a, wv[p]);
         warp_store_f(sm, J, a, 0.f, lane, warp);
     } else {
         double a = 0;
 #pragma unroll
-        for (int p = 0; p < PK; ++p) a += O::nrm2(wv[p]);
+        for (int p = 0; p < PKT; ++p) a += O::nrm2(wv[p]);
         double2 acc = warp_sum(make_double2(a, 0));
         if (lane == 0) sm[J][warp] = acc;
     }
@@ -364,7 +366,7 @@ __global__ void __launch_bounds__(NT) k_maxpy_mdot(Basis<T> V, int J, const doub
 }
 
 // out = (w - sum_j c_j V_j) * scale[col]   (out may alias w)
-template <class T>
+template <class T, int PKT>
 __global__ void __launch_bounds__(NT) k_maxpy_scale(Basis<T> V, int J, const double2* __restrict__ coef, int cstride,
                                                     const T* w, int64_t wsr, T* out, int64_t osr,
                                                     const double* __restrict__ scale, int64_t npk,
@@ -378,10 +380,10 @@ __global__ void __launch_bounds__(NT) k_maxpy_scale(Basis<T> V, int J, const dou
     const T* wc = w + col * wsr;
     T* oc = out + col * osr;
     const double sc = scale ? scale[col] : 1.0;
-    const int64_t base = (int64_t)blockIdx.x * NT * PK + threadIdx.x;
-    typename O::P wv[PK];
+    const int64_t base = (int64_t)blockIdx.x * NT * PKT + threadIdx.x;
+    typename O::P wv[PKT];
 #pragma unroll
-    for (int p = 0; p < PK; ++p) {
+    for (int p = 0; p < PKT; ++p) {
         int64_t i = base + p * NT;
         wv[p] = i < npk ? O::ld(wc, i) : O::zero();
     }
@@ -390,7 +392,7 @@ __global__ void __launch_bounds__(NT) k_maxpy_scale(Basis<T> V, int J, const dou
         const T* vj = vb + j * V.sj;
         const typename O::C c = cs[j];
 #pragma unroll
-        for (int p = 0; p < PK; ++p) {
+        for (int p = 0; p < PKT; ++p) {
             int64_t i = base + p * NT;
             if (i < npk) O::sub_cv(wv[p], c, O::ld_ro(vj, i));
         }
@@ -398,13 +400,13 @@ __global__ void __launch_bounds__(NT) k_maxpy_scale(Basis<T> V, int J, const dou
     if constexpr (O::CPX == 2) {
         const float scf = (float)sc;
 #pragma unroll
-        for (int p = 0; p < PK; ++p) {
+        for (int p = 0; p < PKT; ++p) {
             int64_t i = base + p * NT;
             if (i < npk) O::st(oc, i, O::scalf(wv[p], scf));
         }
     } else {
 #pragma unroll
-        for (int p = 0; p < PK; ++p) {
+        for (int p = 0; p < PKT; ++p) {
             int64_t i = base + p * NT;
             if (i < npk) O::st(oc, i, O::scal(wv[p], sc));
         }
@@ -412,7 +414,7 @@ __global__ void __launch_bounds__(NT) k_maxpy_scale(Basis<T> V, int J, const dou
 }
 
 // x += sum_j c_j V_j in FP64 (x complex128), j < min(J, kk[col]).
-template <class T>
+template <class T, int PKT>
 __global__ void __launch_bounds__(NT) k_update_x(Basis<T> V, int J, const double2* __restrict__ coef, int cstride,
                                                  double2* __restrict__ x, int64_t xsr, int64_t npk,
                                                  const int* __restrict__ skip, const int* __restrict__ kk) {
@@ -425,19 +427,38 @@ __global__ void __launch_bounds__(NT) k_update_x(Basis<T> V, int J, const double
     __syncthreads();
     double2* xc = x + col * xsr;
     const T* vb = V.base + col * V.sr;
-    const int64_t base = (int64_t)blockIdx.x * NT * PK + threadIdx.x;
+    const int64_t base = (int64_t)blockIdx.x * NT * PKT + threadIdx.x;
+    double2 acc[PKT][O::CPX];
 #pragma unroll
-    for (int p = 0; p < PK; ++p) {
-        int64_t i = base + p * NT;
+    for (int p = 0; p < PKT; ++p)
+#pragma unroll
+        for (int q = 0; q < O::CPX; ++q) acc[p][q] = make_double2(0, 0);
+    constexpr int UNR = 8 / PKT;
+    for (int j0 = 0; j0 < J; j0 += UNR) {
+        typename O::P q[UNR][PKT];
+#pragma unroll
+        for (int g = 0; g < UNR; ++g) {
+            const T* vj = vb + (j0 + g) * V.sj;
+#pragma unroll
+            for (int p = 0; p < PKT; ++p) {
+                const int64_t i = base + p * NT;
+                q[g][p] = (j0 + g < J && i < npk) ? O::ld_ro(vj, i) : O::zero();
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < UNR; ++g)
+            if (j0 + g < J)
+#pragma unroll
+                for (int p = 0; p < PKT; ++p) O::add_cv_f64(acc[p], cs[j0 + g], q[g][p]);
+    }
+#pragma unroll
+    for (int p = 0; p < PKT; ++p) {
+        const int64_t i = base + p * NT;
         if (i >= npk) break;
-        double2 acc[O::CPX];
-#pragma unroll
-        for (int q = 0; q < O::CPX; ++q) acc[q] = make_double2(0, 0);
-        for (int j = 0; j < J; ++j) O::add_cv_f64(acc, cs[j], O::ld_ro(vb + j * V.sj, i));
 #pragma unroll
         for (int q = 0; q < O::CPX; ++q) {
             double2 a = xc[i * O::CPX + q];
-            xc[i * O::CPX + q] = make_double2(a.x + acc[q].x, a.y + acc[q].y);
+            xc[i * O::CPX + q] = make_double2(a.x + acc[p][q].x, a.y + acc[p][q].y);
         }
     }
 }
@@ -485,7 +506,7 @@ __global__ void __launch_bounds__(NT) k_update_shifts(Basis<T> V, int J, const d
 // once-orthogonalised candidate, z = A^2 u):  slots [0,J) s = Q^dag u,
 // [J,2J) t = Q^dag z, 2J: u^dag u, 2J+1: u^dag z, 2J+2: z^dag z.  With z = null
 // (the closing pass of a cycle) only s and u^dag u (slot J).
-template <class T>
+template <class T, int PKT>
 __global__ void __launch_bounds__(NT) k_dcgs_dots(Basis<T> V, int J, const T* __restrict__ u,
                                                   const T* __restrict__ z, int64_t wsr, int64_t npk, Reduce rd,
                                                   const int* __restrict__ skip) {
@@ -495,10 +516,10 @@ __global__ void __launch_bounds__(NT) k_dcgs_dots(Basis<T> V, int J, const T* __
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const T* uc = u + col * wsr;
     const T* zc = z ? z + col * wsr : nullptr;
-    const int64_t base = (int64_t)blockIdx.x * NT * PK + threadIdx.x;
-    typename O::P uv[PK], zv[PK];
+    const int64_t base = (int64_t)blockIdx.x * NT * PKT + threadIdx.x;
+    typename O::P uv[PKT], zv[PKT];
 #pragma unroll
-    for (int p = 0; p < PK; ++p) {
+    for (int p = 0; p < PKT; ++p) {
         int64_t i = base + p * NT;
         uv[p] = i < npk ? O::ld(uc, i) : O::zero();
         zv[p] = (zc && i < npk) ? O::ld(zc, i) : O::zero();
@@ -510,44 +531,71 @@ __global__ void __launch_bounds__(NT) k_dcgs_dots(Basis<T> V, int J, const T* __
         // over the whole CTA by one warp in double-float and written as this CTA's
         // FP64 partial.  Four values per vector: Re/Im of q^dag u and of q^dag z.
         constexpr int TL = 8;
-        __shared__ float st[TL * 4][NT];
+        __shared__ float st[TL * 4][NT + 8];  // rows padded: the segmented sums below are bank-conflict free
         double* pd = reinterpret_cast<double*>(rd.partial);
         auto put = [&](int slot, int comp, double v) {
             pd[2 * (((int64_t)col * rd.stride + slot) * rd.nblk + blockIdx.x) + comp] = v;
         };
         const int nv = zc ? 4 : 2;
+        // loads of GB basis vectors are issued together: 8 independent 16-byte
+        // loads in flight per thread (4 with PKT = 4, whose registers hold 4 packs
+        // of u and z already)
+        constexpr int GB = PKT == 4 ? 1 : 8 / PKT;
         for (int l0 = 0; l0 < J; l0 += TL) {
             const int tl = (J - l0) < TL ? (J - l0) : TL;
-            for (int g = 0; g < tl; ++g) {
-                const T* vl = vb + (l0 + g) * V.sj;
-                float sx = 0.f, sy = 0.f, tx = 0.f, ty = 0.f;
 #pragma unroll
-                for (int p = 0; p < PK; ++p) {
-                    int64_t i = base + p * NT;
-                    if (i < npk) {
-                        typename O::P q = O::ld_ro(vl, i);
-                        O::dot_acc(sx, sy, q, uv[p]);
-                        if (zc) O::dot_acc(tx, ty, q, zv[p]);
+            for (int g0 = 0; g0 < TL; g0 += GB) {
+                if (g0 >= tl) break;
+                typename O::P q[GB][PKT];
+#pragma unroll
+                for (int g = 0; g < GB; ++g) {
+                    const T* vl = vb + (l0 + g0 + g) * V.sj;
+#pragma unroll
+                    for (int p = 0; p < PKT; ++p) {
+                        const int64_t i = base + p * NT;
+                        q[g][p] = (g0 + g < tl && i < npk) ? O::ld_ro(vl, i) : O::zero();
                     }
                 }
-                st[g * 4 + 0][threadIdx.x] = sx;
-                st[g * 4 + 1][threadIdx.x] = sy;
-                st[g * 4 + 2][threadIdx.x] = tx;
-                st[g * 4 + 3][threadIdx.x] = ty;
+#pragma unroll
+                for (int g = 0; g < GB; ++g) {
+                    if (g0 + g < tl) {
+                        float sx = 0.f, sy = 0.f, tx = 0.f, ty = 0.f;
+#pragma unroll
+                        for (int p = 0; p < PKT; ++p) {
+                            O::dot_acc(sx, sy, q[g][p], uv[p]);
+                            if (zc) O::dot_acc(tx, ty, q[g][p], zv[p]);
+                        }
+                        st[(g0 + g) * 4 + 0][threadIdx.x] = sx;
+                        st[(g0 + g) * 4 + 1][threadIdx.x] = sy;
+                        st[(g0 + g) * 4 + 2][threadIdx.x] = tx;
+                        st[(g0 + g) * 4 + 3][threadIdx.x] = ty;
+                    }
+                }
             }
             __syncthreads();
-            for (int sl = warp; sl < tl * 4; sl += NWARP) {
+            {
+                // slot sl = tid / 8 (TL * 4 = 32 slots for 256 threads), summed by 8 lanes:
+                // lane seg adds values seg, seg + 8, ... in FP32, then a 3-level shuffle
+                // tree.  Every partial is a sum of at most a few hundred FP32 products
+                // (error ~ eps_32 times the sum of their moduli, the rounding the FP32
+                // products carry anyway); the sum over CTAs is FP64.
+                static_assert(TL * 4 * 8 == NT, "one 8-lane group per slot");
+                const int sl = threadIdx.x >> 3, seg = threadIdx.x & 7;
+                float a = 0.f;
+#pragma unroll
+                for (int k = 0; k < NT / 8; ++k) a += st[sl][k * 8 + seg];
+                a += __shfl_xor_sync(0xffffffffu, a, 1);
+                a += __shfl_xor_sync(0xffffffffu, a, 2);
+                a += __shfl_xor_sync(0xffffffffu, a, 4);
                 const int g = sl >> 2, v = sl & 3;
-                if (v >= nv) continue;
-                const double r = cta_sum_df(st[sl], lane);
-                if (lane == 0) put(v < 2 ? l0 + g : J + l0 + g, v & 1, r);
+                if (seg == 0 && g < tl && v < nv) put(v < 2 ? l0 + g : J + l0 + g, v & 1, (double)a);
             }
             __syncthreads();
         }
         // norms and u^dag z
         float a = 0.f, bx = 0.f, by = 0.f, gz = 0.f;
 #pragma unroll
-        for (int p = 0; p < PK; ++p) {
+        for (int p = 0; p < PKT; ++p) {
             O::nrm2_acc(a, uv[p]);
             if (zc) {
                 O::dot_acc(bx, by, uv[p], zv[p]);
@@ -578,54 +626,107 @@ __global__ void __launch_bounds__(NT) k_dcgs_dots(Basis<T> V, int J, const T* __
         }
         return;
     } else {
-        __shared__ double2 sm[MAXSLOT][NWARP];
-        for (int l = 0; l < J; ++l) {
-            const T* vl = vb + l * V.sj;
-            double2 as = make_double2(0, 0), at = make_double2(0, 0);
+        // FP64 storage: the same tiling with FP64 values; each (vector, component)
+        // slot is summed over the CTA by one warp in a fixed order (8 values per
+        // lane, then a shuffle tree), one warp-reduction per slot instead of one per
+        // warp and vector.
+        constexpr int TL = 4;
+        __shared__ double sd[TL * 4][NT];
+        double* pd = reinterpret_cast<double*>(rd.partial);
+        auto put = [&](int slot, int comp, double v) {
+            pd[2 * (((int64_t)col * rd.stride + slot) * rd.nblk + blockIdx.x) + comp] = v;
+        };
+        auto cta_sum = [&](const double* row) {
+            double a = 0;
 #pragma unroll
-            for (int p = 0; p < PK; ++p) {
-                int64_t i = base + p * NT;
-                if (i < npk) {
-                    typename O::P q = O::ld_ro(vl, i);
-                    as = cadd(as, O::dot(q, uv[p]));
-                    if (zc) at = cadd(at, O::dot(q, zv[p]));
+            for (int k = 0; k < NT / 32; ++k) a += row[lane + 32 * k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            return a;
+        };
+        const int nv = zc ? 4 : 2;
+        constexpr int GB = PKT == 4 ? 1 : 4 / PKT;
+        for (int l0 = 0; l0 < J; l0 += TL) {
+            const int tl = (J - l0) < TL ? (J - l0) : TL;
+#pragma unroll
+            for (int g0 = 0; g0 < TL; g0 += GB) {
+                if (g0 >= tl) break;
+                typename O::P q[GB][PKT];
+#pragma unroll
+                for (int g = 0; g < GB; ++g) {
+                    const T* vl = vb + (l0 + g0 + g) * V.sj;
+#pragma unroll
+                    for (int p = 0; p < PKT; ++p) {
+                        const int64_t i = base + p * NT;
+                        q[g][p] = (g0 + g < tl && i < npk) ? O::ld_ro(vl, i) : O::zero();
+                    }
+                }
+#pragma unroll
+                for (int g = 0; g < GB; ++g) {
+                    if (g0 + g < tl) {
+                        double2 as = make_double2(0, 0), at = make_double2(0, 0);
+#pragma unroll
+                        for (int p = 0; p < PKT; ++p) {
+                            as = cadd(as, O::dot(q[g][p], uv[p]));
+                            if (zc) at = cadd(at, O::dot(q[g][p], zv[p]));
+                        }
+                        sd[(g0 + g) * 4 + 0][threadIdx.x] = as.x;
+                        sd[(g0 + g) * 4 + 1][threadIdx.x] = as.y;
+                        sd[(g0 + g) * 4 + 2][threadIdx.x] = at.x;
+                        sd[(g0 + g) * 4 + 3][threadIdx.x] = at.y;
+                    }
                 }
             }
-            as = warp_sum(as);
-            if (lane == 0) sm[l][warp] = as;
-            if (zc) {
-                at = warp_sum(at);
-                if (lane == 0) sm[J + l][warp] = at;
+            __syncthreads();
+            for (int sl = warp; sl < tl * 4; sl += NWARP) {
+                const int g = sl >> 2, v = sl & 3;
+                if (v >= nv) continue;
+                const double r = cta_sum(sd[sl]);
+                if (lane == 0) put(v < 2 ? l0 + g : J + l0 + g, v & 1, r);
             }
+            __syncthreads();
         }
-        const int base_slot = zc ? 2 * J : J;
-        double a = 0;
-        double2 bz = make_double2(0, 0);
-        double g = 0;
+        // norms and u^dag z
+        double a = 0, bx = 0, by = 0, gz = 0;
 #pragma unroll
-        for (int p = 0; p < PK; ++p) {
+        for (int p = 0; p < PKT; ++p) {
             a += O::nrm2(uv[p]);
             if (zc) {
-                bz = cadd(bz, O::dot(uv[p], zv[p]));
-                g += O::nrm2(zv[p]);
+                const double2 d = O::dot(uv[p], zv[p]);
+                bx += d.x;
+                by += d.y;
+                gz += O::nrm2(zv[p]);
             }
         }
-        double2 r = warp_sum(make_double2(a, 0));
-        if (lane == 0) sm[base_slot][warp] = r;
-        if (zc) {
-            r = warp_sum(bz);
-            if (lane == 0) sm[base_slot + 1][warp] = r;
-            r = warp_sum(make_double2(g, 0));
-            if (lane == 0) sm[base_slot + 2][warp] = r;
+        sd[0][threadIdx.x] = a;
+        sd[1][threadIdx.x] = bx;
+        sd[2][threadIdx.x] = by;
+        sd[3][threadIdx.x] = gz;
+        __syncthreads();
+        const int bs = zc ? 2 * J : J;
+        if (warp < (zc ? 4 : 1)) {
+            const double r = cta_sum(sd[warp]);
+            if (lane == 0) {
+                if (warp == 0) {
+                    put(bs, 0, r);
+                    put(bs, 1, 0.0);
+                } else if (warp == 1) {
+                    put(bs + 1, 0, r);
+                } else if (warp == 2) {
+                    put(bs + 1, 1, r);
+                } else {
+                    put(bs + 2, 0, r);
+                    put(bs + 2, 1, 0.0);
+                }
+            }
         }
-        flush_partials(sm, zc ? 2 * J + 3 : J + 1, rd, col);
     }
 }
 
 // Delayed CGS2, update of step j:  q_j = (u - Q s) / rho  (written over u), and
 // the next candidate  u_{j+1} = z / rho - Q c - d q_j  (when next != null).
 // Coefficients per column: [0,J) s, [J,2J) c, 2J: (1/rho, 0), 2J+1: d.
-template <class T>
+template <class T, int PKT>
 __global__ void __launch_bounds__(NT) k_dcgs_update(Basis<T> V, int J, const double2* __restrict__ coef,
                                                     int cstride, T* u, const T* __restrict__ z, T* next,
                                                     int64_t wsr, int64_t npk, const int* __restrict__ skip) {
@@ -652,26 +753,52 @@ __global__ void __launch_bounds__(NT) k_dcgs_update(Basis<T> V, int J, const dou
     const T* zc = next ? z + col * wsr : nullptr;
     T* nc = next ? next + col * wsr : nullptr;
     const T* vb = V.base + col * V.sr;
-    const int64_t base = (int64_t)blockIdx.x * NT * PK + threadIdx.x;
+    const int64_t base = (int64_t)blockIdx.x * NT * PKT + threadIdx.x;
+    // Q s and Q c with the basis loop outside: the loads of UNR basis vectors
+    // (PKT packs each) are independent and in flight together
+    typename O::P qs[PKT], qc[PKT];
 #pragma unroll
-    for (int p = 0; p < PK; ++p) {
-        int64_t i = base + p * NT;
-        if (i >= npk) break;
-        typename O::P qs = O::zero(), qc = O::zero();
-        for (int l = 0; l < J; ++l) {
-            typename O::P q = O::ld_ro(vb + l * V.sj, i);
-            O::add_cv(qs, cs[l], q);
-            if (nc) O::add_cv(qc, cc[l], q);
+    for (int p = 0; p < PKT; ++p) {
+        qs[p] = O::zero();
+        qc[p] = O::zero();
+    }
+    constexpr int UNR = 8 / PKT;
+    for (int l0 = 0; l0 < J; l0 += UNR) {
+        typename O::P q[UNR][PKT];
+#pragma unroll
+        for (int g = 0; g < UNR; ++g) {
+            const T* vl = vb + (l0 + g) * V.sj;
+#pragma unroll
+            for (int p = 0; p < PKT; ++p) {
+                const int64_t i = base + p * NT;
+                q[g][p] = (l0 + g < J && i < npk) ? O::ld_ro(vl, i) : O::zero();
+            }
         }
+#pragma unroll
+        for (int g = 0; g < UNR; ++g) {
+            if (l0 + g < J) {
+                const typename O::C a = cs[l0 + g], c = cc[l0 + g];
+#pragma unroll
+                for (int p = 0; p < PKT; ++p) {
+                    O::add_cv(qs[p], a, q[g][p]);
+                    if (nc) O::add_cv(qc[p], c, q[g][p]);
+                }
+            }
+        }
+    }
+    typename O::C one;
+    if constexpr (O::CPX == 1) {
+        one = make_double2(1.0, 0.0);
+    } else {
+        one = make_float2(1.0f, 0.0f);
+    }
+#pragma unroll
+    for (int p = 0; p < PKT; ++p) {
+        const int64_t i = base + p * NT;
+        if (i >= npk) break;
         typename O::P uv = O::ld(uc, i);
         // q_j = (u - qs) / rho
-        typename O::C one;
-        if constexpr (O::CPX == 1) {
-            one = make_double2(1.0, 0.0);
-        } else {
-            one = make_float2(1.0f, 0.0f);
-        }
-        O::sub_cv(uv, one, qs);
+        O::sub_cv(uv, one, qs[p]);
         typename O::P qj;
         if constexpr (O::CPX == 2) {
             qj = O::scalf(uv, inv_rho_f);
@@ -686,7 +813,7 @@ __global__ void __launch_bounds__(NT) k_dcgs_update(Basis<T> V, int J, const dou
             } else {
                 nv = O::scal(O::ld(zc, i), inv_rho);
             }
-            O::sub_cv(nv, one, qc);
+            O::sub_cv(nv, one, qc[p]);
             O::sub_cv(nv, dd, qj);
             O::st(nc, i, nv);
         }
@@ -707,6 +834,9 @@ __global__ void __launch_bounds__(NT) k_reduce(Reduce rd, int nslot, int mode, i
     for (int j = warp; j < nslot; j += NWARP) {
         const double2* p = rd.partial + ((int64_t)col * rd.stride + j) * rd.nblk;
         double2 a = make_double2(0, 0);
+        // unrolled so that the loads of up to 8 partials per lane are in flight together
+        // (the sum order, b = lane, lane + 32, ..., is fixed either way)
+#pragma unroll 8
         for (int b = lane; b < rd.nblk; b += 32) a = cadd(a, p[b]);
         a = warp_sum(a);
         if (lane == 0) sums[j] = a;
@@ -1006,13 +1136,78 @@ int reduce_blocks(int64_t n) {
     return (int)(b < 1 ? 1 : b);
 }
 
+namespace {
+int sm_count() {
+    static const int n = [] {
+        int d = 0, v = 0;
+        if (cudaGetDevice(&d) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d) != cudaSuccess)
+            v = 0;
+        return v > 0 ? v : 152;
+    }();
+    return n;
+}
+
+// Packs per thread that nblk CTAs per column need for npk packs (0: too few CTAs).
+int pk_for(int64_t npk, int nblk) {
+    for (int pk = 1; pk <= 4; pk *= 2)
+        if ((int64_t)NT * pk * nblk >= npk) return pk;
+    return 0;
+}
+}  // namespace
+
+// The vector kernels hold 4 CTAs of NT threads per SM (64 registers, 32 KB of
+// shared memory).  A grid of 1.16 waves runs as long as 2 waves, so the CTAs per
+// column are picked from PKT = 4, 2, 1 (in that order of preference) for a grid
+// that fills at least 85 % of its last wave, else the fullest.
+template <class T>
+int wave_blocks(int64_t n, int ncol) {
+    const int64_t npk = n / Ops<T>::CPX;
+    const int64_t slots = (int64_t)sm_count() * 4;
+    int best = 1;
+    double best_eff = -1.0;
+    for (int pk = 4; pk >= 1; pk /= 2) {
+        int64_t nb = (npk + (int64_t)NT * pk - 1) / ((int64_t)NT * pk);
+        if (nb < 1) nb = 1;
+        const double waves = (double)(nb * (ncol > 0 ? ncol : 1)) / (double)slots;
+        const double eff = waves / std::ceil(waves);
+        if (eff >= 0.85) return (int)nb;
+        if (eff > best_eff) {
+            best_eff = eff;
+            best = (int)nb;
+        }
+    }
+    return best;
+}
+
+// Instantiate the kernel call for PKT = 1, 2 or 4.
+#define SGN_PK_SWITCH(PKV, ...)               \
+    switch (PKV) {                            \
+        case 1: {                             \
+            constexpr int PKT_ = 1;           \
+            __VA_ARGS__;                      \
+            break;                            \
+        }                                     \
+        case 2: {                             \
+            constexpr int PKT_ = 2;           \
+            __VA_ARGS__;                      \
+            break;                            \
+        }                                     \
+        case 4: {                             \
+            constexpr int PKT_ = 4;           \
+            __VA_ARGS__;                      \
+            break;                            \
+        }                                     \
+        default:                              \
+            return cudaErrorInvalidValue;     \
+    }
+
 template <class T>
 cudaError_t mdot(Basis<T> V, int J, const T* w, int64_t wsr, int64_t n, int ncol, const Reduce& rd, int with_norm,
                  const int* skip, cudaStream_t st) {
     if (J + 1 > MAXSLOT) return cudaErrorInvalidValue;
     int64_t npk = n / Ops<T>::CPX;
     dim3 grid(rd.nblk, ncol);
-    k_mdot<T><<<grid, NT, 0, st>>>(V, J, w, wsr, npk, rd, with_norm, skip);
+    SGN_PK_SWITCH(pk_for(npk, rd.nblk), k_mdot<T, PKT_><<<grid, NT, 0, st>>>(V, J, w, wsr, npk, rd, with_norm, skip))
     count_launch();
     return cudaGetLastError();
 }
@@ -1031,7 +1226,8 @@ cudaError_t maxpy_mdot(Basis<T> V, int J, const double2* coef, int cstride, T* w
     if (J + 1 > MAXSLOT) return cudaErrorInvalidValue;
     int64_t npk = n / Ops<T>::CPX;
     dim3 grid(rd.nblk, ncol);
-    k_maxpy_mdot<T><<<grid, NT, 0, st>>>(V, J, coef, cstride, w, wsr, npk, rd, skip);
+    SGN_PK_SWITCH(pk_for(npk, rd.nblk),
+                  k_maxpy_mdot<T, PKT_><<<grid, NT, 0, st>>>(V, J, coef, cstride, w, wsr, npk, rd, skip))
     count_launch();
     return cudaGetLastError();
 }
@@ -1041,8 +1237,10 @@ cudaError_t maxpy_scale(Basis<T> V, int J, const double2* coef, int cstride, con
                         int64_t osr, const double* scale, int64_t n, int ncol, const int* skip, cudaStream_t st) {
     if (J > MAXSLOT) return cudaErrorInvalidValue;
     int64_t npk = n / Ops<T>::CPX;
-    dim3 grid(reduce_blocks<T>(n), ncol);
-    k_maxpy_scale<T><<<grid, NT, 0, st>>>(V, J, coef, cstride, w, wsr, out, osr, scale, npk, skip);
+    const int nb = wave_blocks<T>(n, ncol);
+    dim3 grid(nb, ncol);
+    SGN_PK_SWITCH(pk_for(npk, nb), k_maxpy_scale<T, PKT_><<<grid, NT, 0, st>>>(V, J, coef, cstride, w, wsr, out, osr,
+                                                                              scale, npk, skip))
     count_launch();
     return cudaGetLastError();
 }
@@ -1052,8 +1250,10 @@ cudaError_t update_x(Basis<T> V, int J, const double2* coef, int cstride, double
                      int ncol, const int* skip, const int* kk, cudaStream_t st) {
     if (J > MAXSLOT) return cudaErrorInvalidValue;
     int64_t npk = n / Ops<T>::CPX;
-    dim3 grid(reduce_blocks<T>(n), ncol);
-    k_update_x<T><<<grid, NT, 0, st>>>(V, J, coef, cstride, x, xsr, npk, skip, kk);
+    const int nb = wave_blocks<T>(n, ncol);
+    dim3 grid(nb, ncol);
+    SGN_PK_SWITCH(pk_for(npk, nb),
+                  k_update_x<T, PKT_><<<grid, NT, 0, st>>>(V, J, coef, cstride, x, xsr, npk, skip, kk))
     count_launch();
     return cudaGetLastError();
 }
@@ -1076,7 +1276,7 @@ cudaError_t dcgs_dots(Basis<T> V, int J, const T* u, const T* z, int64_t wsr, in
     if (2 * J + 3 > MAXSLOT) return cudaErrorInvalidValue;
     int64_t npk = n / Ops<T>::CPX;
     dim3 grid(rd.nblk, ncol);
-    k_dcgs_dots<T><<<grid, NT, 0, st>>>(V, J, u, z, wsr, npk, rd, skip);
+    SGN_PK_SWITCH(pk_for(npk, rd.nblk), k_dcgs_dots<T, PKT_><<<grid, NT, 0, st>>>(V, J, u, z, wsr, npk, rd, skip))
     count_launch();
     return cudaGetLastError();
 }
@@ -1086,8 +1286,10 @@ cudaError_t dcgs_update(Basis<T> V, int J, const double2* coef, int cstride, T* 
                         int64_t n, int ncol, const int* skip, cudaStream_t st) {
     if (J > MAXSLOT) return cudaErrorInvalidValue;
     int64_t npk = n / Ops<T>::CPX;
-    dim3 grid(reduce_blocks<T>(n), ncol);
-    k_dcgs_update<T><<<grid, NT, 0, st>>>(V, J, coef, cstride, u, z, next, wsr, npk, skip);
+    const int nb = wave_blocks<T>(n, ncol);
+    dim3 grid(nb, ncol);
+    SGN_PK_SWITCH(pk_for(npk, nb), k_dcgs_update<T, PKT_><<<grid, NT, 0, st>>>(V, J, coef, cstride, u, z, next, wsr,
+                                                                              npk, skip))
     count_launch();
     return cudaGetLastError();
 }
@@ -1154,6 +1356,7 @@ cudaError_t links_f64_to_bf16(const double2* in, __nv_bfloat162* out, int64_t co
 
 #define SGN_INST(T)                                                                                              \
     template int reduce_blocks<T>(int64_t);                                                                      \
+    template int wave_blocks<T>(int64_t, int);                                                                   \
     template cudaError_t mdot<T>(Basis<T>, int, const T*, int64_t, int64_t, int, const Reduce&, int, const int*, \
                                  cudaStream_t);                                                                  \
     template cudaError_t maxpy_mdot<T>(Basis<T>, int, const double2*, int, T*, int64_t, int64_t, int,           \

@@ -95,5 +95,9 @@ cudaError_t combine_shifts(const DevState& S, int ncol, cudaStream_t st);
 // Number of blocks per column used by the reductions for n complex elements.
 template <class T>
 int reduce_blocks(int64_t n);
+// CTAs per column for a grid of ncol columns that fills whole waves (1, 2 or 4
+// packs per thread); a Reduce built with it serves every kernel of the file.
+template <class T>
+int wave_blocks(int64_t n, int ncol);
 
 }  // namespace sgn

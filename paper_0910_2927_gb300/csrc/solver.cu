@@ -418,7 +418,7 @@ int get_engine(sgn_ctx* c, int ncol, int k, int s, int prec, Engine** out) {
     E->m = c->m;
     E->n = c->n;
     const size_t esz = prec == SGN_PREC_FP64 ? sizeof(double2) : sizeof(float2);
-    E->nblk = prec == SGN_PREC_FP64 ? reduce_blocks<double2>(c->n) : reduce_blocks<float2>(c->n);
+    E->nblk = prec == SGN_PREC_FP64 ? wave_blocks<double2>(c->n, ncol) : wave_blocks<float2>(c->n, ncol);
     int rs = std::max(2 * k + 4, c->m + 1);
     E->rstride = (rs + 7) & ~7;
     const size_t nc = (size_t)ncol;
@@ -658,11 +658,16 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
     const int m = c->m;
     Engine* E = nullptr;
     SGN_CHECK(get_engine(c, ncol, k, s, SGN_PREC_MIXED, &E));
-    // refinement batch: one shifted system per column, bounded by memory
-    const size_t per_col = (size_t)(k + 4) * n * sizeof(float2) + (size_t)n * sizeof(double2);
-    int B = (int)std::min<size_t>({(size_t)s * ncol, (size_t)4 * ncol, std::max<size_t>(1, kRefineBudgetBytes / per_col)});
+    // refinement batch: one shifted system per column, bounded by memory.  The
+    // corrections only have to gain a factor tol / (FP32 floor ~1e-6) and most of
+    // them converge in a few steps, so they restart sooner than the multishift
+    // phase: a cycle of the engine always runs all its k_refine steps.
+    const int k1 = c->k_refine > 0 ? c->k_refine : std::min(k, 16);
+    const size_t per_col = (size_t)(k1 + 4) * n * sizeof(float2) + (size_t)n * sizeof(double2);
+    size_t bmax = c->refine_batch > 0 ? (size_t)c->refine_batch : (size_t)4 * ncol;
+    int B = (int)std::min<size_t>({(size_t)s * ncol, bmax, std::max<size_t>(1, kRefineBudgetBytes / per_col)});
     Engine* E1 = nullptr;
-    SGN_CHECK(get_engine(c, B, k, 1, SGN_PREC_MIXED, &E1));
+    SGN_CHECK(get_engine(c, B, k1, 1, SGN_PREC_MIXED, &E1));
 
     // io: xs (s ncol) | r0, bt, xP, t, u (ncol each) | d (B) | omega table | FP64 partials
     const size_t field = (size_t)n * sizeof(double2);
@@ -801,6 +806,7 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
         SGN_CUDA(cudaMemcpyAsync(hall.data(), S64.red, sizeof(double2) * hall.size(), cudaMemcpyDeviceToHost, st));
         SGN_CUDA(cudaStreamSynchronize(st));
         std::vector<std::pair<int, int>> todo;  // (shift, column)
+        std::vector<double> todo_rel;           // its relative true residual
         worst = 0;
         for (int i = 0; i < s; ++i)
             for (int col = 0; col < ncol; ++col) {
@@ -811,7 +817,10 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
                     return SGN_ERR_NONFINITE;
                 }
                 worst = std::max(worst, rel);
-                if (rel > c->tol) todo.emplace_back(i, col);
+                if (rel > c->tol) {
+                    todo.emplace_back(i, col);
+                    todo_rel.push_back(rel);
+                }
             }
         if (debug_log())
             fprintf(stderr, "[sgn mixed] round %d: worst true residual %.3e, %zu of %d systems above tol\n", round,
@@ -851,11 +860,16 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
                 SGN_CUDA(convert_f64_to_f32(rsd + ((size_t)i * ncol + col) * n, V0 + (size_t)j * n, n, st));
             }
             SGN_CUDA(cudaMemsetAsync(d, 0, field * B, st));
+            // the correction needs to reduce the worst residual of the batch to a third
+            // of the tolerance, not further (FP32 bases reach about 1e-6 at best)
+            double brel = 0;
+            for (int j = 0; j < nb; ++j) brel = std::max(brel, todo_rel[t0 + j]);
+            const double inner = std::min(0.1, std::max(1e-5, c->tol / (3.0 * brel)));
             RunResult r1;
-            int st1 = run_engine<float2>(c, *E1, a1, std::max(c->tol, 1e-5), c->max_cycles, &r1);
+            int st1 = run_engine<float2>(c, *E1, a1, inner, c->max_cycles, &r1);
             if (debug_log())
-                fprintf(stderr, "[sgn mixed]   batch at %zu (%d systems): status %d cycles %d resmax %.3e\n", t0, nb,
-                        st1, r1.cycles, r1.resmax);
+                fprintf(stderr, "[sgn mixed]   batch at %zu (%d systems): inner tol %.1e status %d cycles %d resmax %.3e\n",
+                        t0, nb, inner, st1, r1.cycles, r1.resmax);
             if (st1 != SGN_OK) return st1;
             ref_cycles += r1.cycles;
             for (int j = 0; j < nb; ++j) {

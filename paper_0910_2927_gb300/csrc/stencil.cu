@@ -64,13 +64,21 @@ struct Field<double> {
             p[2 * k + 1] = {b.x, b.y};
         }
     }
+    // CS: evict-first stores (see k_hw)
+    template <bool CS>
     static __device__ __forceinline__ void store(double2* __restrict__ f, int64_t site, int64_t vol2,
                                                  const Cx<double> p[12]) {
         double2* s = f + 2 * site;
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            s[k * vol2] = make_double2(p[2 * k].x, p[2 * k].y);
-            s[k * vol2 + 1] = make_double2(p[2 * k + 1].x, p[2 * k + 1].y);
+            const double2 a = make_double2(p[2 * k].x, p[2 * k].y), b = make_double2(p[2 * k + 1].x, p[2 * k + 1].y);
+            if constexpr (CS) {
+                __stcs(s + k * vol2, a);
+                __stcs(s + k * vol2 + 1, b);
+            } else {
+                s[k * vol2] = a;
+                s[k * vol2 + 1] = b;
+            }
         }
     }
 };
@@ -87,13 +95,18 @@ struct Field<float> {
             p[2 * k + 1] = {v.z, v.w};
         }
     }
+    template <bool CS>
     static __device__ __forceinline__ void store(float2* __restrict__ f, int64_t site, int64_t vol2,
                                                  const Cx<float> p[12]) {
         float2* s = f + 2 * site;
 #pragma unroll
-        for (int k = 0; k < 6; ++k)
-            *reinterpret_cast<float4*>(s + k * vol2) =
-                make_float4(p[2 * k].x, p[2 * k].y, p[2 * k + 1].x, p[2 * k + 1].y);
+        for (int k = 0; k < 6; ++k) {
+            const float4 v = make_float4(p[2 * k].x, p[2 * k].y, p[2 * k + 1].x, p[2 * k + 1].y);
+            if constexpr (CS)
+                __stcs(reinterpret_cast<float4*>(s + k * vol2), v);
+            else
+                *reinterpret_cast<float4*>(s + k * vol2) = v;
+        }
     }
 };
 
@@ -248,13 +261,22 @@ __device__ __forceinline__ void both_hops(Cx<R> (&acc)[NR][12], const typename F
     hop<R, LinkT, NU, +1, NR>(acc, in, P.stride_rhs, act, U, bw, bw, cb, P.vol);
 }
 
-// Thread (x, y) of the CTA: site blockIdx.x * SX + x, fields NR (blockIdx.y * RB + y) + 0..NR-1.
-template <class R, class LinkT, int NR>
+// CTA b of the 1D grid covers site tile b / ngrp and field group b % ngrp: the
+// field groups of a site tile run back to back, so the link and neighbour lines
+// they share are read from HBM once (with the tile index fastest, each field
+// group would sweep the whole lattice and re-read every link from HBM).
+// Thread (x, y): site tile * SX + x, fields NR (group * RB + y) + 0..NR-1.
+// CS: evict-first stores, for field sets far larger than L2, where a spinor is
+// last read as the neighbour of a site one time slice away and the streaming
+// result would otherwise push it out of L2 first.
+template <class R, class LinkT, int NR, bool CS>
 __global__ void __launch_bounds__(NR == 1 ? 384 : 256)
     k_hw(typename Field<R>::T* __restrict__ out, const typename Field<R>::T* __restrict__ in,
-         const LinkT* __restrict__ U, int nrhs, StencilParams P, const int* __restrict__ skip) {
-    const int64_t site = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int rhs0 = (blockIdx.y * blockDim.y + threadIdx.y) * NR;
+         const LinkT* __restrict__ U, int nrhs, StencilParams P, const int* __restrict__ skip, int ngrp) {
+    const int64_t tile = blockIdx.x / (unsigned)ngrp;
+    const int grp = (int)(blockIdx.x - tile * ngrp);
+    const int64_t site = tile * blockDim.x + threadIdx.x;
+    const int rhs0 = (grp * blockDim.y + threadIdx.y) * NR;
     if (site >= P.vol || rhs0 >= nrhs) return;
     bool act[NR];
     bool any = false;
@@ -300,7 +322,7 @@ __global__ void __launch_bounds__(NR == 1 ? 384 : 256)
         // gamma5 = diag(1, 1, -1, -1)
 #pragma unroll
         for (int k = 6; k < 12; ++k) acc[i][k] = {-acc[i][k].x, -acc[i][k].y};
-        Field<R>::store(out + (rhs0 + i) * P.stride_rhs, site, 2 * P.vol, acc[i]);
+        Field<R>::template store<CS>(out + (rhs0 + i) * P.stride_rhs, site, 2 * P.vol, acc[i]);
     }
 }
 
@@ -342,9 +364,15 @@ template <class R, class LinkT, int NR>
 cudaError_t launch_nr(typename Field<R>::T* out, const typename Field<R>::T* in, const LinkT* U, int nrhs,
                       const StencilParams& p, const int* skip, cudaStream_t st, int sx, int rb) {
     const int groups = (nrhs + NR - 1) / NR;
+    const int ngrp = (groups + rb - 1) / rb;
+    const int64_t tiles = (p.vol + sx - 1) / sx;
+    if (tiles * ngrp > 0x7fffffffLL) return cudaErrorInvalidValue;
     dim3 block(sx, rb);
-    dim3 grid((unsigned)((p.vol + sx - 1) / sx), (unsigned)((groups + rb - 1) / rb));
-    k_hw<R, LinkT, NR><<<grid, block, 0, st>>>(out, in, U, nrhs, p, skip);
+    const bool cs = (double)nrhs * (double)p.vol * 12.0 * sizeof(typename Field<R>::T) > 256.0 * (1 << 20);
+    if (cs)
+        k_hw<R, LinkT, NR, true><<<(unsigned)(tiles * ngrp), block, 0, st>>>(out, in, U, nrhs, p, skip, ngrp);
+    else
+        k_hw<R, LinkT, NR, false><<<(unsigned)(tiles * ngrp), block, 0, st>>>(out, in, U, nrhs, p, skip, ngrp);
     count_launch();
     return cudaGetLastError();
 }

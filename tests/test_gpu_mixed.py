@@ -69,3 +69,37 @@ def test_mixed_point_sources_config1(lattice4):
         xo, _, _ = O.fom_lr(d["dims"], d["U"], b[r], d["mu"], sigma, omega, k=30, tol=1e-12, R=d["R"],
                             L=d["L"], lam=d["lam"])
         assert _rel(x[r], xo) < TOL_MIXED
+
+
+@pytest.mark.parametrize("k_refine,batch", [(4, 5), (24, 0), (0, 7)])
+def test_mixed_refinement_settings(small, k_refine, batch):
+    """The correction solves' restart length and batch size change the work,
+    not the result: every setting meets the tolerance and the oracle's x."""
+    import paper_0910_2927_gb300 as pkg
+    d = small
+    c = O.scale_from_bounds(abs(d["nxt"][0]), 6.5)
+    sigma, omega = O.kenney_laub(12, c)
+    b = si.gaussian_block(d["dims"], 2, 43)
+    with pkg.SignContext(d["dims"], mu=d["mu"]) as ctx:
+        ctx.load_gauge(torch.from_numpy(d["U"]).cuda())
+        ctx.set_rational(sigma, omega)
+        ctx.set_restart(k=16, tol=1e-10, max_cycles=2000)
+        ctx.set_deflation(d["R"], d["L"], d["lam"])
+        ctx.set_precision(pkg.PREC_MIXED, 1e-8)
+        ctx.set_refinement(k_refine, batch)
+        x, rep = ctx.apply(torch.from_numpy(b).cuda())
+        x = x.cpu().numpy()
+    assert rep["status"] == 0 and rep["err_est"] <= 1e-10, rep
+    for r in range(2):
+        xo, _, _ = O.fom_lr(d["dims"], d["U"], b[r], d["mu"], sigma, omega, k=16, tol=1e-12, max_cycles=5000,
+                            R=d["R"], L=d["L"], lam=d["lam"])
+        assert _rel(x[r], xo) < TOL_MIXED
+
+
+def test_refinement_setting_errors():
+    import paper_0910_2927_gb300 as pkg
+    with pkg.SignContext((2, 2, 2, 2)) as ctx:
+        with pytest.raises(pkg.SignError):
+            ctx.set_refinement(65, 0)
+        with pytest.raises(pkg.SignError):
+            ctx.set_refinement(8, -1)
