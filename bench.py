@@ -319,7 +319,8 @@ def run_ours(args, w, name):
         torch.cuda.nvtx.range_pop()
     t_mixed = e0.elapsed_time(e1) / 1000.0
     kt = {}
-    for cls, name_k in ((0, "k_hw<float,float2>"), (1, "k_dcgs_dots<float2>"), (2, "k_dcgs_update<float2>")):
+    for cls, name_k in ((0, "k_hw<float,float2>"), (1, "k_dcgs_dots<float2>"), (2, "k_dcgs_update<float2>"),
+                        (3, "k_reduce"), (4, "k_update_shifts<float2>")):
         ms, nl, by = C.c_double(), C.c_longlong(), C.c_double()
         lib.sgn_get_kernel_timing(ctx._h, cls, C.byref(ms), C.byref(nl), C.byref(by))
         kt[name_k] = {"ms": ms.value, "launches": nl.value, "bytes": by.value}
@@ -330,6 +331,25 @@ def run_ours(args, w, name):
     value = units / t_max
     err = None if x64 is None else float(torch.linalg.vector_norm(xm - x64) / torch.linalg.vector_norm(x64))
     err_mixed, err_fp64 = rel_err(xm), (rel_err(x64) if x64 is not None else None)
+
+    # ---- both forms once more at tol 1e-10 (one warm solve each), beside the headline tolerance
+    at_1e10 = None
+    if not args.skip_fp64_form and TOL != 1e-10:
+        at_1e10 = {}
+        ctx.set_restart(k=w["k"], tol=1e-10, max_cycles=2000)
+        for form, prec in (("fp64_form", pkg.PREC_FP64), ("mixed", pkg.PREC_MIXED)):
+            ctx.set_precision(prec, 1e-8, pkg.LINKS_FP32)
+            ctx.apply(bdev)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            xa, repa = ctx.apply(bdev)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            at_1e10[form] = {"value": nrhs / (e0.elapsed_time(e1) / 1000.0), "unit": "solves/s",
+                             "cycles": repa["cycles"], "refine_cycles": repa["refine_cycles"],
+                             "rel_err": rel_err(xa)}
+        ctx.set_restart(k=w["k"], tol=TOL, max_cycles=2000)
+        ctx.set_precision(pkg.PREC_MIXED, 1e-8, pkg.LINKS_FP32)
 
     # ---- end to end through the ABI with host buffers (copies inside the timed region)
     Bh = np.ascontiguousarray(B)
@@ -375,6 +395,7 @@ def run_ours(args, w, name):
                         "reference": "FP64 form at tol 1e-12, max over columns of ||x - x_ref|| / ||x_ref||"},
             "fp64_form": None if rep64 is None else {"value": fp64_value, "unit": UNIT, "cycles": rep64["cycles"],
                                                      "ms": t64 * 1000},
+            "at_tol_1e-10": at_1e10,
             "mixed_report": {k2: reps[-1][k2] for k2 in ("cycles", "refine_rounds", "refine_cycles", "err_est")},
             "stencil_24^4": st,
             "kernel_times": kt,
@@ -390,16 +411,21 @@ def run_ours(args, w, name):
 
 
 # DRAM bytes (read + write) per algorithmic byte of a kernel, from one ncu capture of the
-# kernel as it stands (profiles/k_dcgs_dots_10x4_mixed.md: 372.4 MB for 368.6 MB at J = 30).
-# An entry must be removed when its kernel changes.
-DRAM_PER_ALGORITHMIC_BYTE = {"k_dcgs_dots<float2>": 372.4 / 368.6}
+# kernel as it stands (the capture is summarised under profiles/).  An entry must be
+# removed when its kernel changes.
+DRAM_PER_ALGORITHMIC_BYTE = {
+    # profiles/k_dcgs_dots_update_10x4_mixed.md, multishift step J = 30 of the 10^4 workload
+    "k_dcgs_dots<float2>": (368.7 + 5.5) / 368.6,
+    "k_dcgs_update<float2>": (368.7 + 19.1) / (368.6 + 23.0),
+}
 
 
 def roofline(kt, hbm, peak_src, t_timed):
     """Dominant kernel of the timed steps (largest summed event time): algorithmic
     bytes per launch / average launch duration, against the measured HBM copy rate;
     traffic = the measured DRAM-to-algorithmic ratio times the average launch's bytes."""
-    name = max(kt, key=lambda k: kt[k]["ms"])
+    # the bandwidth-bound classes (k_reduce sums a few KB of partials per column: latency, not HBM)
+    name = max((k for k in kt if k != "k_reduce"), key=lambda k: kt[k]["ms"])
     d = kt[name]
     if not d["launches"]:
         return None

@@ -258,7 +258,9 @@ SGN_API int sgn_grad_mu(sgn_ctx* ctx, const double* b, const double* g, int nrhs
 /* Kernel timing (observability).  With on = 1, later solves record CUDA events
  * around every launch of the restart cycle's main kernels, inside the captured
  * graph, and accumulate per class: 0 = Wilson stencil, 1 = fused Gram-Schmidt
- * reduction (k_dcgs_dots), 2 = fused Gram-Schmidt update (k_dcgs_update).
+ * reduction (k_dcgs_dots), 2 = fused Gram-Schmidt update (k_dcgs_update),
+ * 3 = second stage of those reductions with the step's scalar work (k_reduce),
+ * 4 = per-shift update x_i += V y_i (k_update_shifts).
  * Each event pair brackets one launch on the solver's stream.  Switching on or
  * off resets the totals. */
 SGN_API int sgn_set_kernel_timing(sgn_ctx* ctx, int on);

@@ -530,7 +530,7 @@ SGN_API int sgn_inner_products(sgn_ctx* c, const double* V, int J, const double*
 SGN_API int sgn_set_kernel_timing(sgn_ctx* c, int on) {
     if (!c) return fail(SGN_ERR_ARG, "sgn_set_kernel_timing: NULL context");
     c->timing = on ? 1 : 0;
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < sgn_ctx::kTimedClasses; ++i) {
         c->t_ms[i] = 0;
         c->t_launches[i] = 0;
         c->t_bytes[i] = 0;
@@ -539,7 +539,7 @@ SGN_API int sgn_set_kernel_timing(sgn_ctx* c, int on) {
 }
 
 SGN_API int sgn_get_kernel_timing(sgn_ctx* c, int cls, double* ms, long long* launches, double* bytes) {
-    if (!c || cls < 0 || cls > 2) return fail(SGN_ERR_ARG, "sgn_get_kernel_timing: bad argument");
+    if (!c || cls < 0 || cls >= sgn_ctx::kTimedClasses) return fail(SGN_ERR_ARG, "sgn_get_kernel_timing: bad argument");
     if (ms) *ms = c->t_ms[cls];
     if (launches) *launches = c->t_launches[cls];
     if (bytes) *bytes = c->t_bytes[cls];

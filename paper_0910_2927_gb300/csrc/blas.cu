@@ -13,6 +13,8 @@
 // the per-column sum over CTAs -- is FP64 in a fixed order (no atomics).
 #include "blas.cuh"
 
+#include <algorithm>
+
 namespace sgn {
 namespace {
 
@@ -490,11 +492,17 @@ __global__ void __launch_bounds__(NT) k_update_shifts(Basis<T> V, int J, const d
         typename O::P acc[SG];
 #pragma unroll
         for (int g = 0; g < SG; ++g) acc[g] = O::zero();
-        for (int j = 0; j < J; ++j) {
-            typename O::P v = O::ld_ro(vb + j * V.sj, i);
+        // loads of 4 basis vectors in flight together
+        for (int j0 = 0; j0 < J; j0 += 4) {
+            typename O::P v[4];
 #pragma unroll
-            for (int g = 0; g < SG; ++g)
-                if (g < ng) O::add_cv(acc[g], ys[(g0 + g) * J + j], v);
+            for (int u = 0; u < 4; ++u) v[u] = j0 + u < J ? O::ld_ro(vb + (j0 + u) * V.sj, i) : O::zero();
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (j0 + u < J)
+#pragma unroll
+                    for (int g = 0; g < SG; ++g)
+                        if (g < ng) O::add_cv(acc[g], ys[(g0 + g) * J + j0 + u], v[u]);
         }
 #pragma unroll
         for (int g = 0; g < SG; ++g)
@@ -821,27 +829,11 @@ __global__ void __launch_bounds__(NT) k_dcgs_update(Basis<T> V, int J, const dou
 }
 
 // Second stage of every reduction plus the scalar bookkeeping that consumes it.
-__global__ void __launch_bounds__(NT) k_reduce(Reduce rd, int nslot, int mode, int colidx, DevState S,
-                                               const double2* __restrict__ lambda) {
-    const int col = blockIdx.x;
-    // RM_BETA_FIRST starts a solve; RM_BETA_RESTART must still see columns that
-    // broke down in this cycle; every other mode is column work proper.
-    if (mode == RM_BETA_RESTART && S.done[col]) return;
-    if (mode != RM_BETA_FIRST && mode != RM_BETA_RESTART && S.skip[col]) return;
+// The scalar work of a reduction once the slot sums of column col are known
+// (sums: shared memory, nslot entries).  Called by every thread of one CTA.
+__device__ void reduce_tail(const double2* sums, int col, int nslot, int mode, int colidx, const DevState& S,
+                            const double2* __restrict__ lambda) {
     __shared__ double2 gsh[MAXSLOT];
-    __shared__ double2 sums[MAXSLOT];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int j = warp; j < nslot; j += NWARP) {
-        const double2* p = rd.partial + ((int64_t)col * rd.stride + j) * rd.nblk;
-        double2 a = make_double2(0, 0);
-        // unrolled so that the loads of up to 8 partials per lane are in flight together
-        // (the sum order, b = lane, lane + 32, ..., is fixed either way)
-#pragma unroll 8
-        for (int b = lane; b < rd.nblk; b += 32) a = cadd(a, p[b]);
-        a = warp_sum(a);
-        if (lane == 0) sums[j] = a;
-    }
-    __syncthreads();
     const int64_t cr = (int64_t)col * S.rstride;
     switch (mode) {
         case RM_STORE:
@@ -1017,6 +1009,63 @@ __global__ void __launch_bounds__(NT) k_reduce(Reduce rd, int nslot, int mode, i
     }
 }
 
+__global__ void __launch_bounds__(NT) k_reduce(Reduce rd, int nslot, int mode, int colidx, DevState S,
+                                               const double2* __restrict__ lambda) {
+    const int col = blockIdx.x;
+    // RM_BETA_FIRST starts a solve; RM_BETA_RESTART must still see columns that
+    // broke down in this cycle; every other mode is column work proper.
+    if (mode == RM_BETA_RESTART && S.done[col]) return;
+    if (mode != RM_BETA_FIRST && mode != RM_BETA_RESTART && S.skip[col]) return;
+    __shared__ double2 sums[MAXSLOT];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = warp; j < nslot; j += NWARP) {
+        const double2* p = rd.partial + ((int64_t)col * rd.stride + j) * rd.nblk;
+        double2 a = make_double2(0, 0);
+        // unrolled so that the loads of up to 8 partials per lane are in flight together
+        // (the sum order, b = lane, lane + 32, ..., is fixed either way)
+#pragma unroll 8
+        for (int b = lane; b < rd.nblk; b += 32) a = cadd(a, p[b]);
+        a = warp_sum(a);
+        if (lane == 0) sums[j] = a;
+    }
+    __syncthreads();
+    reduce_tail(sums, col, nslot, mode, colidx, S, lambda);
+}
+
+// Split form: CTA (col, g) sums slots g * NWARP .. g * NWARP + NWARP - 1 (one warp each,
+// the same fixed order as k_reduce) into S.sums; the last CTA of the column to
+// arrive loads all sums and does the scalar work.  Results are identical to
+// k_reduce's whatever the arrival order.
+__global__ void __launch_bounds__(NT) k_reduce_split(Reduce rd, int nslot, int mode, int colidx, DevState S,
+                                                     const double2* __restrict__ lambda) {
+    const int col = blockIdx.x;
+    if (mode == RM_BETA_RESTART && S.done[col]) return;
+    if (mode != RM_BETA_FIRST && mode != RM_BETA_RESTART && S.skip[col]) return;
+    __shared__ double2 sums[MAXSLOT];
+    __shared__ int last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t cr = (int64_t)col * S.rstride;
+    const int j = blockIdx.y * NWARP + warp;
+    if (j < nslot) {
+        const double2* p = rd.partial + ((int64_t)col * rd.stride + j) * rd.nblk;
+        double2 a = make_double2(0, 0);
+#pragma unroll 8
+        for (int b = lane; b < rd.nblk; b += 32) a = cadd(a, p[b]);
+        a = warp_sum(a);
+        if (lane == 0) S.sums[cr + j] = a;
+    }
+    __threadfence();  // this CTA's sums are visible device-wide before it is counted
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&S.rcount[col], 1) == (int)gridDim.y - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int i = threadIdx.x; i < nslot; i += NT) sums[i] = __ldcg(S.sums + cr + i);  // from L2, not a stale L1
+    if (threadIdx.x == 0) S.rcount[col] = 0;  // ready for the next launch
+    __syncthreads();
+    reduce_tail(sums, col, nslot, mode, colidx, S, lambda);
+}
+
 // out = a x + b y + c z on whole blocks (real coefficients; z may be null).
 template <class T>
 __global__ void __launch_bounds__(NT) k_axpby3(T* __restrict__ out, double a, const T* __restrict__ x, double b,
@@ -1120,6 +1169,23 @@ __global__ void k_f64_to_bf16(const double2* __restrict__ in, __nv_bfloat162* __
     }
 }
 
+// r_j += sigma_j d_j - w_j for nb systems: r_j at r + roff[j] (complex128), w_j = A^2 d_j
+// in FP32 and d_j in FP64, both at j * n.
+__global__ void k_correct_residuals(double2* __restrict__ r, const long long* __restrict__ roff,
+                                    const double* __restrict__ sig, const float2* __restrict__ w,
+                                    const double2* __restrict__ d, int64_t n) {
+    const int j = blockIdx.y;
+    double2* rj = r + roff[j];
+    const double s = sig[j];
+    const float2* wj = w + (int64_t)j * n;
+    const double2* dj = d + (int64_t)j * n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const double2 rv = rj[e], dv = dj[e];
+        const float2 wv = wj[e];
+        rj[e] = make_double2(rv.x - (double)wv.x + s * dv.x, rv.y - (double)wv.y + s * dv.y);
+    }
+}
+
 inline unsigned grid_for(int64_t count) {
     int64_t g = (count + 255) / 256;
     if (g > 152 * 16) g = 152 * 16;
@@ -1215,7 +1281,11 @@ cudaError_t mdot(Basis<T> V, int J, const T* w, int64_t wsr, int64_t n, int ncol
 cudaError_t reduce(const Reduce& rd, int nslot, int ncol, int mode, int colidx, const DevState& S,
                    const double2* lambda, cudaStream_t st) {
     if (nslot > MAXSLOT) return cudaErrorInvalidValue;
-    k_reduce<<<ncol, NT, 0, st>>>(rd, nslot, mode, colidx, S, lambda);
+    const int groups = (nslot + NWARP - 1) / NWARP;
+    if (S.sums && S.rcount && groups > 1)
+        k_reduce_split<<<dim3(ncol, groups), NT, 0, st>>>(rd, nslot, mode, colidx, S, lambda);
+    else
+        k_reduce<<<ncol, NT, 0, st>>>(rd, nslot, mode, colidx, S, lambda);
     count_launch();
     return cudaGetLastError();
 }
@@ -1302,6 +1372,16 @@ template cudaError_t dcgs_update<double2>(Basis<double2>, int, const double2*, i
                                           double2*, int64_t, int64_t, int, const int*, cudaStream_t);
 template cudaError_t dcgs_update<float2>(Basis<float2>, int, const double2*, int, float2*, const float2*, float2*,
                                          int64_t, int64_t, int, const int*, cudaStream_t);
+
+cudaError_t correct_residuals(double2* r, const long long* roff, const double* sig, const float2* w,
+                              const double2* d, int64_t n, int nb, cudaStream_t st) {
+    if (nb < 1) return cudaSuccess;
+    if (nb > 65535) return cudaErrorInvalidValue;
+    unsigned gx = (unsigned)std::min<int64_t>((n + NT - 1) / NT, 1024);
+    k_correct_residuals<<<dim3(gx, nb), NT, 0, st>>>(r, roff, sig, w, d, n);
+    count_launch();
+    return cudaGetLastError();
+}
 
 template <class T>
 cudaError_t axpby3(T* out, double a, const T* x, double b, const T* y, double c, const T* z, int64_t count,

@@ -26,6 +26,11 @@ struct DevState {
     int* done;         // [col] converged (column work is skipped)
     int* skip;         // [col] done or broken down in this cycle
     int* err;          // [1] device error word (bit 0: singular shifted system; bit 1: non-finite)
+    // Optional (both or neither): per-slot sums and per-column arrival counters for the
+    // split second-stage reduction (several CTAs per column, the last one does the
+    // column's scalar work).  Null: one CTA per column.
+    double2* sums = nullptr;  // [col][rstride]
+    int* rcount = nullptr;    // [col], zero between launches
     int kmax;
     int s;
     int rstride;
@@ -91,6 +96,22 @@ cudaError_t links_f64_to_bf16(const double2* in, __nv_bfloat162* out, int64_t co
 cudaError_t prepare_small_kernels();
 cudaError_t shifted_solves(const DevState& S, int ncol, cudaStream_t st);
 cudaError_t combine_shifts(const DevState& S, int ncol, cudaStream_t st);
+
+// Refinement residual update r_j += sigma_j d_j - w_j (w_j = A^2 d_j in FP32) for nb
+// systems: r_j at r + roff[j], w_j and d_j at j * n.
+cudaError_t correct_residuals(double2* r, const long long* roff, const double* sig, const float2* w,
+                              const double2* d, int64_t n, int nb, cudaStream_t st);
+
+// Tall-skinny products of a basis V (J <= 64 fields, stride sv) with N columns W
+// (complex128, stride sw): tsmm_tn writes the partials of V^dag W into rd (then
+// reduce(rd, J, N, RM_STORE, ...) gives red[col * rstride + j]); tsmm_nn does
+// W_col += alpha sum_j V_j C[col * cstride + j].  FP32 products, FP64 sums over CTAs.
+template <class TV>
+cudaError_t tsmm_tn(const TV* V, int64_t sv, int J, const double2* W, int64_t sw, int N, int64_t n,
+                    const Reduce& rd, cudaStream_t st);
+template <class TV>
+cudaError_t tsmm_nn(const TV* V, int64_t sv, int J, const double2* C, int cstride, double2* W, int64_t sw, int N,
+                    int64_t n, double alpha, cudaStream_t st);
 
 // Number of blocks per column used by the reductions for n complex elements.
 template <class T>

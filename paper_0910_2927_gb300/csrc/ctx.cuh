@@ -106,9 +106,10 @@ struct sgn_ctx {
     std::map<int, sgn::StencilShape> shapes;
     // kernel timing totals per class (stencil, Gram-Schmidt reduction, Gram-Schmidt update)
     int timing = 0;
-    double t_ms[3] = {0, 0, 0};
-    long long t_launches[3] = {0, 0, 0};
-    double t_bytes[3] = {0, 0, 0};
+    static constexpr int kTimedClasses = 5;
+    double t_ms[kTimedClasses] = {};
+    long long t_launches[kTimedClasses] = {};
+    double t_bytes[kTimedClasses] = {};
 };
 
 namespace sgn {
@@ -119,7 +120,8 @@ void fill_fp32_coefficients(StencilParams& p);
 cudaError_t apply_hw64(const sgn_ctx* c, double2* out, const double2* in, int ncol, bool adjoint, const int* skip,
                        cudaStream_t st);
 cudaError_t apply_hw32(const sgn_ctx* c, float2* out, const float2* in, int ncol, bool adjoint, const int* skip,
-                       cudaStream_t st);
+                       cudaStream_t st,
+                       bool fp32_links = false);
 
 int solve(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int ncol, bool adjoint, bool no_a,
           sgn_report* rep);

@@ -96,10 +96,13 @@ cudaError_t pack_links(const double2* natural, double2* packed, int64_t vol, cud
 // double, float or bf16 (Link).  skip: per-field flags (non-zero: skip), may be null.
 // Launch shape: sx sites (x fastest) by rb threads per CTA, each thread nr
 // fields of its site (nr <= 3 FP32, 1 FP64); {0, 0, 1} picks the default.
+// pipe = 1 selects the FP32 kernel that stages neighbour spinors through shared
+// memory with cp.async (a stage ahead of the computation; nr <= 2).
 struct StencilShape {
     int sx = 0;
     int rb = 0;
     int nr = 1;
+    int pipe = 0;
 };
 cudaError_t launch_hw_f64(double2* out, const double2* in, const double2* U, int nrhs,
                           const StencilParams& p, const int* skip, cudaStream_t st, StencilShape sh = {});

@@ -96,10 +96,11 @@ cudaError_t apply_hw64(const sgn_ctx* c, double2* out, const double2* in, int nc
 }
 
 cudaError_t apply_hw32(const sgn_ctx* c, float2* out, const float2* in, int ncol, bool adjoint, const int* skip,
-                       cudaStream_t st) {
+                       cudaStream_t st, bool fp32_links) {
     StencilParams p = stencil_params(c, adjoint);
-    const int prec = c->link_storage == SGN_LINKS_BF16 ? 2 : 1;
-    if (c->link_storage == SGN_LINKS_BF16)
+    const bool bf16 = c->link_storage == SGN_LINKS_BF16 && !fp32_links;
+    const int prec = bf16 ? 2 : 1;
+    if (bf16)
         return launch_hw_f32_bf16links(out, in, reinterpret_cast<const __nv_bfloat162*>(c->U16.p), ncol, p, skip, st,
                                        shape_for(c, prec, ncol));
     return launch_hw_f32(out, in, reinterpret_cast<const float2*>(c->U32.p), ncol, p, skip, st,
@@ -117,10 +118,10 @@ int tune_stencil(sgn_ctx* c, int prec, int ncol, void* in, void* out) {
         c->shapes[key] = StencilShape{};
         return SGN_OK;
     }
-    // SGN_STENCIL_SHAPE="sx,rb,nr" fixes the shape of every stencil launch (checked at launch)
+    // SGN_STENCIL_SHAPE="sx,rb,nr[,pipe]" fixes the shape of every stencil launch (checked at launch)
     if (const char* fix = getenv("SGN_STENCIL_SHAPE")) {
         StencilShape sh;
-        if (sscanf(fix, "%d,%d,%d", &sh.sx, &sh.rb, &sh.nr) == 3) {
+        if (sscanf(fix, "%d,%d,%d,%d", &sh.sx, &sh.rb, &sh.nr, &sh.pipe) >= 3) {
             c->shapes[key] = sh;
             return SGN_OK;
         }
@@ -128,16 +129,17 @@ int tune_stencil(sgn_ctx* c, int prec, int ncol, void* in, void* out) {
     cudaStream_t st = c->work;
     const StencilParams p = stencil_params(c, false);
     std::vector<StencilShape> cands;
-    for (int nr : {1, 2, 3}) {
-        if (nr > ncol || (prec == 0 && nr > 1)) continue;
-        const int groups = (ncol + nr - 1) / nr;
-        const int maxt = nr == 1 ? 384 : 256;
-        for (int rb : {1, 2, 3, 4, 6, 8, 12, 16}) {
-            if (rb > groups) continue;
-            for (int sx : {32, 64, 128, 256})
-                if (sx * rb <= maxt && sx * rb >= 64) cands.push_back({sx, rb, nr});
+    for (int pipe = 0; pipe <= (prec == 0 ? 0 : 1); ++pipe)
+        for (int nr : {1, 2, 3}) {
+            if (nr > ncol || (prec == 0 && nr > 1) || (pipe && nr > 2)) continue;
+            const int groups = (ncol + nr - 1) / nr;
+            const int maxt = nr == 1 && !pipe ? 384 : 256;
+            for (int rb : {1, 2, 3, 4, 6, 8, 12, 16}) {
+                if (rb > groups) continue;
+                for (int sx : {32, 64, 128, 256})
+                    if (sx * rb <= maxt && sx * rb >= 64) cands.push_back({sx, rb, nr, pipe});
+            }
         }
-    }
     if (cands.empty()) cands.push_back({});
     auto run = [&](StencilShape sh) -> cudaError_t {
         if (prec == 0)
@@ -173,8 +175,8 @@ int tune_stencil(sgn_ctx* c, int prec, int ncol, void* in, void* out) {
         return s && s[0] == '1';
     }();
     if (dbg)
-        fprintf(stderr, "[sgn tune] stencil prec %d ncol %d -> sx %d rb %d nr %d (%.3f ms / 3)\n", prec, ncol, pick.sx,
-                pick.rb, pick.nr, best);
+        fprintf(stderr, "[sgn tune] stencil prec %d ncol %d -> sx %d rb %d nr %d pipe %d (%.3f ms / 3)\n", prec, ncol,
+                pick.sx, pick.rb, pick.nr, pick.pipe, best);
     return SGN_OK;
 }
 
@@ -323,7 +325,9 @@ cudaError_t cycle_dcgs(const sgn_ctx* c, Engine& E, const CycleArgs& a, cudaStre
         CU(tm.begin(1, (j + 2) * fb));
         CU(dcgs_dots<T>(VB, j, V + j * sj, w, sr, n, ncol, rd, S.skip, st));
         CU(tm.end());
+        CU(tm.begin(3, (double)(2 * j + 3) * E.nblk * sizeof(double2) * ncol));
         CU(reduce(rd, 2 * j + 3, ncol, RM_DCGS, j, S, nullptr, st));
+        CU(tm.end());
         CU(tm.begin(2, (j + 4) * fb));
         CU(dcgs_update<T>(VB, j, S.red, S.rstride, V + j * sj, w, V + (j + 1) * sj, sr, n, ncol, S.skip, st));
         CU(tm.end());
@@ -332,14 +336,21 @@ cudaError_t cycle_dcgs(const sgn_ctx* c, Engine& E, const CycleArgs& a, cudaStre
     CU(tm.begin(1, (k + 1) * fb));
     CU(dcgs_dots<T>(VB, k, V + k * sj, nullptr, sr, n, ncol, rd, S.skip, st));
     CU(tm.end());
+    CU(tm.begin(3, (double)(k + 1) * E.nblk * sizeof(double2) * ncol));
     CU(reduce(rd, k + 1, ncol, RM_DCGS_FINAL, k, S, nullptr, st));
+    CU(tm.end());
     CU(tm.begin(2, (k + 2) * fb));
     CU(dcgs_update<T>(VB, k, S.red, S.rstride, V + k * sj, nullptr, nullptr, sr, n, ncol, S.skip, st));
     CU(tm.end());
     CU(shifted_solves(S, ncol, st));
     CU(combine_shifts(S, ncol, st));
     if (a.xacc) CU(update_x<T>(VB, k, S.coef, S.rstride, a.xacc, a.xsr, n, ncol, S.done, S.kk, st));
-    if (a.xs) CU(update_shifts<T>(VB, k, S.y, E.s, k, a.xs, a.xs_shift, a.xs_col, n, ncol, S.done, S.kk, st));
+    if (a.xs) {
+        // the basis once per group of 8 shifts, every per-shift iterate read and written (FP64)
+        CU(tm.begin(4, (double)((E.s + 7) / 8) * k * fb + 2.0 * E.s * ncol * n * sizeof(double2)));
+        CU(update_shifts<T>(VB, k, S.y, E.s, k, a.xs, a.xs_shift, a.xs_col, n, ncol, S.done, S.kk, st));
+        CU(tm.end());
+    }
     T* Vk = V + k * sj;
     if (a.project && a.m > 0) {
         const Basis<T> LB{reinterpret_cast<const T*>(a.L), n, 0};
@@ -446,6 +457,8 @@ int get_engine(sgn_ctx* c, int ncol, int k, int s, int prec, Engine** out) {
     size_t oi[3];
     for (int i = 0; i < 3; ++i) oi[i] = take(nc * sizeof(int));
     size_t oerr = take(sizeof(int));
+    size_t osums = take(nc * E->rstride * sizeof(double2));
+    size_t ocnt = take(nc * sizeof(int));
     SGN_CHECK(dev_alloc(c, E->arena, off));
     char* base = reinterpret_cast<char*>(E->arena.p);
     E->V = base + oV;
@@ -472,6 +485,8 @@ int get_engine(sgn_ctx* c, int ncol, int k, int s, int prec, Engine** out) {
     S.done = reinterpret_cast<int*>(base + oi[1]);
     S.skip = reinterpret_cast<int*>(base + oi[2]);
     S.err = reinterpret_cast<int*>(base + oerr);
+    S.sums = reinterpret_cast<double2*>(base + osums);
+    S.rcount = reinterpret_cast<int*>(base + ocnt);
     S.kmax = k;
     S.s = s;
     S.rstride = E->rstride;
@@ -689,6 +704,7 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
     size_t o_red = take(sizeof(double2) * ncmax * rs64);
     size_t o_part = take(sizeof(double2) * (size_t)ncmax * rs64 * nblk64);
     size_t o_flags = take(sizeof(int) * 2 * ncmax);
+    size_t o_roff = take(sizeof(long long) * B), o_rsig = take(sizeof(double) * B);
     SGN_CHECK(ensure_io(c, off));
     char* io = reinterpret_cast<char*>(c->io.p);
     double2* xs = reinterpret_cast<double2*>(io + o_xs);
@@ -700,6 +716,8 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
     double2* d = reinterpret_cast<double2*>(io + o_d);
     double2* rsd = reinterpret_cast<double2*>(io + o_rs);  // true residuals r_i, [i][col][n]
     double2* omtab = reinterpret_cast<double2*>(io + o_om);
+    long long* roff_dev = reinterpret_cast<long long*>(io + o_roff);
+    double* rsig_dev = reinterpret_cast<double*>(io + o_rsig);
     // FP64 reductions use their own partials and state (the FP32 engines size theirs for float packs)
     DevState S64{};
     S64.red = reinterpret_cast<double2*>(io + o_red);
@@ -792,15 +810,21 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
     std::vector<double> sig1(B), om1(B, 1.0);
     const int nall = s * ncol;  // every (shift, column) pair as one column of [i][col][n]
     std::vector<double2> hall((size_t)nall * rs64);
+    std::vector<long long> roff(B);
+    std::vector<double> rsig(B);
     for (int round = 0; round <= max_rounds; ++round) {
-        // true residuals r_i = b~ - (A^2 - sigma_i) x_i of every shifted system (FP64)
-        for (int i = 0; i < s; ++i) {
-            double2* xi = xs + (size_t)i * ncol * n;
-            SGN_CUDA(apply_hw64(c, t64, xi, ncol, adjoint, nullptr, st));
-            SGN_CUDA(apply_hw64(c, u64, t64, ncol, adjoint, nullptr, st));
-            SGN_CUDA(axpby3<double2>(rsd + (size_t)i * ncol * n, 1.0, bt, -1.0, u64, c->sigma[i], xi,
-                                     (int64_t)ncol * n, st));
-        }
+        // true residuals r_i = b~ - (A^2 - sigma_i) x_i of every shifted system: from
+        // scratch in FP64 in round 0; later rounds carry them along with the corrections
+        // (r_i -= R c_i with x_i += R (Lambda^2 - sigma_i)^{-1} c_i, r_i -= (A^2 - sigma_i) d_i
+        // with x_i += d_i), where FP32 products of the small d_i are exact to ~1e-7 ||r_i||
+        if (round == 0)
+            for (int i = 0; i < s; ++i) {
+                double2* xi = xs + (size_t)i * ncol * n;
+                SGN_CUDA(apply_hw64(c, t64, xi, ncol, adjoint, nullptr, st));
+                SGN_CUDA(apply_hw64(c, u64, t64, ncol, adjoint, nullptr, st));
+                SGN_CUDA(axpby3<double2>(rsd + (size_t)i * ncol * n, 1.0, bt, -1.0, u64, c->sigma[i], xi,
+                                         (int64_t)ncol * n, st));
+            }
         SGN_CUDA(mdot<double2>(Basis<double2>{rsd, 0, n}, 0, rsd, n, n, nall, rd64, 1, nullptr, st));
         SGN_CUDA(reduce(rd64, 1, nall, RM_STORE, 0, S64, nullptr, st));
         SGN_CUDA(cudaMemcpyAsync(hall.data(), S64.red, sizeof(double2) * hall.size(), cudaMemcpyDeviceToHost, st));
@@ -830,10 +854,11 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
         if (m > 0) {
             // the range(P) part of each residual is solved exactly in the eigenbasis,
             // (A^2 - sigma)^{-1} R = R (Lambda^2 - sigma)^{-1}:  x_i += R (Lambda^2 - sigma_i)^{-1} L^dag r_i,
-            // and the Krylov corrections work on (I - P) r_i.  One launch each for all pairs.
-            SGN_CUDA(mdot<double2>(LB, m, rsd, n, n, nall, rd64, 0, nullptr, st));
+            // and the Krylov corrections work on (I - P) r_i.  One launch each for all pairs,
+            // with the FP32 copies of L and R read once per tile of columns (tsmm.cu).
+            SGN_CUDA(tsmm_tn<float2>(Lb32, n, m, rsd, n, nall, n, rd64, st));
             SGN_CUDA(reduce(rd64, m, nall, RM_STORE, 0, S64, nullptr, st));
-            SGN_CUDA(maxpy_scale<double2>(RB, m, S64.red, rs64, rsd, n, rsd, n, nullptr, n, nall, nullptr, st));
+            SGN_CUDA(tsmm_nn<float2>(Rb32, n, m, S64.red, rs64, rsd, n, nall, n, -1.0, st));
             SGN_CUDA(cudaMemcpyAsync(hall.data(), S64.red, sizeof(double2) * hall.size(), cudaMemcpyDeviceToHost, st));
             SGN_CUDA(cudaStreamSynchronize(st));
             for (int i = 0; i < s; ++i)
@@ -845,7 +870,7 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
                         v = make_double2(q.real(), q.imag());
                     }
             SGN_CUDA(cudaMemcpyAsync(S64.red, hall.data(), sizeof(double2) * hall.size(), cudaMemcpyHostToDevice, st));
-            SGN_CUDA(update_x<double2>(RB, m, S64.red, rs64, xs, n, n, nall, nullptr, nullptr, st));
+            SGN_CUDA(tsmm_nn<float2>(Rb32, n, m, S64.red, rs64, xs, n, nall, n, 1.0, st));
             SGN_CUDA(cudaStreamSynchronize(st));
         }
         // correction solves, B systems at a time, one system per column
@@ -872,6 +897,23 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
                         t0, nb, inner, st1, r1.cycles, r1.resmax);
             if (st1 != SGN_OK) return st1;
             ref_cycles += r1.cycles;
+            // r_i -= (A^2 - sigma_i) d_i:  A^2 d in FP32 on the engine's scratch fields
+            {
+                float2* w32 = reinterpret_cast<float2*>(E1->w);
+                float2* t32 = reinterpret_cast<float2*>(E1->t);
+                SGN_CUDA(convert_f64_to_f32(d, w32, (int64_t)nb * n, st));
+                // FP32 links even when the solves run on BF16 ones: the carried residual
+                // must see the true operator, not the one the corrections were solved with
+                SGN_CUDA(apply_hw32(c, t32, w32, nb, adjoint, nullptr, st, true));
+                SGN_CUDA(apply_hw32(c, w32, t32, nb, adjoint, nullptr, st, true));
+                for (int j = 0; j < nb; ++j) {
+                    roff[j] = (long long)((size_t)todo[t0 + j].first * ncol + todo[t0 + j].second) * n;
+                    rsig[j] = c->sigma[todo[t0 + j].first];
+                }
+                SGN_CUDA(cudaMemcpyAsync(roff_dev, roff.data(), sizeof(long long) * nb, cudaMemcpyHostToDevice, st));
+                SGN_CUDA(cudaMemcpyAsync(rsig_dev, rsig.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, st));
+                SGN_CUDA(correct_residuals(rsd, roff_dev, rsig_dev, w32, d, n, nb, st));
+            }
             for (int j = 0; j < nb; ++j) {
                 const int i = todo[t0 + j].first, col = todo[t0 + j].second;
                 double2* xi = xs + ((size_t)i * ncol + col) * n;

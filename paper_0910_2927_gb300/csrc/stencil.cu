@@ -140,39 +140,35 @@ struct Link<float, __nv_bfloat162> {
 //   (1 + S gamma) psi = [h ; S B^dag h],  h = psi_up + S B psi_dn,
 //   gamma_NU = [[0, B], [B^dag, 0]]:  B = -i sigma_{x,y,z}, or 1 for t.
 // Each link entry is loaded once and applied to the NR fields.
-template <class R, class LinkT, int NU, int S, int NR>
-__device__ __forceinline__ void hop(Cx<R> (&acc)[NR][12], const typename Field<R>::T* __restrict__ in,
-                                    int64_t stride_rhs, const bool (&act)[NR], const LinkT* __restrict__ U,
-                                    int64_t link_site, int64_t nb, R coef, int64_t vol) {
+
+// Spin projection h = psi_up + S B psi_dn of one neighbour spinor.
+template <class R, int NU, int S>
+__device__ __forceinline__ void project(const Cx<R> (&p)[12], Cx<R> (&h0)[3], Cx<R> (&h1)[3]) {
     const R s = R(S);
-    Cx<R> h0[NR][3], h1[NR][3];
 #pragma unroll
-    for (int i = 0; i < NR; ++i) {
-        Cx<R> p[12];
-        if (act[i]) {
-            Field<R>::load(in + i * stride_rhs, nb, 2 * vol, p);
-        } else {
-#pragma unroll
-            for (int k = 0; k < 12; ++k) p[k] = {R(0), R(0)};
-        }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            Cx<R> p0 = p[c], p1 = p[3 + c], p2 = p[6 + c], p3 = p[9 + c];
-            if constexpr (NU == 0) {  // B psi_dn = (-i p3, -i p2)
-                h0[i][c] = p0 + scale(mul_mi(p3), s);
-                h1[i][c] = p1 + scale(mul_mi(p2), s);
-            } else if constexpr (NU == 1) {  // (-p3, p2)
-                h0[i][c] = p0 - scale(p3, s);
-                h1[i][c] = p1 + scale(p2, s);
-            } else if constexpr (NU == 2) {  // (-i p2, i p3)
-                h0[i][c] = p0 + scale(mul_mi(p2), s);
-                h1[i][c] = p1 + scale(mul_i(p3), s);
-            } else {  // (p2, p3)
-                h0[i][c] = p0 + scale(p2, s);
-                h1[i][c] = p1 + scale(p3, s);
-            }
+    for (int c = 0; c < 3; ++c) {
+        Cx<R> p0 = p[c], p1 = p[3 + c], p2 = p[6 + c], p3 = p[9 + c];
+        if constexpr (NU == 0) {  // B psi_dn = (-i p3, -i p2)
+            h0[c] = p0 + scale(mul_mi(p3), s);
+            h1[c] = p1 + scale(mul_mi(p2), s);
+        } else if constexpr (NU == 1) {  // (-p3, p2)
+            h0[c] = p0 - scale(p3, s);
+            h1[c] = p1 + scale(p2, s);
+        } else if constexpr (NU == 2) {  // (-i p2, i p3)
+            h0[c] = p0 + scale(mul_mi(p2), s);
+            h1[c] = p1 + scale(mul_i(p3), s);
+        } else {  // (p2, p3)
+            h0[c] = p0 + scale(p2, s);
+            h1[c] = p1 + scale(p3, s);
         }
     }
+}
+
+// The link multiplication and the reconstruction into acc for NR projected spinors.
+template <class R, class LinkT, int NU, int S, int NR>
+__device__ __forceinline__ void hop_links(Cx<R> (&acc)[NR][12], const Cx<R> (&h0)[NR][3], const Cx<R> (&h1)[NR][3],
+                                          const LinkT* __restrict__ U, int64_t link_site, R coef, int64_t vol) {
+    const R s = R(S);
     // packed links: entry (row, col) of U_NU(site) at ((NU * 9 + 3 row + col) * vol + site)
     const LinkT* lb = U + (int64_t)NU * 9 * vol + link_site;
     const R cs = coef * s;
@@ -221,6 +217,26 @@ __device__ __forceinline__ void hop(Cx<R> (&acc)[NR][12], const typename Field<R
             }
         }
     }
+}
+
+
+template <class R, class LinkT, int NU, int S, int NR>
+__device__ __forceinline__ void hop(Cx<R> (&acc)[NR][12], const typename Field<R>::T* __restrict__ in,
+                                    int64_t stride_rhs, const bool (&act)[NR], const LinkT* __restrict__ U,
+                                    int64_t link_site, int64_t nb, R coef, int64_t vol) {
+    Cx<R> h0[NR][3], h1[NR][3];
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+        Cx<R> p[12];
+        if (act[i]) {
+            Field<R>::load(in + i * stride_rhs, nb, 2 * vol, p);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) p[k] = {R(0), R(0)};
+        }
+        project<R, NU, S>(p, h0[i], h1[i]);
+    }
+    hop_links<R, LinkT, NU, S, NR>(acc, h0, h1, U, link_site, coef, vol);
 }
 
 template <class R>
@@ -326,6 +342,190 @@ __global__ void __launch_bounds__(NR == 1 ? 384 : 256)
     }
 }
 
+// ---- pipelined FP32 form ------------------------------------------------------
+// The same stencil with the neighbour spinors staged through shared memory:
+// each thread copies its own next stage (the site itself, then the 8 hops)
+// with cp.async while it computes the current one, so one stage of loads is
+// always in flight per thread without holding registers for it.  Shared
+// memory: 2 buffers x NR fields x 6 planes x 16 bytes per thread, thread-major
+// (consecutive threads, consecutive 16-byte words: no bank conflicts).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <int NR>
+struct PipeCtx {
+    float4* sbuf;
+    int nthr, tid;
+    const float2* in;
+    int64_t stride_rhs, vol2;
+    bool act[NR];
+    __device__ __forceinline__ float4* slot(int buf, int i, int k) const {
+        return sbuf + ((buf * NR + i) * 6 + k) * nthr + tid;
+    }
+    // stage `buf` <- the spinors of site nb of the NR fields
+    __device__ __forceinline__ void issue(int buf, int nb) const {
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            if (!act[i]) continue;
+            const float2* src = in + i * stride_rhs + 2 * (int64_t)nb;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) cp_async16(slot(buf, i, k), src + k * vol2);
+        }
+    }
+    __device__ __forceinline__ void read(int buf, int i, Cx<float> (&p)[12]) const {
+        if (act[i]) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const float4 v = *slot(buf, i, k);
+                p[2 * k] = {v.x, v.y};
+                p[2 * k + 1] = {v.z, v.w};
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) p[k] = {0.f, 0.f};
+        }
+    }
+};
+
+// Site and coefficient of stage ST (0: the site itself; 2 nu + 1, 2 nu + 2: the forward
+// and backward neighbour in direction nu), 32-bit site indices (vol < 2^27).
+template <int ST>
+__device__ __forceinline__ int stage_site(int site, const int (&co)[4], const StencilParams& P, float* coef) {
+    if constexpr (ST == 0) {
+        *coef = P.diag32;
+        return site;
+    } else {
+        constexpr int NU = (ST - 1) / 2;
+        int stride = 1;
+#pragma unroll
+        for (int d = 0; d < NU; ++d) stride *= P.L[d];
+        const int L = P.L[NU];
+        if constexpr (ST % 2) {  // forward
+            float c = P.cf32[NU];
+            int nb = site + stride;
+            if (co[NU] == L - 1) {
+                nb = site - (L - 1) * stride;
+                if (P.ap[NU]) c = -c;
+            }
+            *coef = c;
+            return nb;
+        } else {  // backward
+            float c = P.cb32[NU];
+            int nb = site - stride;
+            if (co[NU] == 0) {
+                nb = site + (L - 1) * stride;
+                if (P.ap[NU]) c = -c;
+            }
+            *coef = c;
+            return nb;
+        }
+    }
+}
+
+// Stage ST (1..8) = hop NU = (ST - 1) / 2, forward (S = -1) for odd ST; its data sit in
+// buffer ST % 2.  Before computing it, the next stage's copy is issued into the other
+// buffer, which the previous stage finished reading.
+template <class LinkT, int NR, int ST>
+__device__ __forceinline__ void pipe_stage(Cx<float> (&acc)[NR][12], const PipeCtx<NR>& pc,
+                                           const LinkT* __restrict__ U, int site, const int (&co)[4],
+                                           const StencilParams& P) {
+    constexpr int NU = (ST - 1) / 2;
+    constexpr int S = (ST % 2) ? -1 : +1;
+    if constexpr (ST < 8) {
+        float unused;
+        pc.issue((ST + 1) % 2, stage_site<ST + 1>(site, co, P, &unused));
+        cp_async_commit();
+        cp_async_wait<1>();
+    } else {
+        cp_async_wait<0>();
+    }
+    float coef;
+    const int nb = stage_site<ST>(site, co, P, &coef);
+    Cx<float> h0[NR][3], h1[NR][3];
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+        Cx<float> p[12];
+        pc.read(ST % 2, i, p);
+        project<float, NU, S>(p, h0[i], h1[i]);
+    }
+    // forward hops use U_nu(site), backward ones U_nu(site - nu)^dag
+    hop_links<float, LinkT, NU, S, NR>(acc, h0, h1, U, (ST % 2) ? site : nb, coef, P.vol);
+}
+
+template <class LinkT, int NR, bool CS>
+__global__ void __launch_bounds__(256)
+    k_hw_pipe(float2* __restrict__ out, const float2* __restrict__ in, const LinkT* __restrict__ U, int nrhs,
+              StencilParams P, const int* __restrict__ skip, int ngrp) {
+    extern __shared__ float4 sbuf[];
+    const int64_t tile = blockIdx.x / (unsigned)ngrp;
+    const int grp = (int)(blockIdx.x - tile * ngrp);
+    const int64_t site = tile * blockDim.x + threadIdx.x;
+    const int rhs0 = (grp * blockDim.y + threadIdx.y) * NR;
+    if (site >= P.vol || rhs0 >= nrhs) return;  // no barrier below: early exit is safe
+    PipeCtx<NR> pc;
+    pc.sbuf = sbuf;
+    pc.nthr = blockDim.x * blockDim.y;
+    pc.tid = threadIdx.y * blockDim.x + threadIdx.x;
+    pc.in = in + rhs0 * P.stride_rhs;
+    pc.stride_rhs = P.stride_rhs;
+    pc.vol2 = 2 * P.vol;
+    bool any = false;
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+        pc.act[i] = rhs0 + i < nrhs && !(skip && skip[rhs0 + i]);
+        any |= pc.act[i];
+    }
+    if (!any) return;
+    int co[4];
+    {
+        const uint32_t s0 = (uint32_t)site;
+        const uint32_t q0 = P.div[0].div(s0);
+        co[0] = (int)(s0 - q0 * (uint32_t)P.L[0]);
+        const uint32_t q1 = P.div[1].div(q0);
+        co[1] = (int)(q0 - q1 * (uint32_t)P.L[1]);
+        const uint32_t q2 = P.div[2].div(q1);
+        co[2] = (int)(q1 - q2 * (uint32_t)P.L[2]);
+        co[3] = (int)q2;
+    }
+    const int s32 = (int)site;
+    float c0;
+    pc.issue(0, stage_site<0>(s32, co, P, &c0));
+    cp_async_commit();
+    {
+        float unused;
+        pc.issue(1, stage_site<1>(s32, co, P, &unused));
+    }
+    cp_async_commit();
+    cp_async_wait<1>();
+    Cx<float> acc[NR][12];
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+        pc.read(0, i, acc[i]);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[i][k] = scale(acc[i][k], c0);
+    }
+    pipe_stage<LinkT, NR, 1>(acc, pc, U, s32, co, P);
+    pipe_stage<LinkT, NR, 2>(acc, pc, U, s32, co, P);
+    pipe_stage<LinkT, NR, 3>(acc, pc, U, s32, co, P);
+    pipe_stage<LinkT, NR, 4>(acc, pc, U, s32, co, P);
+    pipe_stage<LinkT, NR, 5>(acc, pc, U, s32, co, P);
+    pipe_stage<LinkT, NR, 6>(acc, pc, U, s32, co, P);
+    pipe_stage<LinkT, NR, 7>(acc, pc, U, s32, co, P);
+    pipe_stage<LinkT, NR, 8>(acc, pc, U, s32, co, P);
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+        if (!pc.act[i]) continue;
+#pragma unroll
+        for (int k = 6; k < 12; ++k) acc[i][k] = {-acc[i][k].x, -acc[i][k].y};
+        Field<float>::template store<CS>(out + (rhs0 + i) * P.stride_rhs, site, 2 * P.vol, acc[i]);
+    }
+}
+
 // ---- layout conversions (one thread per site of one field) --------------------
 template <class T>
 __global__ void k_pack(const T* __restrict__ in, T* __restrict__ out, int64_t vol) {
@@ -377,10 +577,51 @@ cudaError_t launch_nr(typename Field<R>::T* out, const typename Field<R>::T* in,
     return cudaGetLastError();
 }
 
+template <class LinkT, int NR>
+cudaError_t launch_pipe(float2* out, const float2* in, const LinkT* U, int nrhs, const StencilParams& p,
+                        const int* skip, cudaStream_t st, int sx, int rb) {
+    const int groups = (nrhs + NR - 1) / NR;
+    const int ngrp = (groups + rb - 1) / rb;
+    const int64_t tiles = (p.vol + sx - 1) / sx;
+    if (tiles * ngrp > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)2 * NR * 6 * sizeof(float4) * sx * rb;
+    const bool cs = (double)nrhs * (double)p.vol * 12.0 * sizeof(float2) > 256.0 * (1 << 20);
+    // opt in to more than 48 KB of dynamic shared memory, once per kernel and device
+    static bool opted[2][64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    const int maxs = 2 * 2 * 6 * (int)sizeof(float4) * 256;
+    if (!opted[cs][dev]) {
+        e = cs ? cudaFuncSetAttribute(k_hw_pipe<LinkT, NR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs)
+               : cudaFuncSetAttribute(k_hw_pipe<LinkT, NR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxs);
+        if (e != cudaSuccess) return e;
+        opted[cs][dev] = true;
+    }
+    dim3 block(sx, rb);
+    if (cs)
+        k_hw_pipe<LinkT, NR, true><<<(unsigned)(tiles * ngrp), block, smem, st>>>(out, in, U, nrhs, p, skip, ngrp);
+    else
+        k_hw_pipe<LinkT, NR, false><<<(unsigned)(tiles * ngrp), block, smem, st>>>(out, in, U, nrhs, p, skip, ngrp);
+    count_launch();
+    return cudaGetLastError();
+}
+
 template <class R, class LinkT>
 cudaError_t launch(typename Field<R>::T* out, const typename Field<R>::T* in, const LinkT* U, int nrhs,
                    const StencilParams& p, const int* skip, cudaStream_t st, StencilShape sh) {
     if (nrhs <= 0 || p.vol <= 0) return cudaSuccess;
+    if (sh.pipe) {  // the pipelined FP32 kernel: 1 or 2 fields per thread, up to 256 threads per CTA
+        if constexpr (sizeof(R) == 4) {
+            if (sh.sx % 32 != 0 || sh.rb < 1 || sh.sx * sh.rb > 256 || sh.nr < 1 || sh.nr > 2)
+                return cudaErrorInvalidValue;
+            if (sh.nr == 1) return launch_pipe<LinkT, 1>(out, in, U, nrhs, p, skip, st, sh.sx, sh.rb);
+            return launch_pipe<LinkT, 2>(out, in, U, nrhs, p, skip, st, sh.sx, sh.rb);
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
     if (sh.sx > 0 && sh.rb > 0) {  // a tuned shape: validate it against the kernel's launch bounds
         const int maxnr = sizeof(R) == 8 ? 1 : 3;  // more fields per thread spill registers
         if (sh.sx % 32 != 0 || sh.nr < 1 || sh.nr > maxnr || sh.sx * sh.rb > (sh.nr == 1 ? 384 : 256))

@@ -103,11 +103,13 @@ def test_packed_layout_roundtrip_and_stencil():
                 assert torch.equal(direct, via)
 
 
-@pytest.mark.parametrize("shape", ["32,4,3", "64,2,2", "32,2,3", "64,3,1", "128,1,2"])
+@pytest.mark.parametrize("shape", ["32,4,3", "64,2,2", "32,2,3", "64,3,1", "128,1,2",
+                                   "32,4,1,1", "64,2,2,1", "128,1,2,1", "256,1,1,1"])
 def test_fp32_stencil_launch_shapes(shape, monkeypatch):
-    """Every launch shape (sites per CTA, thread rows, fields per thread) gives
+    """Every launch shape (sites per CTA, thread rows, fields per thread, and the
+    kernel that stages neighbours through shared memory with cp.async) gives
     the oracle's result, including field counts that leave the last thread's
-    group of fields ragged (5 fields, 3 per thread)."""
+    group of fields ragged (5 fields, 2 or 3 per thread)."""
     import paper_0910_2927_gb300 as pkg
     monkeypatch.setenv("SGN_STENCIL_SHAPE", shape)
     dims, mu = (5, 2, 3, 7), 0.3
@@ -135,3 +137,20 @@ def test_invalid_launch_shape_is_an_error(monkeypatch):
         ctx.set_precision(pkg.PREC_MIXED, 1e-8, pkg.LINKS_FP32)
         with pytest.raises(pkg.SignError):
             ctx.hw(torch.from_numpy(b).cuda(), precision=pkg.PREC_MIXED)
+
+
+@pytest.mark.parametrize("shape", ["64,2,2,1", "32,4,1,1"])
+def test_pipelined_stencil_bf16_links_and_many_fields(shape, monkeypatch):
+    """The shared-memory staged kernel with BF16 links and 13 fields (several CTAs
+    per site tile) matches the oracle within the BF16 rounding of the links."""
+    import paper_0910_2927_gb300 as pkg
+    monkeypatch.setenv("SGN_STENCIL_SHAPE", shape)
+    dims, mu = (4, 3, 4, 5), 0.4
+    U = si.random_su3_links(dims, 0.7, 35)
+    b = si.gaussian_block(dims, 13, 36)
+    with _ctx(dims, U, mu) as ctx:
+        ctx.set_precision(pkg.PREC_MIXED, 1e-8, pkg.LINKS_BF16)
+        out = ctx.hw(torch.from_numpy(b).cuda(), precision=pkg.PREC_MIXED).cpu().numpy()
+    for r in (0, 6, 12):
+        ref = O.hw(dims, U, b[r], mu)
+        assert np.linalg.norm(out[r] - ref) / np.linalg.norm(ref) < 2e-2
