@@ -168,6 +168,16 @@ SGN_API int sgn_set_deflation(sgn_ctx* ctx, int m, const double* R, const double
  * Errors: SGN_ERR_DEFLATION (no convergence or ambiguous selection). */
 SGN_API int sgn_build_deflation(sgn_ctx* ctx, int m, int extra, double eig_tol, double* lambda_out);
 
+/* The next e eigenpairs beyond the deflated ones (right R, left L with
+ * L^dag R = I, also biorthogonal to the deflated pairs; lambda: e complex128),
+ * in the layout of sgn_set_deflation.  They are not deflated in the solve; the
+ * derivative sgn_grad_mu treats them exactly in its reduced resolvents, so that
+ * its iterative part works on the spectrum beyond them.  sgn_build_deflation
+ * keeps its `extra` pairs here.  e = 0 clears them.  Errors: SGN_ERR_ARG,
+ * SGN_ERR_NONFINITE. */
+SGN_API int sgn_set_deflation_extra(sgn_ctx* ctx, int e, const double* R, const double* L, const double* lambda,
+                                    int on_device);
+
 /* Copy the current deflation data out: R, L (n x m each) and lambda (m), all
  * complex128 host arrays sized by the caller (any may be NULL). */
 SGN_API int sgn_get_deflation(sgn_ctx* ctx, int* m, double* R, double* L, double* lambda);
@@ -245,14 +255,19 @@ SGN_API int sgn_inner_products_noalloc(const double* V, int J, const double* w, 
  * (only the time hops of D_W(mu) depend on mu, Sec. 1). */
 SGN_API int sgn_dhw_dmu_apply(sgn_ctx* ctx, const double* in, double* out, int nrhs);
 
-/* Derivative of the loss Re<g, x(mu)> with x = sum_i omega_i A (A^2 - sigma_i)^{-1} b
- * (no deflation, m = 0) with respect to mu, per column:
- *   dmu[c] = Re sum_i omega_i < z_i, A' b - A' A x_i - A A' x_i >,
- *   x_i = (A^2 - sigma_i)^{-1} A b,  z_i = (A^dag^2 - sigma_i)^{-1} g,  A' = dH_W/dmu,
- * from one forward and one adjoint multishift solve (per-shift iterates kept).
- * b, g: nrhs complex128 device fields; dmu: host array of nrhs doubles.
- * Errors: SGN_ERR_STATE if deflation data is set (the eigenvector-motion terms
- * of the deflated function are not part of this entry point). */
+/* Derivative with respect to mu of the loss Re<g, x(mu)>, x = F(A) b the deflated
+ * rational sign function this context applies (Sec. 4, eq. (6.2)),
+ * F(A) = R S L^dag + G(A)(I - P), G(A) = sum_i omega_i (A^2 - sigma_i)^{-1} A,
+ * A = H_W(mu), A' = dH_W/dmu, per column:
+ *   dmu[c] = Re [ sum_i omega_i < z_i, A' v - A' A x_i - A A' x_i >        (v = (I - P) b)
+ *               - sum_j (l_j^dag b) < S_j^dag (s_j g - G(A)^dag g), A' r_j >
+ *               - sum_j (s_j - g(lambda_j)) <g, r_j> l_j^dag A' S_j b ],
+ * x_i = (A^2 - sigma_i)^{-1} A v, z_i = (A^dag^2 - sigma_i)^{-1} g, s_j = sign(Re lambda_j),
+ * S_j = (A - lambda_j)^{-1}(I - r_j l_j^dag) (the eigenvector motion of the
+ * deflated pairs; the deflation data must be the eigenpairs at this mu).  The
+ * reduced resolvents come from multishift solves with the complex shifts
+ * lambda_j^2.  With m = 0 only the first sum remains.
+ * b, g: nrhs complex128 device fields; dmu: host array of nrhs doubles. */
 SGN_API int sgn_grad_mu(sgn_ctx* ctx, const double* b, const double* g, int nrhs, double* dmu);
 
 /* Kernel timing (observability).  With on = 1, later solves record CUDA events

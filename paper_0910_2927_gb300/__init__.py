@@ -134,13 +134,21 @@ class SignContext:
             raise ValueError(f"links must hold V*36 = {self.vol * 36} complex entries, got {size}")
         check(lib().sgn_load_gauge(self._h, C.c_void_p(ptr), on_dev))
 
-    def set_deflation(self, R, L, lam):
-        """R, L: (n, m) right / left eigenvectors with L^dag R = I; lam: (m,) eigenvalues."""
+    def set_deflation(self, R, L, lam, extra=None):
+        """R, L: (n, m) right / left eigenvectors with L^dag R = I; lam: (m,) eigenvalues.
+        extra = (Rx, Lx, lamx): the next eigenpairs (not deflated; used by the mu-derivative)."""
         torch = _torch()
         if R is None or (hasattr(R, "shape") and R.shape[1] == 0):
             check(lib().sgn_set_deflation(self._h, 0, None, None, None, 0))
             self.m = 0
             return
+        self._set_pairs(lib().sgn_set_deflation, R, L, lam)
+        self.m = R.shape[1]
+        if extra is not None:
+            self._set_pairs(lib().sgn_set_deflation_extra, *extra)
+
+    def _set_pairs(self, fn, R, L, lam):
+        torch = _torch()
         m = R.shape[1]
         if isinstance(R, torch.Tensor):
             Rt = R.transpose(0, 1).to(torch.complex128).contiguous()
@@ -158,10 +166,8 @@ class SignContext:
             ptrs = (Rt.ctypes.data, Lt.ctypes.data, lt.ctypes.data)
             on_dev = 0
             keep = (Rt, Lt, lt)
-        check(lib().sgn_set_deflation(self._h, int(m), C.c_void_p(ptrs[0]), C.c_void_p(ptrs[1]),
-                                      C.c_void_p(ptrs[2]), on_dev))
+        check(fn(self._h, int(m), C.c_void_p(ptrs[0]), C.c_void_p(ptrs[1]), C.c_void_p(ptrs[2]), on_dev))
         del keep
-        self.m = m
 
     def build_deflation(self, m, extra=4, eig_tol=1e-10):
         lam = np.empty(m + extra, dtype=np.complex128)

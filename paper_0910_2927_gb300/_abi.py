@@ -46,6 +46,7 @@ SIGNATURES = {
     "sgn_set_precision": (C.c_int, [P, C.c_int, C.c_double, C.c_int]),
     "sgn_set_refinement": (C.c_int, [P, C.c_int, C.c_int]),
     "sgn_set_deflation": (C.c_int, [P, C.c_int, P, P, P, C.c_int]),
+    "sgn_set_deflation_extra": (C.c_int, [P, C.c_int, P, P, P, C.c_int]),
     "sgn_build_deflation": (C.c_int, [P, C.c_int, C.c_int, C.c_double, P]),
     "sgn_get_deflation": (C.c_int, [P, C.POINTER(C.c_int), P, P, P]),
     "sgn_apply": (C.c_int, [P, P, P, C.c_int, C.c_int, C.POINTER(Report)]),

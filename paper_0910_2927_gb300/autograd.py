@@ -4,8 +4,10 @@ Backward:
   grad_b  = sign(H_W(mu))^dag grad_x, one adjoint solve (SGN_APPLY_ADJOINT: the
             same kernels at -mu with L and R exchanged);
   grad_mu = Re <grad_x, dx/dmu>, from sgn_grad_mu (per-shift forward iterates
-            and per-shift adjoint iterates, recomputed in the backward pass):
-            defined for the undeflated rational function (m = 0).
+            and per-shift adjoint iterates, recomputed in the backward pass; with
+            deflation also the motion of the deflated eigenpairs, through
+            complex-shift multishift solves for the reduced resolvents).  The
+            deflation data must be the eigenpairs at the forward's mu.
 """
 from __future__ import annotations
 

@@ -42,6 +42,8 @@ int leave(sgn_ctx* c) {
 int drop_deflation(sgn_ctx* c) {
     c->m = 0;
     c->lam.clear();
+    c->mx = 0;
+    c->lamx.clear();
     return SGN_OK;
 }
 
@@ -124,6 +126,8 @@ SGN_API int sgn_destroy(sgn_ctx* c) {
     dev_free(c, c->L32);
     dev_free(c, c->lam_dev);
     dev_free(c, c->lamc_dev);
+    dev_free(c, c->Rx64);
+    dev_free(c, c->Lx64);
     dev_free(c, c->io);
     dev_free(c, c->stage);
     dev_free(c, c->ip_scratch);
@@ -284,6 +288,38 @@ SGN_API int sgn_set_deflation(sgn_ctx* c, int m, const double* R, const double* 
     c->lam.resize(m);
     for (int j = 0; j < m; ++j) c->lam[j] = {lam[2 * j], lam[2 * j + 1]};
     c->m = m;
+    return SGN_OK;
+}
+
+SGN_API int sgn_set_deflation_extra(sgn_ctx* c, int e, const double* R, const double* L, const double* lambda,
+                                    int on_device) {
+    if (!c || e < 0 || e > 64) return fail(SGN_ERR_ARG, "sgn_set_deflation_extra: need 0 <= e <= 64");
+    if (e == 0) {
+        c->mx = 0;
+        c->lamx.clear();
+        return SGN_OK;
+    }
+    if (!R || !L || !lambda) return fail(SGN_ERR_ARG, "sgn_set_deflation_extra: NULL argument");
+    const size_t cnt = (size_t)c->n * e;
+    std::vector<double> lam(2 * (size_t)e);
+    if (on_device) {
+        SGN_CUDA(cudaMemcpy(lam.data(), lambda, sizeof(double) * 2 * e, cudaMemcpyDeviceToHost));
+    } else {
+        std::memcpy(lam.data(), lambda, sizeof(double) * 2 * e);
+        if (!finite_host(R, 2 * cnt) || !finite_host(L, 2 * cnt))
+            return fail(SGN_ERR_NONFINITE, "sgn_set_deflation_extra: non-finite vector entry");
+    }
+    if (!finite_host(lam.data(), 2 * (size_t)e)) return fail(SGN_ERR_NONFINITE, "sgn_set_deflation_extra: bad lambda");
+    SGN_CHECK(enter(c));
+    SGN_CHECK(dev_alloc(c, c->Rx64, cnt * sizeof(double2)));
+    SGN_CHECK(dev_alloc(c, c->Lx64, cnt * sizeof(double2)));
+    SGN_CHECK(fields_in(c, as<double2>(c->Rx64), R, e, on_device));
+    SGN_CHECK(fields_in(c, as<double2>(c->Lx64), L, e, on_device));
+    SGN_CUDA(cudaStreamSynchronize(c->work));
+    SGN_CHECK(leave(c));
+    c->lamx.resize(e);
+    for (int j = 0; j < e; ++j) c->lamx[j] = {lam[2 * j], lam[2 * j + 1]};
+    c->mx = e;
     return SGN_OK;
 }
 
@@ -482,7 +518,6 @@ SGN_API int sgn_dhw_dmu_apply(sgn_ctx* c, const double* in, double* out, int nrh
 SGN_API int sgn_grad_mu(sgn_ctx* c, const double* b, const double* g, int nrhs, double* dmu) {
     if (!c || !b || !g || !dmu || nrhs < 1) return fail(SGN_ERR_ARG, "sgn_grad_mu: bad argument");
     if (!c->have_gauge || c->sigma.empty()) return fail(SGN_ERR_STATE, "sgn_grad_mu: gauge field and rational function needed");
-    if (c->m > 0) return fail(SGN_ERR_STATE, "sgn_grad_mu: defined for the undeflated function (m = 0) only");
     SGN_CHECK(enter(c));
     const size_t nn = (size_t)c->n * nrhs;
     SGN_CHECK(dev_alloc(c, c->stage, 2 * nn * sizeof(double2)));

@@ -22,6 +22,8 @@ struct DevState {
     double* resest;    // [col] max_i |rho_i| ||r|| / ||b~||
     const double* sigma;  // [col][s] shifts (per column: the mixed refinement solves one shift per column)
     const double* omega;  // [col][s] weights
+    const double* sigma_im = nullptr;  // [col][s] imaginary parts of the shifts (null: real shifts)
+    double2* gres = nullptr;  // [col][kmax + 1] minimal-residual form: coefficients of the new residual in V_{k+1}
     int* kk;           // [col] Krylov dimension of the current cycle
     int* done;         // [col] converged (column work is skipped)
     int* skip;         // [col] done or broken down in this cycle
@@ -95,6 +97,9 @@ cudaError_t links_f64_to_bf16(const double2* in, __nv_bfloat162* out, int64_t co
 // per device (before any stream capture).
 cudaError_t prepare_small_kernels();
 cudaError_t shifted_solves(const DevState& S, int ncol, cudaStream_t st);
+// Minimal-residual (GMRES) form for one shift per column: y, rho = 1 and the new
+// residual's coefficients in S.gres (k_shifted_lsq).
+cudaError_t shifted_lsq(const DevState& S, int ncol, cudaStream_t st);
 cudaError_t combine_shifts(const DevState& S, int ncol, cudaStream_t st);
 
 // Refinement residual update r_j += sigma_j d_j - w_j (w_j = A^2 d_j in FP32) for nb

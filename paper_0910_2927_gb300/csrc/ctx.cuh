@@ -40,6 +40,7 @@ struct Engine {
     DevState S{};
     double* sigma_dev = nullptr;  // [ncol][s]
     double* omega_dev = nullptr;
+    double* sigma_im_dev = nullptr;  // [ncol][s] imaginary parts (zero unless complex shifts are set)
     // host mirrors of the per-column flags (pinned)
     int* h_done = nullptr;
     double* h_resest = nullptr;
@@ -92,6 +93,11 @@ struct sgn_ctx {
     int m = 0;
     sgn::DevBuf R64, L64, R32, L32, lam_dev, lamc_dev;
     std::vector<std::complex<double>> lam;
+    // the next mx eigenpairs beyond the deflated ones (biorthonormal to them): not
+    // deflated in the solve, but the derivative's reduced resolvents treat them exactly
+    int mx = 0;
+    sgn::DevBuf Rx64, Lx64;
+    std::vector<std::complex<double>> lamx;
 
     // engines keyed by configuration
     std::map<uint64_t, std::unique_ptr<sgn::Engine>> engines;
@@ -124,12 +130,16 @@ cudaError_t apply_hw32(const sgn_ctx* c, float2* out, const float2* in, int ncol
                        bool fp32_links = false);
 
 int solve(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int ncol, bool adjoint, bool no_a,
-          sgn_report* rep);
+          sgn_report* rep,
+          const std::vector<std::complex<double>>* cshift = nullptr);
 // Pick the fastest stencil launch shape for (precision, ncol) by timing candidates
 // on the given buffers (ncol fields each); cached in the context.  Not during capture.
 int tune_stencil(sgn_ctx* c, int prec, int ncol, void* in, void* out);
 // Dot products <a_c, b_c> of ncol pairs of FP64 fields (host result, FP64 reductions).
 int field_dots(sgn_ctx* c, const double2* a, const double2* b, int ncol, std::vector<std::complex<double>>& out);
+// (A^2 - shift_col)^{-1} (I - Rp Lp^dag) rhs_col, one complex shift per column, restarted GMRES (FP64)
+int solve_columns_gmres(sgn_ctx* c, const double2* rhs, int ncol, const std::vector<std::complex<double>>& shift,
+                        bool adjoint, double2* out, const double2* Rp, const double2* Lp, int mp);
 int build_deflation(sgn_ctx* c, int m, int extra, double eig_tol, double* lambda_out);
 // dH_W/dmu on ncol FP64 fields, and the mu-derivative of Re<g, x> (grad.cu).
 cudaError_t apply_dhw_dmu64(const sgn_ctx* c, double2* out, const double2* in, int ncol, cudaStream_t st);

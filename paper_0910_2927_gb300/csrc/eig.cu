@@ -547,7 +547,7 @@ int build_deflation(sgn_ctx* c, int m, int extra, double eig_tol, double* lambda
     const int q = std::min(100, want + std::max(12, want / 2));
     const int64_t n = c->n;
     DevBuf RL;
-    SGN_CHECK(dev_alloc(c, RL, sizeof(double2) * (size_t)n * (2 * want + m)));
+    SGN_CHECK(dev_alloc(c, RL, sizeof(double2) * (size_t)n * (3 * want)));
     double2* Rw = reinterpret_cast<double2*>(RL.p);
     double2* Lw = Rw + (size_t)want * n;
     double2* Lm = Lw + (size_t)want * n;
@@ -564,10 +564,11 @@ int build_deflation(sgn_ctx* c, int m, int extra, double eig_tol, double* lambda
         set_error("deflation set-up: |lambda_m| and |lambda_m+1| coincide; choose another m");
         return SGN_ERR_DEFLATION;
     }
-    // pair every right eigenvalue with the left one whose conjugate is closest
-    std::vector<int> pick(m, -1);
+    // pair every right eigenvalue with the left one whose conjugate is closest (all
+    // `want` pairs: the m deflated ones and the extra ones kept for the derivative)
+    std::vector<int> pick(want, -1);
     std::vector<char> used(want, 0);
-    for (int j = 0; j < m; ++j) {
+    for (int j = 0; j < want; ++j) {
         double best = INFINITY;
         for (int l = 0; l < want; ++l) {
             if (used[l]) continue;
@@ -584,33 +585,34 @@ int build_deflation(sgn_ctx* c, int m, int extra, double eig_tol, double* lambda
             return SGN_ERR_DEFLATION;
         }
     }
-    for (int j = 0; j < m; ++j)
+    for (int j = 0; j < want; ++j)
         SGN_CUDA(cudaMemcpyAsync(Lm + (size_t)j * n, Lw + (size_t)pick[j] * n, sizeof(double2) * n,
                                  cudaMemcpyDeviceToDevice, st));
-    // L <- L M^{-dag}, M = L^dag R  (then L^dag R = I)
+    // L <- L M^{-dag}, M = L^dag R  (then L^dag R = I over all want pairs)
+    const int w2 = want;
     {
         Work W;
-        rc = setup(W, c, m, sizeof(double2), reduce_blocks<double2>(n));
+        rc = setup(W, c, w2, sizeof(double2), reduce_blocks<double2>(n));
         std::vector<cd> M;
-        if (rc == SGN_OK) rc = gram<double2>(W, Lm, m, Rw, m, M);
-        std::vector<cd> Mh((size_t)m * m), X((size_t)m * m, 0.0);
+        if (rc == SGN_OK) rc = gram<double2>(W, Lm, w2, Rw, w2, M);
+        std::vector<cd> Mh((size_t)w2 * w2), X((size_t)w2 * w2, 0.0);
         if (rc == SGN_OK) {
-            for (int i = 0; i < m; ++i)
-                for (int j = 0; j < m; ++j) Mh[(size_t)i * m + j] = std::conj(M[(size_t)j * m + i]);
-            for (int i = 0; i < m; ++i) X[(size_t)i * m + i] = 1.0;
-            if (dense_solve(m, m, Mh, X)) {
+            for (int i = 0; i < w2; ++i)
+                for (int j = 0; j < w2; ++j) Mh[(size_t)i * w2 + j] = std::conj(M[(size_t)j * w2 + i]);
+            for (int i = 0; i < w2; ++i) X[(size_t)i * w2 + i] = 1.0;
+            if (dense_solve(w2, w2, Mh, X)) {
                 set_error("deflation set-up: L^dag R is singular");
                 rc = SGN_ERR_DEFLATION;
             }
         }
         // X = M^{-dag}; L_new = L X, written to the Lw slot
-        if (rc == SGN_OK) rc = combine<double2>(W, Lm, m, X, m, Lw);
+        if (rc == SGN_OK) rc = combine<double2>(W, Lm, w2, X, w2, Lw);
         std::vector<cd> chk;
-        if (rc == SGN_OK) rc = gram<double2>(W, Lw, m, Rw, m, chk);
+        if (rc == SGN_OK) rc = gram<double2>(W, Lw, w2, Rw, w2, chk);
         if (rc == SGN_OK) {
             double e = 0;
-            for (int i = 0; i < m; ++i)
-                for (int j = 0; j < m; ++j) e = std::max(e, std::abs(chk[(size_t)i * m + j] - (i == j ? 1.0 : 0.0)));
+            for (int i = 0; i < w2; ++i)
+                for (int j = 0; j < w2; ++j) e = std::max(e, std::abs(chk[(size_t)i * w2 + j] - (i == j ? 1.0 : 0.0)));
             if (!(e < 1e-8)) {
                 set_error("deflation set-up: biorthonormalisation failed (||L^dag R - I|| = " + std::to_string(e) +
                           ")");
@@ -642,10 +644,21 @@ int build_deflation(sgn_ctx* c, int m, int extra, double eig_tol, double* lambda
     }
     SGN_CUDA(cudaMemcpyAsync(c->lam_dev.p, hl.data(), sizeof(double2) * m, cudaMemcpyHostToDevice, st));
     SGN_CUDA(cudaMemcpyAsync(c->lamc_dev.p, hlc.data(), sizeof(double2) * m, cudaMemcpyHostToDevice, st));
+    // the extra pairs, for the derivative's reduced resolvents
+    const int mx = want - m;
+    if (mx > 0) {
+        const size_t cx = (size_t)n * mx;
+        SGN_CHECK(dev_alloc(c, c->Rx64, cx * sizeof(double2)));
+        SGN_CHECK(dev_alloc(c, c->Lx64, cx * sizeof(double2)));
+        SGN_CUDA(cudaMemcpyAsync(c->Rx64.p, Rw + (size_t)m * n, cx * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+        SGN_CUDA(cudaMemcpyAsync(c->Lx64.p, Lw + (size_t)m * n, cx * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    }
     SGN_CUDA(cudaStreamSynchronize(st));
     dev_free(c, RL);
     c->lam.assign(lamR.begin(), lamR.begin() + m);
     c->m = m;
+    c->mx = mx;
+    c->lamx.assign(lamR.begin() + m, lamR.begin() + want);
     if (lambda_out)
         for (int j = 0; j < want; ++j) {
             lambda_out[2 * j] = lamR[j].real();

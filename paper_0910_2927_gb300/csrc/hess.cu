@@ -30,12 +30,16 @@ __global__ void __launch_bounds__(32) k_shifted_solve(DevState S) {
     const int kk = S.kk[col];
     const double2* H = S.H + (int64_t)col * (km + 1) * km;
     const double sigma = S.sigma[(int64_t)col * S.s + i];
+    const double sigma_im = S.sigma_im ? S.sigma_im[(int64_t)col * S.s + i] : 0.0;
     extern __shared__ double2 U[];  // [kk][km] upper factor, row-major
     __shared__ double2 zU[KMAX];
     const int c0 = lane, c1 = lane + 32;
     auto Hm = [&](int r, int c) -> double2 {  // (H - sigma I)[r][c]
         double2 h = H[(int64_t)r * km + c];
-        if (r == c) h.x -= sigma;
+        if (r == c) {
+            h.x -= sigma;
+            h.y -= sigma_im;
+        }
         return h;
     };
     double2 w0 = c0 < kk ? Hm(0, c0) : make_double2(0, 0);
@@ -129,11 +133,92 @@ __global__ void k_combine(DevState S) {
     }
 }
 
+// Minimal-residual form for one shift per column (restarted GMRES):  y = argmin
+// || beta rho e_1 - (Hbar_k - sigma I~) y ||  by Givens rotations, with the
+// coefficients of the new residual, c = beta rho e_1 - (Hbar_k - sigma I~) y, in
+// gres[col][0..kk] (the next restart vector is V_{k+1} c) and rho = 1.  One CTA per
+// column; the rotations run on one thread over a shared-memory copy (k <= 64:
+// O(k^2) work, once per cycle).
+__global__ void k_shifted_lsq(DevState S) {
+    const int col = blockIdx.x;
+    if (S.done[col] || threadIdx.x != 0) return;
+    const int km = S.kmax;
+    const int kk = S.kk[col];
+    const double2* H = S.H + (int64_t)col * (km + 1) * km;
+    const double sig = S.sigma[(int64_t)col * S.s];
+    const double sig_im = S.sigma_im ? S.sigma_im[(int64_t)col * S.s] : 0.0;
+    extern __shared__ double2 M[];  // [(kk + 1)][km]
+    __shared__ double2 g[KMAX + 1];
+    for (int r = 0; r <= kk; ++r)
+        for (int c = 0; c < kk; ++c) {
+            double2 h = H[(int64_t)r * km + c];
+            if (r == c) {
+                h.x -= sig;
+                h.y -= sig_im;
+            }
+            M[r * km + c] = h;
+        }
+    const double beta = S.beta[col];
+    const double2 rho = S.rho[(int64_t)col * S.s];
+    const double2 b0 = make_double2(beta * rho.x, beta * rho.y);
+    for (int r = 0; r <= kk; ++r) g[r] = r == 0 ? b0 : make_double2(0, 0);
+    // rows c and c+1: G = [[conj(cs), conj(sn)], [-sn, cs]] zeroes M[c+1][c]
+    for (int c = 0; c < kk; ++c) {
+        const double2 a = M[c * km + c], b = M[(c + 1) * km + c];
+        const double nr = sqrt(cabs2(a) + cabs2(b));
+        if (!(nr > 0)) continue;  // zero column (only at a breakdown): y_c = 0 below
+        const double2 cs = make_double2(a.x / nr, a.y / nr), sn = make_double2(b.x / nr, b.y / nr);
+        for (int j = c; j < kk; ++j) {
+            const double2 x = M[c * km + j], y = M[(c + 1) * km + j];
+            M[c * km + j] = cadd(cconjmul(cs, x), cconjmul(sn, y));
+            M[(c + 1) * km + j] = csub(cmul(cs, y), cmul(sn, x));
+        }
+        const double2 x = g[c], y = g[c + 1];
+        g[c] = cadd(cconjmul(cs, x), cconjmul(sn, y));
+        g[c + 1] = csub(cmul(cs, y), cmul(sn, x));
+    }
+    double2* yv = S.y + (int64_t)col * S.s * km;
+    for (int r = kk - 1; r >= 0; --r) {
+        double2 z = g[r];
+        for (int j = r + 1; j < kk; ++j) z = csub(z, cmul(M[r * km + j], yv[j]));
+        const double2 d = M[r * km + r];
+        const double dd = cabs2(d);
+        yv[r] = dd > 0 ? make_double2((z.x * d.x + z.y * d.y) / dd, (z.y * d.x - z.x * d.y) / dd) : make_double2(0, 0);
+    }
+    for (int j = kk; j < km; ++j) yv[j] = make_double2(0, 0);
+    // c = beta rho e_1 - (Hbar - sigma I~) y, from the unrotated matrix
+    double2* cres = S.gres + (int64_t)col * (km + 1);
+    for (int r = 0; r <= km; ++r) {
+        double2 acc = r == 0 ? b0 : make_double2(0, 0);
+        if (r <= kk)
+            for (int c = (r > 0 ? r - 1 : 0); c < kk; ++c) {
+                double2 h = H[(int64_t)r * km + c];
+                if (r == c) {
+                    h.x -= sig;
+                    h.y -= sig_im;
+                }
+                acc = csub(acc, cmul(h, yv[c]));
+            }
+        cres[r] = acc;
+    }
+    S.rho[(int64_t)col * S.s] = make_double2(1, 0);
+}
+
 }  // namespace
 
+cudaError_t shifted_lsq(const DevState& S, int ncol, cudaStream_t st) {
+    if (S.s != 1 || !S.gres || S.kmax > KMAX) return cudaErrorInvalidValue;
+    k_shifted_lsq<<<ncol, 32, sizeof(double2) * (S.kmax + 1) * S.kmax, st>>>(S);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t prepare_small_kernels() {
-    return cudaFuncSetAttribute(k_shifted_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(sizeof(double2) * KMAX * KMAX));
+    cudaError_t e = cudaFuncSetAttribute(k_shifted_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(double2) * KMAX * KMAX));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_shifted_lsq, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(double2) * (KMAX + 1) * KMAX));
 }
 
 cudaError_t shifted_solves(const DevState& S, int ncol, cudaStream_t st) {

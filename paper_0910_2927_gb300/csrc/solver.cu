@@ -220,6 +220,7 @@ struct CycleArgs {
     int64_t xsr = 0;
     double2* xs = nullptr;    // FP64 per-shift iterates, may be null
     int64_t xs_shift = 0, xs_col = 0;
+    bool gmres = false;       // minimal-residual restarts (one shift per column, FP64 engines)
 };
 
 uint64_t cycle_key(const sgn_ctx* c, const Engine& E, const CycleArgs& a) {
@@ -239,6 +240,7 @@ uint64_t cycle_key(const sgn_ctx* c, const Engine& E, const CycleArgs& a) {
     h = mix(h, (uint64_t)(uintptr_t)a.xs);
     h = mix(h, a.xs_shift);
     h = mix(h, a.xs_col);
+    h = mix(h, a.gmres);
     h = mix(h, (uint64_t)(uintptr_t)c->U64.p);
     h = mix(h, (uint64_t)(uintptr_t)c->U32.p);
     h = mix(h, (uint64_t)(uintptr_t)c->U16.p);
@@ -342,7 +344,11 @@ cudaError_t cycle_dcgs(const sgn_ctx* c, Engine& E, const CycleArgs& a, cudaStre
     CU(tm.begin(2, (k + 2) * fb));
     CU(dcgs_update<T>(VB, k, S.red, S.rstride, V + k * sj, nullptr, nullptr, sr, n, ncol, S.skip, st));
     CU(tm.end());
-    CU(shifted_solves(S, ncol, st));
+    if (a.gmres) {
+        CU(shifted_lsq(S, ncol, st));
+    } else {
+        CU(shifted_solves(S, ncol, st));
+    }
     CU(combine_shifts(S, ncol, st));
     if (a.xacc) CU(update_x<T>(VB, k, S.coef, S.rstride, a.xacc, a.xsr, n, ncol, S.done, S.kk, st));
     if (a.xs) {
@@ -352,6 +358,14 @@ cudaError_t cycle_dcgs(const sgn_ctx* c, Engine& E, const CycleArgs& a, cudaStre
         CU(tm.end());
     }
     T* Vk = V + k * sj;
+    if constexpr (sizeof(T) == sizeof(double2)) {
+        if (a.gmres) {  // the minimal residual r = V_{k+1} c becomes the restart vector
+            T* tt = reinterpret_cast<T*>(E.t);
+            CU(cudaMemsetAsync(tt, 0, sizeof(T) * (size_t)ncol * n, st));
+            CU(update_x<T>(VB, k + 1, S.gres, k + 1, reinterpret_cast<double2*>(tt), n, n, ncol, S.done, nullptr, st));
+            CU(cudaMemcpyAsync(Vk, tt, sizeof(T) * (size_t)ncol * n, cudaMemcpyDeviceToDevice, st));
+        }
+    }
     if (a.project && a.m > 0) {
         const Basis<T> LB{reinterpret_cast<const T*>(a.L), n, 0};
         const Basis<T> RB{reinterpret_cast<const T*>(a.R), n, 0};
@@ -454,11 +468,13 @@ int get_engine(sgn_ctx* c, int ncol, int k, int s, int prec, Engine** out) {
     for (int i = 0; i < 5; ++i) od[i] = take(nc * sizeof(double));
     size_t osig = take(nc * (size_t)s * sizeof(double));
     size_t oom = take(nc * (size_t)s * sizeof(double));
+    size_t osim = take(nc * (size_t)s * sizeof(double));
     size_t oi[3];
     for (int i = 0; i < 3; ++i) oi[i] = take(nc * sizeof(int));
     size_t oerr = take(sizeof(int));
     size_t osums = take(nc * E->rstride * sizeof(double2));
     size_t ocnt = take(nc * sizeof(int));
+    size_t ogres = take(nc * (size_t)(k + 1) * sizeof(double2));
     SGN_CHECK(dev_alloc(c, E->arena, off));
     char* base = reinterpret_cast<char*>(E->arena.p);
     E->V = base + oV;
@@ -479,14 +495,17 @@ int get_engine(sgn_ctx* c, int ncol, int k, int s, int prec, Engine** out) {
     S.resest = reinterpret_cast<double*>(base + od[4]);
     E->sigma_dev = reinterpret_cast<double*>(base + osig);
     E->omega_dev = reinterpret_cast<double*>(base + oom);
+    E->sigma_im_dev = reinterpret_cast<double*>(base + osim);
     S.sigma = E->sigma_dev;
     S.omega = E->omega_dev;
+    S.sigma_im = E->sigma_im_dev;
     S.kk = reinterpret_cast<int*>(base + oi[0]);
     S.done = reinterpret_cast<int*>(base + oi[1]);
     S.skip = reinterpret_cast<int*>(base + oi[2]);
     S.err = reinterpret_cast<int*>(base + oerr);
     S.sums = reinterpret_cast<double2*>(base + osums);
     S.rcount = reinterpret_cast<int*>(base + ocnt);
+    S.gres = reinterpret_cast<double2*>(base + ogres);
     S.kmax = k;
     S.s = s;
     S.rstride = E->rstride;
@@ -643,9 +662,15 @@ int ensure_io(sgn_ctx* c, size_t bytes) {
     return dev_alloc(c, c->io, bytes);
 }
 
-int fill_shift_tables(sgn_ctx* c, Engine& E, const double* sig_cols, const double* om_cols) {
-    SGN_CUDA(cudaMemcpyAsync(E.sigma_dev, sig_cols, sizeof(double) * E.ncol * E.s, cudaMemcpyHostToDevice, c->work));
-    SGN_CUDA(cudaMemcpyAsync(E.omega_dev, om_cols, sizeof(double) * E.ncol * E.s, cudaMemcpyHostToDevice, c->work));
+int fill_shift_tables(sgn_ctx* c, Engine& E, const double* sig_cols, const double* om_cols,
+                      const double* sig_im_cols = nullptr) {
+    const size_t bytes = sizeof(double) * E.ncol * E.s;
+    SGN_CUDA(cudaMemcpyAsync(E.sigma_dev, sig_cols, bytes, cudaMemcpyHostToDevice, c->work));
+    SGN_CUDA(cudaMemcpyAsync(E.omega_dev, om_cols, bytes, cudaMemcpyHostToDevice, c->work));
+    if (sig_im_cols)
+        SGN_CUDA(cudaMemcpyAsync(E.sigma_im_dev, sig_im_cols, bytes, cudaMemcpyHostToDevice, c->work));
+    else
+        SGN_CUDA(cudaMemsetAsync(E.sigma_im_dev, 0, bytes, c->work));
     return SGN_OK;
 }
 
@@ -948,15 +973,20 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
 
 // x = x_P + sum_i omega_i x_i on ncol device fields (FP64).  See sgn_apply.
 int solve(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int ncol, bool adjoint, bool no_a,
-          sgn_report* rep) {
+          sgn_report* rep, const std::vector<std::complex<double>>* cshift) {
     cudaStream_t st = c->work;
     const int64_t n = c->n;
-    const int s = (int)c->sigma.size();
+    // cshift: complex shifts with unit weights instead of the rational function's (FP64 form)
+    const int s = cshift ? (int)cshift->size() : (int)c->sigma.size();
     const int k = c->k;
     const int m = c->m;
-    if (c->precision == SGN_PREC_MIXED) return solve_mixed(c, b, x, x_shift, ncol, adjoint, no_a, rep);
+    if (c->precision == SGN_PREC_MIXED && !cshift) return solve_mixed(c, b, x, x_shift, ncol, adjoint, no_a, rep);
+    if (s < 1) {
+        set_error("solve: no shifts");
+        return SGN_ERR_ARG;
+    }
     Engine* E = nullptr;
-    SGN_CHECK(get_engine(c, ncol, k, s, c->precision, &E));
+    SGN_CHECK(get_engine(c, ncol, k, s, SGN_PREC_FP64, &E));
     // io: xacc (ncol n) | r0 (ncol n) | xs (s ncol n, optional)
     const size_t field = (size_t)n * sizeof(double2);
     const size_t f_cols = align256(field * ncol);
@@ -967,13 +997,14 @@ int solve(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int ncol, 
     double2* r0 = reinterpret_cast<double2*>(io + f_cols);
     double2* xs = x_shift ? reinterpret_cast<double2*>(io + 2 * f_cols) : nullptr;
 
-    std::vector<double> sig_cols((size_t)ncol * s), om_cols((size_t)ncol * s);
+    std::vector<double> sig_cols((size_t)ncol * s), om_cols((size_t)ncol * s), sim_cols((size_t)ncol * s, 0.0);
     for (int col = 0; col < ncol; ++col)
         for (int i = 0; i < s; ++i) {
-            sig_cols[(size_t)col * s + i] = c->sigma[i];
-            om_cols[(size_t)col * s + i] = c->omega[i];
+            sig_cols[(size_t)col * s + i] = cshift ? (*cshift)[i].real() : c->sigma[i];
+            sim_cols[(size_t)col * s + i] = cshift ? (*cshift)[i].imag() : 0.0;
+            om_cols[(size_t)col * s + i] = cshift ? 1.0 : c->omega[i];
         }
-    SGN_CHECK(fill_shift_tables(c, *E, sig_cols.data(), om_cols.data()));
+    SGN_CHECK(fill_shift_tables(c, *E, sig_cols.data(), om_cols.data(), sim_cols.data()));
 
     const double2* Lb = reinterpret_cast<const double2*>(adjoint ? c->R64.p : c->L64.p);
     const double2* Rb = reinterpret_cast<const double2*>(adjoint ? c->L64.p : c->R64.p);
@@ -1033,6 +1064,79 @@ int solve(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int ncol, 
         int bd = 0;
         for (int i = 0; i < ncol; ++i) bd |= E->h_kk[i] < k;
         rep->breakdown = bd;
+    }
+    return status;
+}
+
+// (A^2 - shift_col)^{-1} (I - P) rhs_col for ncol columns, one complex shift each (A^dag
+// with adjoint), by restarted GMRES in the FP64 engine: minimal-residual restarts, the
+// deflation projection after every cycle, no A applied to the right-hand side.  Shifts
+// inside the field of values of A^2 (where FOM's H_k - shift can be singular) are fine.
+int solve_columns_gmres(sgn_ctx* c, const double2* rhs, int ncol, const std::vector<std::complex<double>>& shift,
+                        bool adjoint, double2* out, const double2* Rp, const double2* Lp, int mp) {
+    cudaStream_t st = c->work;
+    const int64_t n = c->n;
+    const int k = c->k;
+    const int m = mp;  // projected pairs: Rp, Lp (n x mp, biorthonormal), null for none
+    if ((int)shift.size() != ncol || ncol < 1 || (m > 0 && (!Rp || !Lp))) {
+        set_error("solve_columns_gmres: one shift per column");
+        return SGN_ERR_ARG;
+    }
+    // batches bounded by the engine's memory (k + 4 fields per column)
+    const size_t per_col = (size_t)(k + 4) * n * sizeof(double2);
+    const int bmax = (int)std::max<size_t>(1, std::min<size_t>(ncol, kRefineBudgetBytes / 2 / per_col));
+    if (ncol > bmax) {
+        for (int c0 = 0; c0 < ncol; c0 += bmax) {
+            const int nb = std::min(bmax, ncol - c0);
+            std::vector<std::complex<double>> sub(shift.begin() + c0, shift.begin() + c0 + nb);
+            SGN_CHECK(solve_columns_gmres(c, rhs + (size_t)c0 * n, nb, sub, adjoint, out + (size_t)c0 * n, Rp, Lp, mp));
+        }
+        return SGN_OK;
+    }
+    // the engine key includes c->m; the projection count here is mp
+    const int m_saved = c->m;
+    c->m = mp;
+    Engine* E = nullptr;
+    const int ge = get_engine(c, ncol, k, 1, SGN_PREC_FP64, &E);
+    c->m = m_saved;
+    SGN_CHECK(ge);
+    const size_t field = (size_t)n * sizeof(double2);
+    std::vector<double> sig(ncol), sim(ncol), om(ncol, 1.0);
+    for (int col = 0; col < ncol; ++col) {
+        sig[col] = shift[col].real();
+        sim[col] = shift[col].imag();
+    }
+    SGN_CHECK(fill_shift_tables(c, *E, sig.data(), om.data(), sim.data()));
+    const double2* Lb = adjoint ? Rp : Lp;
+    const double2* Rb = adjoint ? Lp : Rp;
+    SGN_CUDA(cudaMemsetAsync(E->S.done, 0, ncol * sizeof(int), st));
+    SGN_CUDA(cudaMemsetAsync(E->S.skip, 0, ncol * sizeof(int), st));
+    SGN_CUDA(cudaMemsetAsync(out, 0, field * ncol, st));
+    double2* V0 = reinterpret_cast<double2*>(E->V);
+    SGN_CUDA(cudaMemcpyAsync(V0, rhs, field * ncol, cudaMemcpyDeviceToDevice, st));
+    if (m > 0) {  // r = (I - P) rhs
+        const Reduce rd{E->partial, E->nblk, E->rstride};
+        const Basis<double2> LB{Lb, n, 0}, RB{Rb, n, 0};
+        SGN_CUDA(mdot<double2>(LB, m, V0, n, n, ncol, rd, 0, nullptr, st));
+        SGN_CUDA(reduce(rd, m, ncol, RM_STORE, 0, E->S, nullptr, st));
+        SGN_CUDA(maxpy_scale<double2>(RB, m, E->S.red, E->rstride, V0, n, V0, n, nullptr, n, ncol, nullptr, st));
+    }
+    SGN_CHECK(tune_stencil(c, 0, ncol, E->V, E->t));
+    CycleArgs a;
+    a.adjoint = adjoint;
+    a.L = Lb;
+    a.R = Rb;
+    a.m = m;
+    a.project = 1;
+    a.xs = out;
+    a.xs_shift = (int64_t)ncol * n;
+    a.xs_col = n;
+    a.gmres = true;
+    RunResult rr;
+    int status = run_engine<double2>(c, *E, a, c->tol, c->max_cycles, &rr);
+    if (status == SGN_OK && !rr.converged) {
+        status = SGN_ERR_NOT_CONVERGED;
+        set_error("solve_columns_gmres: max_cycles reached before every system met the tolerance");
     }
     return status;
 }

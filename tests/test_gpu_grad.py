@@ -97,3 +97,55 @@ def test_config4_finite_differences():
     dir_ad = np.real(np.vdot(bt.grad.cpu().numpy(), d))
     assert abs(float(mut.grad) - fd) < 1e-5 * max(1.0, abs(fd))
     assert abs(dir_ad - dir_fd) < 1e-5 * max(1.0, abs(dir_fd))
+
+
+@pytest.mark.parametrize("mu,m", [(0.5, 6), (0.3, 10)])
+def test_deflated_gradient_matches_dense_daleckii_krein(mu, m):
+    """With m deflated pairs (and 4 extra ones set for the derivative) the forward applies
+    F = X f~(Lambda) X^{-1}, f~ = sign(Re lambda)
+    on the deflated eigenvalues and g elsewhere (g(t) = t sum omega / (t^2 - sigma)).  Its
+    derivative along A' is X (F^ o (X^{-1} A' X)) X^{-1} with the divided differences of f~:
+    the motion of the deflated eigenvectors is in the off-diagonal terms between deflated and
+    undeflated eigenvalues.  The GPU gradient (forward and adjoint solves, complex-shift
+    solves for the reduced resolvents) must match it."""
+    from paper_0910_2927_gb300.autograd import SignApply
+    dims = (3, 2, 3, 4)
+    U = si.random_su3_links(dims, 0.7, 57)
+    b = si.gaussian_field(dims, 58)
+    c = si.gaussian_field(dims, 59)
+    sigma, omega = O.kenney_laub(12, 0.4)
+    A = O.dense_hw(dims, U, mu)
+    h = 1e-6
+    Ad = (O.dense_hw(dims, U, mu + h) - O.dense_hw(dims, U, mu - h)) / (2 * h)   # A' (linear in e^{+-mu})
+    dec = O.eig(A)
+    e = 4  # the next eigenpairs, kept for the reduced resolvents of the derivative
+    Ra, La, lama, _ = O.critical_eigenpairs(A, m + e, decomposition=dec)
+    R, L, lam = Ra[:, :m], La[:, :m], lama[:m]
+    w, X, Xi = dec
+    order = np.lexsort((w.imag, w.real, np.abs(w)))
+    w, X, Xi = w[order], X[:, order], Xi[order, :]
+    g = lambda t: t * np.sum(omega[None, :] / (t[:, None] ** 2 - sigma[None, :]), axis=1)
+    gp = lambda t: np.sum(omega[None, :] * (-(t[:, None] ** 2) - sigma[None, :]) / (t[:, None] ** 2 - sigma[None, :]) ** 2,
+                          axis=1)
+    fw = g(w)
+    fpw = gp(w)
+    fw[:m] = np.sign(w[:m].real)
+    fpw[:m] = 0.0
+    D = w[:, None] - w[None, :]
+    same = np.abs(D) < 1e-12
+    Fh = np.where(same, 0, (fw[:, None] - fw[None, :]) / np.where(same, 1, D))
+    Fh[np.arange(len(w)), np.arange(len(w))] = fpw
+    dF = X @ (Fh * (Xi @ Ad @ X)) @ Xi
+    dmu_ref = np.real(np.vdot(c, dF @ b))
+    x_ref = X @ (fw * (Xi @ b))
+    bt = torch.from_numpy(b).cuda().requires_grad_(True)
+    mut = torch.tensor(mu, dtype=torch.float64, requires_grad=True)
+    with _ctx(dims, U, mu, sigma, omega) as ctx:
+        ctx.set_deflation(R, L, lam, extra=(Ra[:, m:], La[:, m:], lama[m:]))
+        x = SignApply.apply(bt, mut, ctx)
+        assert np.linalg.norm(x.detach().cpu().numpy() - x_ref) < 1e-9 * np.linalg.norm(x_ref)
+        loss = torch.vdot(torch.from_numpy(c).cuda(), x).real
+        loss.backward()
+    gb_ref = (X @ (fw[:, None] * Xi)).conj().T @ c
+    assert np.linalg.norm(bt.grad.cpu().numpy() - gb_ref) < 1e-9 * np.linalg.norm(gb_ref)
+    assert abs(float(mut.grad) - dmu_ref) < 1e-7 * max(1.0, abs(dmu_ref)), (float(mut.grad), dmu_ref)
