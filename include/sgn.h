@@ -67,6 +67,14 @@ typedef enum { SGN_PREC_FP64 = 0, SGN_PREC_MIXED = 1 } sgn_precision;
 /* Storage of the FP32 stencil's links (mixed form only). */
 typedef enum { SGN_LINKS_FP32 = 0, SGN_LINKS_BF16 = 1 } sgn_link_storage;
 
+/* Which Krylov space carries the partial fractions (Sec. 2 with eq. (6.2)):
+ *  SGN_FORM_A2:  the s systems (A^2 - sigma_i) x_i = A (I - P) b in K(A^2) (default);
+ *  SGN_FORM_A:   the same function split as t / (t^2 - sigma) = [(t - a)^{-1} + (t + a)^{-1}] / 2,
+ *                a = sqrt(sigma_i) (a = +-i tan(theta_i)/c for eq. (6.2)'s negative shifts):
+ *                2s systems (A -+ a_i) x = (I - P) b with weights omega_i / 2 in K(A) --
+ *                one stencil per Krylov step instead of two.  FP64 form only. */
+typedef enum { SGN_FORM_A2 = 0, SGN_FORM_A = 1 } sgn_formulation;
+
 /* Flags of sgn_apply. */
 #define SGN_APPLY_HOST_BUFFERS 1  /* b and x are host pointers (copied inside the call) */
 #define SGN_APPLY_ADJOINT 2       /* apply sign(H_W(-mu)) = sign(H_W(mu))^dag instead */
@@ -143,6 +151,11 @@ SGN_API int sgn_set_restart(sgn_ctx* ctx, int k, double tol, int max_cycles, int
  * of x that refinement aims at (e.g. 1e-8).  link_storage selects FP32 or BF16
  * links for the FP32 stencil. */
 SGN_API int sgn_set_precision(sgn_ctx* ctx, int precision, double target_rel_err, int link_storage);
+
+/* Krylov space of the partial fractions (sgn_formulation).  SGN_FORM_A needs
+ * the FP64 form and has no per-shift output (sgn_apply_shifts, sgn_grad_mu
+ * return SGN_ERR_STATE).  Errors: SGN_ERR_ARG. */
+SGN_API int sgn_set_formulation(sgn_ctx* ctx, int form);
 
 /* Mixed form only (no counterpart in the paper, which works in FP64): the
  * restart length of the FP32 correction solves that bring each shifted

@@ -11,11 +11,11 @@ import ctypes as C
 import numpy as np
 
 from . import _abi
-from ._abi import (APPLY_ADJOINT, APPLY_HOST_BUFFERS, HW_ADJOINT, HW_PACKED, LINKS_BF16, LINKS_FP32, PREC_FP64,
-                   PREC_MIXED, Report, SignError, check, lib)
+from ._abi import (APPLY_ADJOINT, APPLY_HOST_BUFFERS, FORM_A, FORM_A2, HW_ADJOINT, HW_PACKED, LINKS_BF16,
+                   LINKS_FP32, PREC_FP64, PREC_MIXED, Report, SignError, check, lib)
 
 __all__ = ["SignContext", "kenney_laub", "SignError", "PREC_FP64", "PREC_MIXED", "LINKS_FP32", "LINKS_BF16",
-           "HW_ADJOINT", "HW_PACKED", "sign_apply", "SignApply"]
+           "HW_ADJOINT", "HW_PACKED", "FORM_A2", "FORM_A", "sign_apply", "SignApply"]
 
 
 def kenney_laub(s: int, c: float = 1.0):
@@ -112,6 +112,10 @@ class SignContext:
 
     def set_precision(self, precision=PREC_FP64, target_rel_err=1e-8, link_storage=LINKS_FP32):
         check(lib().sgn_set_precision(self._h, int(precision), float(target_rel_err), int(link_storage)))
+
+    def set_formulation(self, form=FORM_A2):
+        """FORM_A2: s systems in K(A^2) (eq. 6.2 as written); FORM_A: 2s systems in K(A)."""
+        check(lib().sgn_set_formulation(self._h, int(form)))
 
     def set_refinement(self, k_refine=0, max_batch=0):
         """Mixed form: restart length and batch size of the correction solves (0: defaults)."""

@@ -15,6 +15,7 @@ PREC_FP64, PREC_MIXED = 0, 1
 LINKS_FP32, LINKS_BF16 = 0, 1
 APPLY_HOST_BUFFERS, APPLY_ADJOINT, APPLY_NO_A = 1, 2, 4
 HW_ADJOINT, HW_PACKED = 1, 2
+FORM_A2, FORM_A = 0, 1
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
@@ -45,6 +46,7 @@ SIGNATURES = {
     "sgn_set_restart": (C.c_int, [P, C.c_int, C.c_double, C.c_int, C.c_int]),
     "sgn_set_precision": (C.c_int, [P, C.c_int, C.c_double, C.c_int]),
     "sgn_set_refinement": (C.c_int, [P, C.c_int, C.c_int]),
+    "sgn_set_formulation": (C.c_int, [P, C.c_int]),
     "sgn_set_deflation": (C.c_int, [P, C.c_int, P, P, P, C.c_int]),
     "sgn_set_deflation_extra": (C.c_int, [P, C.c_int, P, P, P, C.c_int]),
     "sgn_build_deflation": (C.c_int, [P, C.c_int, C.c_int, C.c_double, P]),

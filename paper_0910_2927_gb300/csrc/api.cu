@@ -242,6 +242,12 @@ SGN_API int sgn_set_precision(sgn_ctx* c, int precision, double target_rel_err, 
     return SGN_OK;
 }
 
+SGN_API int sgn_set_formulation(sgn_ctx* c, int form) {
+    if (!c || (form != SGN_FORM_A2 && form != SGN_FORM_A)) return fail(SGN_ERR_ARG, "sgn_set_formulation: bad argument");
+    c->form = form;
+    return SGN_OK;
+}
+
 SGN_API int sgn_set_refinement(sgn_ctx* c, int k_refine, int max_batch) {
     if (!c || k_refine < 0 || k_refine > 64 || max_batch < 0 || max_batch > 4096)
         return fail(SGN_ERR_ARG, "sgn_set_refinement: need 0 <= k_refine <= 64, 0 <= max_batch <= 4096");
@@ -518,6 +524,7 @@ SGN_API int sgn_dhw_dmu_apply(sgn_ctx* c, const double* in, double* out, int nrh
 SGN_API int sgn_grad_mu(sgn_ctx* c, const double* b, const double* g, int nrhs, double* dmu) {
     if (!c || !b || !g || !dmu || nrhs < 1) return fail(SGN_ERR_ARG, "sgn_grad_mu: bad argument");
     if (!c->have_gauge || c->sigma.empty()) return fail(SGN_ERR_STATE, "sgn_grad_mu: gauge field and rational function needed");
+    if (c->form != SGN_FORM_A2) return fail(SGN_ERR_STATE, "sgn_grad_mu: needs the A^2 formulation (per-shift iterates)");
     SGN_CHECK(enter(c));
     const size_t nn = (size_t)c->n * nrhs;
     SGN_CHECK(dev_alloc(c, c->stage, 2 * nn * sizeof(double2)));

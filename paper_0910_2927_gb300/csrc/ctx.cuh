@@ -86,6 +86,7 @@ struct sgn_ctx {
     int precision = SGN_PREC_FP64;
     double target = 1e-8;
     int link_storage = SGN_LINKS_FP32;
+    int form = SGN_FORM_A2;  // Krylov space of the partial fractions (sgn_formulation)
     int k_refine = 0;    // restart length of the mixed form's correction solves (0: min(k, 16))
     int refine_batch = 0;  // shifted systems per correction batch (0: min(s nrhs, 4 nrhs), memory-bounded)
 

@@ -221,6 +221,7 @@ struct CycleArgs {
     double2* xs = nullptr;    // FP64 per-shift iterates, may be null
     int64_t xs_shift = 0, xs_col = 0;
     bool gmres = false;       // minimal-residual restarts (one shift per column, FP64 engines)
+    bool op_a = false;        // Krylov space of A itself (the split form), else of A^2
 };
 
 uint64_t cycle_key(const sgn_ctx* c, const Engine& E, const CycleArgs& a) {
@@ -241,6 +242,7 @@ uint64_t cycle_key(const sgn_ctx* c, const Engine& E, const CycleArgs& a) {
     h = mix(h, a.xs_shift);
     h = mix(h, a.xs_col);
     h = mix(h, a.gmres);
+    h = mix(h, a.op_a);
     h = mix(h, (uint64_t)(uintptr_t)c->U64.p);
     h = mix(h, (uint64_t)(uintptr_t)c->U32.p);
     h = mix(h, (uint64_t)(uintptr_t)c->U16.p);
@@ -317,13 +319,15 @@ cudaError_t cycle_dcgs(const sgn_ctx* c, Engine& E, const CycleArgs& a, cudaStre
     const double stb = (double)c->vol * 4 * 9 * sizeof(T) + 2 * fb;  // links once, in and out once
     Timer tm(c, E, st);
     for (int j = 0; j < k; ++j) {
-        // z = A^2 u_j (u_j: candidate for v_j, once orthogonalised)
+        // z = A^2 u_j (u_j: candidate for v_j, once orthogonalised); z = A u_j in the split form
         CU(tm.begin(0, stb));
-        CU(apply_hw<T>(c, t, V + j * sj, ncol, a.adjoint, S.skip, st));
+        CU(apply_hw<T>(c, a.op_a ? w : t, V + j * sj, ncol, a.adjoint, S.skip, st));
         CU(tm.end());
-        CU(tm.begin(0, stb));
-        CU(apply_hw<T>(c, w, t, ncol, a.adjoint, S.skip, st));
-        CU(tm.end());
+        if (!a.op_a) {
+            CU(tm.begin(0, stb));
+            CU(apply_hw<T>(c, w, t, ncol, a.adjoint, S.skip, st));
+            CU(tm.end());
+        }
         CU(tm.begin(1, (j + 2) * fb));
         CU(dcgs_dots<T>(VB, j, V + j * sj, w, sr, n, ncol, rd, S.skip, st));
         CU(tm.end());
@@ -396,8 +400,12 @@ cudaError_t cycle(const sgn_ctx* c, Engine& E, const CycleArgs& a, cudaStream_t 
     const Basis<T> VB{V, sj, sr};
     for (int j = 0; j < k; ++j) {
         // w = A^2 v_j
-        CU(apply_hw<T>(c, t, V + j * sj, ncol, a.adjoint, S.skip, st));
-        CU(apply_hw<T>(c, w, t, ncol, a.adjoint, S.skip, st));
+        if (a.op_a) {
+            CU(apply_hw<T>(c, w, V + j * sj, ncol, a.adjoint, S.skip, st));
+        } else {
+            CU(apply_hw<T>(c, t, V + j * sj, ncol, a.adjoint, S.skip, st));
+            CU(apply_hw<T>(c, w, t, ncol, a.adjoint, S.skip, st));
+        }
         // CGS2: h1 = V^dag w; w -= V h1, h2 = V^dag w; v_{j+1} = (w - V h2) / h_{j+1,j}
         CU(mdot<T>(VB, j + 1, w, sr, n, ncol, rd, 1, S.skip, st));
         CU(reduce(rd, j + 2, ncol, RM_H1, j, S, nullptr, st));
@@ -976,10 +984,38 @@ int solve(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int ncol, 
           sgn_report* rep, const std::vector<std::complex<double>>* cshift) {
     cudaStream_t st = c->work;
     const int64_t n = c->n;
-    // cshift: complex shifts with unit weights instead of the rational function's (FP64 form)
-    const int s = cshift ? (int)cshift->size() : (int)c->sigma.size();
+    // Shifted systems and weights: cshift (complex shifts, unit weights); the split form
+    // t / (t^2 - sigma) = 1/2 [(t - a)^{-1} + (t + a)^{-1}], a = sqrt(sigma): 2s systems in A
+    // itself with weights omega/2 and no A on the right-hand side; else eq. (6.2)'s s
+    // systems in A^2.
+    const bool split = !cshift && c->form == SGN_FORM_A;
+    std::vector<std::complex<double>> sh;
+    std::vector<double> wt;
+    if (cshift) {
+        sh = *cshift;
+        wt.assign(sh.size(), 1.0);
+    } else if (split) {
+        for (size_t i = 0; i < c->sigma.size(); ++i) {
+            const std::complex<double> a = std::sqrt(std::complex<double>(c->sigma[i], 0.0));
+            sh.push_back(a);
+            sh.push_back(-a);
+            wt.push_back(0.5 * c->omega[i]);
+            wt.push_back(0.5 * c->omega[i]);
+        }
+    } else {
+        for (size_t i = 0; i < c->sigma.size(); ++i) {
+            sh.push_back(c->sigma[i]);
+            wt.push_back(c->omega[i]);
+        }
+    }
+    const int s = (int)sh.size();
     const int k = c->k;
     const int m = c->m;
+    if (split && (c->precision == SGN_PREC_MIXED || x_shift)) {
+        set_error("solve: the split form (Krylov space of A) runs in the FP64 form, without per-shift output");
+        return SGN_ERR_STATE;
+    }
+    if (split) no_a = true;
     if (c->precision == SGN_PREC_MIXED && !cshift) return solve_mixed(c, b, x, x_shift, ncol, adjoint, no_a, rep);
     if (s < 1) {
         set_error("solve: no shifts");
@@ -1000,9 +1036,9 @@ int solve(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int ncol, 
     std::vector<double> sig_cols((size_t)ncol * s), om_cols((size_t)ncol * s), sim_cols((size_t)ncol * s, 0.0);
     for (int col = 0; col < ncol; ++col)
         for (int i = 0; i < s; ++i) {
-            sig_cols[(size_t)col * s + i] = cshift ? (*cshift)[i].real() : c->sigma[i];
-            sim_cols[(size_t)col * s + i] = cshift ? (*cshift)[i].imag() : 0.0;
-            om_cols[(size_t)col * s + i] = cshift ? 1.0 : c->omega[i];
+            sig_cols[(size_t)col * s + i] = sh[i].real();
+            sim_cols[(size_t)col * s + i] = sh[i].imag();
+            om_cols[(size_t)col * s + i] = wt[i];
         }
     SGN_CHECK(fill_shift_tables(c, *E, sig_cols.data(), om_cols.data(), sim_cols.data()));
 
@@ -1043,6 +1079,7 @@ int solve(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int ncol, 
     a.xs = xs;
     a.xs_shift = (int64_t)ncol * n;
     a.xs_col = n;
+    a.op_a = split;
     RunResult rr;
     int status = run_engine<double2>(c, *E, a, c->tol, c->max_cycles, &rr);
     if (status == SGN_OK) {
@@ -1056,7 +1093,7 @@ int solve(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int ncol, 
     if (rep) {
         rep->status = status;
         rep->cycles = rr.cycles;
-        rep->matvecs = 1 + 2 * k * rr.cycles;
+        rep->matvecs = split ? k * rr.cycles : 1 + 2 * k * rr.cycles;
         rep->refine_rounds = 0;
         rep->refine_cycles = 0;
         rep->res_est = rr.resmax;

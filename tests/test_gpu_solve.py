@@ -142,3 +142,32 @@ def test_edge_cases(small):
         assert rep["breakdown"] == 1 and rep["status"] == 0
         g = w[j] * np.sum(omega / (w[j] ** 2 - sigma))
         assert _rel(x.cpu().numpy(), g * bev) < 1e-10
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_split_form_matches_dense_target(lattice4, adjoint):
+    """The split form (2s systems (A -+ a_i) in the Krylov space of A, weights omega_i/2)
+    computes the same deflated rational function as the A^2 form: both match the dense
+    target to the solve tolerance, the split form with k A-applications per cycle."""
+    import paper_0910_2927_gb300 as pkg
+    d = lattice4
+    c = O.scale_from_bounds(abs(d["lam_next"][0]), 6.0)
+    sigma, omega = O.kenney_laub(16, c)
+    b = np.stack([d["b"], si.gaussian_field(d["dims"], 77)])
+    mu = -d["mu"] if adjoint else d["mu"]
+    A = O.dense_hw(d["dims"], d["U"], mu)
+    R, L, lam = (d["L"], d["R"], np.conj(d["lam"])) if adjoint else (d["R"], d["L"], d["lam"])
+    with _ctx(d["dims"], d["U"], d["mu"], sigma, omega, k=30, tol=1e-12) as ctx:
+        ctx.set_deflation(d["R"], d["L"], d["lam"])
+        ctx.set_formulation(pkg.FORM_A)
+        x, rep = ctx.apply(torch.from_numpy(b).cuda(), adjoint=adjoint)
+        x = x.cpu().numpy()
+        assert rep["status"] == 0 and rep["matvecs"] == 30 * rep["cycles"]
+        with pytest.raises(pkg.SignError):       # no per-shift iterates in the split form
+            ctx.apply(torch.from_numpy(b).cuda(), shifts=True)
+        ctx.set_precision(pkg.PREC_MIXED, 1e-8)
+        with pytest.raises(pkg.SignError):       # FP64 form only
+            ctx.apply(torch.from_numpy(b).cuda())
+    for r in range(2):
+        xstar = O.deflated_target(A, b[r], sigma, omega, R, L, lam)
+        assert _rel(x[r], xstar) < 1e-9
