@@ -142,38 +142,50 @@ def dist_env():
 
 
 class Dist:
-    def __init__(self, world, local):
+    """Replicas: one workload per rank, no collective on the data path; only the
+    timing (max over ranks) and the unit count (sum over ranks) are reduced.
+    backend "nccl" on the rank's GPU (the benchmark), "gloo" on the CPU (tests)."""
+
+    def __init__(self, world, local, backend="nccl"):
         self.world = world
         self.pg = None
+        self.device = "cuda" if backend == "nccl" else "cpu"
         if world > 1:
             import torch.distributed as dist
             import torch
-            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+            if backend == "nccl":
+                dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+            else:
+                dist.init_process_group(backend)
             self.pg = dist
 
     def barrier(self):
         if self.pg:
             self.pg.barrier()
 
-    def max(self, v):
+    def _reduce(self, v, op):
         if not self.pg:
             return v
         import torch
-        t = torch.tensor([float(v)], device="cuda")
-        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        t = torch.tensor([float(v)], dtype=torch.float64, device=self.device)
+        self.pg.all_reduce(t, op=op)
         return float(t.item())
 
+    def max(self, v):
+        return self._reduce(v, self.pg.ReduceOp.MAX if self.pg else None)
+
     def sum(self, v):
-        if not self.pg:
-            return v
-        import torch
-        t = torch.tensor([float(v)], device="cuda")
-        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
-        return float(t.item())
+        return self._reduce(v, self.pg.ReduceOp.SUM if self.pg else None)
 
     def close(self):
         if self.pg:
             self.pg.destroy_process_group()
+
+
+def whole_job_rate(D, units_local, seconds_local):
+    """Units processed by all ranks over the slowest rank's time (weak scaling)."""
+    t_max = D.max(seconds_local)
+    return D.sum(units_local) / t_max, t_max
 
 
 # ------------------------------------------------------------------- oracle --
@@ -342,9 +354,7 @@ def run_ours(args, w, name):
         kt[name_k] = {"ms": ms.value, "launches": nl.value, "bytes": by.value}
     lib.sgn_set_kernel_timing(ctx._h, 0)
     D.barrier()
-    t_max = D.max(t_mixed)
-    units = D.sum(nrhs * args.steps)
-    value = units / t_max
+    value, t_max = whole_job_rate(D, nrhs * args.steps, t_mixed)
     err = None if x64 is None else float(torch.linalg.vector_norm(xm - x64) / torch.linalg.vector_norm(x64))
     err_mixed, err_fp64 = rel_err(xm), (rel_err(x64) if x64 is not None else None)
 
@@ -375,7 +385,7 @@ def run_ours(args, w, name):
         ts = time.perf_counter()
         xh, reph = ctx.apply(Bh)
         tt.append(time.perf_counter() - ts)
-    e2e_value = D.sum(nrhs) / D.max(statistics.median(tt))
+    e2e_value, _ = whole_job_rate(D, nrhs, statistics.median(tt))
     ctx.close()
 
     # ---- stencil alone at 24^4 (HBM-bound): FP32 links and spinors, 12 columns

@@ -1,0 +1,71 @@
+"""The benchmark's multi-GPU path is replicas only (one workload per rank, no
+collective on the data path): the whole-job rate is the units of all ranks over
+the slowest rank's time.  Checked here with two gloo ranks on the CPU."""
+import io
+import os
+import socket
+import sys
+from contextlib import redirect_stdout
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    import bench
+    D = bench.Dist(world, rank, backend="gloo")
+    units = 12 * (rank + 1)           # ranks may process different amounts
+    seconds = 0.5 + rank              # the slowest rank sets the time
+    value, t_max = bench.whole_job_rate(D, units, seconds)
+    D.barrier()
+    out[rank] = (value, t_max)
+    D.close()
+
+
+def test_whole_job_rate_two_gloo_ranks():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    procs = [ctx.Process(target=_rank, args=(r, world, port, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    for r in range(world):
+        value, t_max = out[r]
+        assert t_max == pytest.approx(1.5)
+        assert value == pytest.approx((12 + 24) / 1.5)
+
+
+def test_single_rank_needs_no_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    D = bench.Dist(1, 0)
+    assert bench.whole_job_rate(D, 24, 2.0) == (12.0, 2.0)
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
+    """Under torchrun every rank but 0 exits without work and prints nothing."""
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    buf = io.StringIO()
+    with redirect_stdout(buf):
+        bench.reference_arm(None, bench.WORKLOADS["4^4"], "4^4")
+    assert buf.getvalue() == ""
