@@ -246,6 +246,53 @@ def sign_eig(A, decomposition=None):
     return (X * np.where(w.real > 0, 1.0, -1.0)) @ Xinv
 
 
+def roberts_newton_sign(M, tol=1e-14, max_it=100):
+    """sign(M) of a small dense matrix by Roberts' Newton iteration (Sec. 6, the
+    direct-projection comparison): X_0 = M, X_{j+1} = (X_j + X_j^{-1}) / 2 until the
+    update is below tol relative to X_j."""
+    X = np.asarray(M, dtype=np.complex128).copy()
+    for _ in range(max_it):
+        Xn = 0.5 * (X + np.linalg.inv(X))
+        if np.linalg.norm(Xn - X) <= tol * np.linalg.norm(Xn):
+            return Xn
+        X = Xn
+    return X
+
+
+def direct_projection(A, b, k, R=None, L=None, lam=None):
+    """Direct projection of eq. (6.3): x = x_P + ||r|| V_k sign(H_k) e_1 with r = (I - P) b,
+    x_P = R sign(Re Lambda) L^dag b, and V_k, H_k from k steps of Arnoldi on A started at r
+    (classical Gram-Schmidt with one reorthogonalisation, eq. (2.4)); sign(H_k) by
+    Roberts' Newton iteration.  For k = n (no breakdown) the result is sign(A) b exactly."""
+    n = A.shape[0]
+    b = np.asarray(b, dtype=np.complex128).reshape(-1)
+    if R is None or R.shape[1] == 0:
+        xP = np.zeros(n, dtype=np.complex128)
+        r = b.copy()
+    else:
+        c = L.conj().T @ b
+        xP = R @ (np.where(np.asarray(lam).real > 0, 1.0, -1.0) * c)
+        r = b - R @ c
+    beta = np.linalg.norm(r)
+    V = np.zeros((n, k + 1), dtype=np.complex128)
+    H = np.zeros((k + 1, k), dtype=np.complex128)
+    V[:, 0] = r / beta
+    kk = k
+    for j in range(k):
+        w = A @ V[:, j]
+        for _ in range(2):
+            h = V[:, :j + 1].conj().T @ w
+            w = w - V[:, :j + 1] @ h
+            H[:j + 1, j] += h
+        H[j + 1, j] = np.linalg.norm(w)
+        if H[j + 1, j].real <= 1e-14 * np.linalg.norm(H[:j + 2, j]):
+            kk = j + 1
+            break
+        V[:, j + 1] = w / H[j + 1, j]
+    S = roberts_newton_sign(H[:kk, :kk])
+    return xP + beta * (V[:, :kk] @ S[:, 0])
+
+
 def sign_schur(A):
     """Exact sign(A) from the Schur form sorted right half-plane first.
 

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+import seeded_inputs as si
 
 
 @pytest.mark.parametrize("s", [1, 2, 7, 16, 20])
@@ -64,3 +65,29 @@ def test_error_bound_matches_direct_evaluation():
     for s, c in [(16, 0.6), (20, 0.3)]:
         direct = np.max(np.abs(np.sign(lam.real) - O.kl_closed_form(c * lam, s)))
         assert O.rational_error_bound(lam, s, c) == pytest.approx(direct, rel=1e-6, abs=1e-15)
+
+
+def test_roberts_newton_sign_is_the_spectral_sign():
+    """Roberts' iteration on a random non-normal matrix equals sign(M) = X sign(Re L) X^{-1}."""
+    rng = np.random.default_rng(5)
+    M = rng.standard_normal((12, 12)) + 1j * rng.standard_normal((12, 12))
+    S = O.roberts_newton_sign(M)
+    w, X = np.linalg.eig(M)
+    ref = (X * np.where(w.real > 0, 1.0, -1.0)) @ np.linalg.inv(X)
+    assert np.linalg.norm(S - ref) < 1e-10 * np.linalg.norm(ref)
+    assert np.linalg.norm(S @ S - np.eye(12)) < 1e-10 * 12
+
+
+def test_direct_projection_exact_at_full_dimension():
+    """Eq. (6.3) with k = n (the Krylov space is the whole space) gives sign(A) b; with
+    deflation the deflated part is exact at any k and the error falls as k grows."""
+    dims, mu = (2, 2, 2, 2), 0.4
+    U = si.random_su3_links(dims, 0.6, 81)
+    A = O.dense_hw(dims, U, mu)
+    b = si.gaussian_field(dims, 82)
+    xs = O.sign_eig(A) @ b
+    n = A.shape[0]
+    assert np.linalg.norm(O.direct_projection(A, b, n) - xs) < 1e-9 * np.linalg.norm(xs)
+    R, L, lam, _ = O.critical_eigenpairs(A, 6, extra=1)
+    errs = [np.linalg.norm(O.direct_projection(A, b, k, R, L, lam) - xs) for k in (16, 48, n)]
+    assert errs[2] < 1e-9 * np.linalg.norm(xs) and errs[1] < errs[0]
