@@ -10,7 +10,9 @@ Two layers, both FP64:
   Algorithm 1 (restarted FOM-LR(m,k)) in the A^2 reading of eq. (6.2).
 * O1, dense (NumPy/SciPy, small lattices only): the dense matrix of H_W(mu),
   its eigendecomposition (critical eigenpairs for LR deflation, Sec. 4), the
-  dense deflated rational target and the exact sign function.
+  dense deflated rational target and the exact sign function; the direct
+  projection of eq. (6.3) (non-restarted Arnoldi on A, sign(H_k) by Roberts'
+  Newton iteration), the method the paper compares Algorithm 1 with.
 
 Every function names the passage of the paper it follows.
 """
@@ -238,6 +240,81 @@ def deflated_target(A, b, sigma, omega, R=None, L=None, lam=None):
     for sg, om in zip(sigma, omega):
         x += om * np.linalg.solve(A2 - sg * eye, bt)
     return x
+
+
+def gmres_lr(A, b, sigma, omega, k, tol, max_cycles=1000, R=None, L=None, lam=None, seed=None):
+    """LR-deflated restarted multishift GMRES (GMRES-LR, Sec. 4 with Sec. 2's restarted multishift
+    GMRES of the cited Frommer-Glassner work), A^2 reading of eq. (6.2), dense A, small cases.
+
+    x = x_P + sum_i omega_i x_i with (A^2 - sigma_i) x_i = A (I - P) b.  One Krylov space of A^2
+    per cycle, built by Arnoldi (CGS2) from the seed residual r.  The seed shift (default: the
+    smallest |sigma_i|) takes the minimal-residual step, y_s = argmin ||beta e_1 - (Hbar_k -
+    sigma_s I~) y||, leaving r <- V_{k+1} z, z = beta e_1 - (Hbar_k - sigma_s I~) y_s.  Every other
+    shift keeps its residual collinear, r_i = rho_i r: (Hbar_k - sigma_i I~) y_i + rho_i' z =
+    beta rho_i e_1, a square (k+1) x (k+1) system for (y_i, rho_i').  After each cycle the new
+    seed residual is projected with I - P (eq. (4.5)).  Converged when every |rho_i| ||r|| <=
+    tol ||A (I - P) b||.  Returns (x, cycles, [|rho_i| ||r|| / ||b~||])."""
+    n = A.shape[0]
+    b = np.asarray(b, dtype=np.complex128).reshape(-1)
+    sigma = np.asarray(sigma, dtype=np.complex128)
+    omega = np.asarray(omega, dtype=np.float64)
+    s = len(sigma)
+    seed = int(np.argmin(np.abs(sigma))) if seed is None else int(seed)
+    if R is None or R.shape[1] == 0:
+        xP = np.zeros(n, dtype=np.complex128)
+        r0 = b.copy()
+        proj = lambda v: v
+    else:
+        c = L.conj().T @ b
+        xP = R @ (np.where(np.asarray(lam).real > 0, 1.0, -1.0) * c)
+        r0 = b - R @ c
+        proj = lambda v: v - R @ (L.conj().T @ v)
+    bt = A @ r0
+    bnorm = np.linalg.norm(bt)
+    r = bt.copy()
+    rho = np.ones(s, dtype=np.complex128)
+    active = np.ones(s, dtype=bool)
+    X = np.zeros((s, n), dtype=np.complex128)
+    cycles = 0
+    res = np.abs(rho) * np.linalg.norm(r) / bnorm
+    while cycles < max_cycles and np.any(res > tol):
+        beta = np.linalg.norm(r)
+        V = np.zeros((n, k + 1), dtype=np.complex128)
+        H = np.zeros((k + 1, k), dtype=np.complex128)
+        V[:, 0] = r / beta
+        kk = k
+        for j in range(k):
+            w = A @ (A @ V[:, j])
+            for _ in range(2):
+                h = V[:, :j + 1].conj().T @ w
+                w = w - V[:, :j + 1] @ h
+                H[:j + 1, j] += h
+            H[j + 1, j] = np.linalg.norm(w)
+            if abs(H[j + 1, j]) <= 1e-14 * np.linalg.norm(H[:j + 2, j]):
+                kk = j + 1
+                break
+            V[:, j + 1] = w / H[j + 1, j]
+        Hb = H[:kk + 1, :kk]
+        It = np.eye(kk + 1, kk)
+        e1 = np.zeros(kk + 1, dtype=np.complex128)
+        e1[0] = beta
+        # the seed's residual is the reference vector: rho[seed] = 1 throughout
+        Ms = Hb - sigma[seed] * It
+        ys = np.linalg.lstsq(Ms, e1, rcond=None)[0]
+        z = e1 - Ms @ ys
+        X[seed] += V[:, :kk] @ ys
+        for i in range(s):
+            if i == seed or not active[i]:
+                continue
+            Mi = np.concatenate([Hb - sigma[i] * It, z[:, None]], axis=1)
+            sol = np.linalg.solve(Mi, rho[i] * e1)
+            X[i] += V[:, :kk] @ sol[:kk]
+            rho[i] = sol[kk]
+        r = proj(V[:, :kk + 1] @ z)
+        cycles += 1
+        res = np.abs(rho) * np.linalg.norm(r) / bnorm
+        active = active & (res > tol)
+    return xP + omega @ X, cycles, res
 
 
 def sign_eig(A, decomposition=None):

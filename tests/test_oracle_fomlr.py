@@ -149,3 +149,60 @@ def test_critical_pairs(lattice4):
     assert np.abs(L.conj().T @ A - lam[:, None] * L.conj().T).max() < 1e-10
     assert np.abs(L.conj().T @ R - np.eye(len(lam))).max() < 1e-10
     assert np.all(np.abs(lam) <= abs(d["lam_next"][0]) + 1e-15)
+
+
+def _gm_setup(dims=(2, 2, 2, 2), mu=0.3, seed=61):
+    U = si.random_su3_links(dims, 0.6, seed)
+    A = O.dense_hw(dims, U, mu)
+    b = si.gaussian_field(dims, seed + 1)
+    return A, b
+
+
+def test_gmres_lr_single_shift_is_minimal_residual():
+    """s = 1, one cycle: the iterate minimises ||b~ - (A^2 - sigma) x|| over K_k(A^2, b~) (the
+    defining property of GMRES), checked by least squares on an explicit power basis."""
+    A, b = _gm_setup()
+    n = A.shape[0]
+    A2 = A @ A
+    bt = A @ b
+    sg, k = -0.7, 6
+    x, cyc, _ = O.gmres_lr(A, b, [sg], [1.0], k, tol=1e-30, max_cycles=1)
+    K = np.empty((n, k), dtype=np.complex128)
+    v = bt / np.linalg.norm(bt)
+    for j in range(k):
+        K[:, j] = v
+        v = A2 @ v
+        v /= np.linalg.norm(v)
+    M = (A2 - sg * np.eye(n)) @ K
+    y = np.linalg.lstsq(M, bt, rcond=None)[0]
+    assert cyc == 1
+    assert np.linalg.norm(x - K @ y) < 1e-8 * np.linalg.norm(K @ y)
+
+
+def test_gmres_lr_residuals_collinear_and_converges_to_target():
+    """Multishift: after one cycle every shift's true residual is a multiple of the seed's
+    (the collinearity that lets all shifts share one Krylov space); run to convergence, the
+    deflated sum equals the dense target of eqs. (4.2)-(4.3) with (6.2)."""
+    A, b = _gm_setup()
+    n = A.shape[0]
+    A2 = A @ A
+    bt = A @ b
+    sigma, omega = O.kenney_laub(5, 1.0)
+    k = 8
+    # per-shift iterates from one cycle: weights e_i pick one shift at a time
+    res = []
+    for i in range(len(sigma)):
+        w = np.zeros(len(sigma))
+        w[i] = 1.0
+        xi, _, _ = O.gmres_lr(A, b, sigma, w, k, tol=1e-30, max_cycles=1)
+        res.append(bt - (A2 - sigma[i] * np.eye(n)) @ xi)
+    seed = int(np.argmin(np.abs(sigma)))
+    r0 = res[seed]
+    for i, ri in enumerate(res):
+        coef = np.vdot(r0, ri) / np.vdot(r0, r0)
+        assert np.linalg.norm(ri - coef * r0) < 1e-9 * np.linalg.norm(ri)
+    R, L, lam, _ = O.critical_eigenpairs(A, 6, extra=1)
+    x, cyc, rr = O.gmres_lr(A, b, sigma, omega, k, tol=1e-11, max_cycles=500, R=R, L=L, lam=lam)
+    xt = O.deflated_target(A, b, sigma, omega, R, L, lam)
+    assert cyc > 1 and np.max(rr) <= 1e-11
+    assert np.linalg.norm(x - xt) < 1e-9 * np.linalg.norm(xt)
