@@ -322,7 +322,38 @@ def run_ours(args, w, name):
                  "matvecs_A2_form": rep64["matvecs"], "rel_err": rel_err(xs_)}
         ctx.set_formulation(pkg.FORM_A2)
 
-    # ---- mixed form (the headline); per-kernel CUDA events inside the captured cycles
+    # ---- GMRES-LR (restarted multishift GMRES, LR-deflated), FP64 form of the same function
+    gmres = None
+    if not args.skip_fp64_form:
+        ctx.set_precision(pkg.PREC_FP64)
+        ctx.set_method(pkg.METHOD_GMRES)
+        ctx.apply(bdev)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        xg_, repg_ = ctx.apply(bdev)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tg = e0.elapsed_time(e1) / 1000.0
+        gmres = {"value": nrhs / tg, "unit": UNIT, "cycles": repg_["cycles"], "cycles_fom": rep64["cycles"],
+                 "rel_err": rel_err(xg_)}
+        ctx.set_method(pkg.METHOD_FOM)
+        del xg_
+
+    # ---- the direct projection of eq. (6.3) (non-restarted Arnoldi on A, Roberts' Newton on
+    # H_k) at the Krylov dimensions asked for: the method the paper compares Algorithm 1 with
+    direct = []
+    for kd in [int(v) for v in args.direct_k.split(",") if v.strip()]:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        t0 = time.perf_counter()
+        xd, ku = ctx.apply_direct(bdev, kd)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        td = time.perf_counter() - t0
+        direct.append({"k": ku, "value": nrhs / td, "unit": UNIT, "seconds": td,
+                       "rel_diff_vs_rational_tol_1e-12": rel_err(xd)})
+        del xd
+
     import ctypes as C
     lib = pkg.lib()
     ctx.set_precision(pkg.PREC_MIXED, 1e-8, pkg.LINKS_FP32)
@@ -423,6 +454,8 @@ def run_ours(args, w, name):
                                                      "ms": t64 * 1000},
             "at_tol_1e-10": at_1e10,
             "fp64_split_form": split,
+            "fp64_gmres_lr": gmres,
+            "direct_projection": direct or None,
             "mixed_report": {k2: reps[-1][k2] for k2 in ("cycles", "refine_rounds", "refine_cycles", "err_est")},
             "stencil_24^4": st,
             "kernel_times": kt,
@@ -515,6 +548,7 @@ def main():
                     help="stopping tolerance on the shifted-system residuals, both forms")
     ap.add_argument("--skip-fp64-form", action="store_true", help="do not time the plain FP64 form")
     ap.add_argument("--no-stencil-24", action="store_true", help="do not time the 24^4 stencil")
+    ap.add_argument("--direct-k", default="", help="comma-separated Krylov dimensions for the direct projection")
     ap.add_argument("--stencil-only", action="store_true",
                     help="time only the 12-column FP32 stencil at 24^4 and print its numbers")
     args = ap.parse_args()

@@ -75,6 +75,17 @@ typedef enum { SGN_LINKS_FP32 = 0, SGN_LINKS_BF16 = 1 } sgn_link_storage;
  *                one stencil per Krylov step instead of two.  FP64 form only. */
 typedef enum { SGN_FORM_A2 = 0, SGN_FORM_A = 1 } sgn_formulation;
 
+/* The multishift Krylov method (Sec. 2 and Sec. 4):
+ *  SGN_METHOD_FOM:   FOM-LR, Algorithm 1 (default);
+ *  SGN_METHOD_GMRES: GMRES-LR, restarted multishift GMRES with LR deflation: the shift of
+ *                    smallest modulus (the slowest system) takes the minimal-residual step,
+ *                    y_s = argmin ||beta e_1 - (Hbar_k - sigma_s I~) y||, and its residual
+ *                    V_{k+1} z restarts the next cycle; every other shift keeps its residual
+ *                    collinear by the bordered (k+1) x (k+1) system
+ *                    [Hbar_k - sigma_i I~ | z] (y_i, rho_i') = beta rho_i e_1.
+ *                    FP64 form of SGN_FORM_A2 only. */
+typedef enum { SGN_METHOD_FOM = 0, SGN_METHOD_GMRES = 1 } sgn_method;
+
 /* Flags of sgn_apply. */
 #define SGN_APPLY_HOST_BUFFERS 1  /* b and x are host pointers (copied inside the call) */
 #define SGN_APPLY_ADJOINT 2       /* apply sign(H_W(-mu)) = sign(H_W(mu))^dag instead */
@@ -157,6 +168,10 @@ SGN_API int sgn_set_precision(sgn_ctx* ctx, int precision, double target_rel_err
  * return SGN_ERR_STATE).  Errors: SGN_ERR_ARG. */
 SGN_API int sgn_set_formulation(sgn_ctx* ctx, int form);
 
+/* Multishift method (sgn_method).  SGN_METHOD_GMRES with the mixed form or SGN_FORM_A
+ * makes sgn_apply return SGN_ERR_STATE.  Errors: SGN_ERR_ARG. */
+SGN_API int sgn_set_method(sgn_ctx* ctx, int method);
+
 /* Mixed form only (no counterpart in the paper, which works in FP64): the
  * restart length of the FP32 correction solves that bring each shifted
  * system's true FP64 residual below the tolerance (0: min(k, 16)), and how many
@@ -223,6 +238,39 @@ SGN_API int sgn_apply_shifts(sgn_ctx* ctx, const double* b, double* x, double* x
  * runs on the caller's packed fields directly (no staging, one kernel).
  * Errors: SGN_ERR_ARG (unknown precision or flag), SGN_ERR_STATE (no gauge). */
 SGN_API int sgn_hw_apply(sgn_ctx* ctx, const void* in, void* out, int nrhs, int precision, int flags);
+
+/* The overlap operator built on the sign function (Sec. 1):
+ *   y = D_ov b = b + gamma5 F(A) b,
+ * F(A) the deflated rational sign function sgn_apply computes (same settings:
+ * precision, deflation, tolerance).  b, y: nrhs complex128 device fields, natural
+ * order, not overlapping.  Errors: SGN_ERR_STATE (no gauge / rational function). */
+SGN_API int sgn_overlap_apply(sgn_ctx* ctx, const double* b, double* y, int nrhs);
+
+/* x = D_ov^{-1} b by restarted GMRES(k) from x = 0, every Arnoldi step one batched
+ * sign solve over the nrhs columns; stops when every column has
+ * ||b - D_ov x|| <= tol ||b|| (checked on the true residual at each restart) or after
+ * max_restarts restarts.  iterations (may be NULL): applications of D_ov in the Arnoldi
+ * steps; relres (may be NULL): the worst column's final relative residual.  The inner
+ * solves' tolerance (sgn_set_restart) should be well below tol.  b, x: device fields.
+ * Errors: SGN_ERR_ARG (k outside 1..64), SGN_ERR_NOT_CONVERGED (x holds the last iterate). */
+SGN_API int sgn_overlap_solve(sgn_ctx* ctx, const double* b, double* x, int nrhs, double tol, int k,
+                              int max_restarts, int* iterations, double* relres);
+
+/* The direct projection the paper compares Algorithm 1 with (Sec. 6, eq. (6.3)):
+ *   x = x_P + ||r|| V_k sign(H_k) e_1,   r = (I - P) b,   x_P = R sign(Re Lambda) L^dag b,
+ * V_k, H_k from k steps of Arnoldi on A = H_W(mu) itself started at r (two classical
+ * Gram-Schmidt passes, FP64), sign(H_k) by Roberts' Newton iteration
+ * X <- (X + X^{-1}) / 2 on the host.  No rational approximation and no restarts: the
+ * k + 1 basis fields per column stay in device memory, and the Newton step costs
+ * O(k^3) per column.  Uses the deflation set up by sgn_build_deflation or
+ * sgn_set_deflation (none when m = 0); ignores the rational function, precision and
+ * tolerance settings.  flags: 0 or SGN_APPLY_ADJOINT (A^dag = H_W(-mu)).  b, x: nrhs
+ * complex128 device fields, natural order, not overlapping.  k_used (may be NULL):
+ * the largest Krylov dimension used, below k only when an invariant subspace was
+ * found (where the projection is exact).  Errors: SGN_ERR_ARG (k outside 1..4096,
+ * unknown flag), SGN_ERR_STATE (no gauge), SGN_ERR_NOT_CONVERGED (the Newton
+ * iteration met a singular iterate: a Ritz value on the imaginary axis). */
+SGN_API int sgn_apply_direct(sgn_ctx* ctx, const double* b, double* x, int nrhs, int k, int flags, int* k_used);
 
 /* Layout conversion of nfield fields between the natural order
  * [site][spin][colour] and the packed order the library keeps internally:
@@ -295,7 +343,8 @@ SGN_API int sgn_set_kernel_timing(sgn_ctx* ctx, int on);
 
 /* Totals of class `cls` since timing was switched on: summed milliseconds,
  * launches, and algorithmic bytes (each input field read once, each output
- * field written once). */
+ * field written once; only the columns not yet converged when the cycle
+ * started count, since converged columns skip their work). */
 SGN_API int sgn_get_kernel_timing(sgn_ctx* ctx, int cls, double* ms, long long* launches, double* bytes);
 
 /* Thread-local message for the last failing call of this thread. */

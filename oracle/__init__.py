@@ -242,7 +242,8 @@ def deflated_target(A, b, sigma, omega, R=None, L=None, lam=None):
     return x
 
 
-def gmres_lr(A, b, sigma, omega, k, tol, max_cycles=1000, R=None, L=None, lam=None, seed=None):
+def gmres_lr(A, b, sigma, omega, k, tol, max_cycles=1000, R=None, L=None, lam=None, seed=None,
+             want_shifts=False):
     """LR-deflated restarted multishift GMRES (GMRES-LR, Sec. 4 with Sec. 2's restarted multishift
     GMRES of the cited Frommer-Glassner work), A^2 reading of eq. (6.2), dense A, small cases.
 
@@ -273,7 +274,6 @@ def gmres_lr(A, b, sigma, omega, k, tol, max_cycles=1000, R=None, L=None, lam=No
     bnorm = np.linalg.norm(bt)
     r = bt.copy()
     rho = np.ones(s, dtype=np.complex128)
-    active = np.ones(s, dtype=bool)
     X = np.zeros((s, n), dtype=np.complex128)
     cycles = 0
     res = np.abs(rho) * np.linalg.norm(r) / bnorm
@@ -304,7 +304,7 @@ def gmres_lr(A, b, sigma, omega, k, tol, max_cycles=1000, R=None, L=None, lam=No
         z = e1 - Ms @ ys
         X[seed] += V[:, :kk] @ ys
         for i in range(s):
-            if i == seed or not active[i]:
+            if i == seed:
                 continue
             Mi = np.concatenate([Hb - sigma[i] * It, z[:, None]], axis=1)
             sol = np.linalg.solve(Mi, rho[i] * e1)
@@ -313,7 +313,8 @@ def gmres_lr(A, b, sigma, omega, k, tol, max_cycles=1000, R=None, L=None, lam=No
         r = proj(V[:, :kk + 1] @ z)
         cycles += 1
         res = np.abs(rho) * np.linalg.norm(r) / bnorm
-        active = active & (res > tol)
+    if want_shifts:
+        return xP + omega @ X, cycles, res, X
     return xP + omega @ X, cycles, res
 
 

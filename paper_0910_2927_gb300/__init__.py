@@ -12,10 +12,10 @@ import numpy as np
 
 from . import _abi
 from ._abi import (APPLY_ADJOINT, APPLY_HOST_BUFFERS, FORM_A, FORM_A2, HW_ADJOINT, HW_PACKED, LINKS_BF16,
-                   LINKS_FP32, PREC_FP64, PREC_MIXED, Report, SignError, check, lib)
+                   LINKS_FP32, METHOD_FOM, METHOD_GMRES, PREC_FP64, PREC_MIXED, Report, SignError, check, lib)
 
 __all__ = ["SignContext", "kenney_laub", "SignError", "PREC_FP64", "PREC_MIXED", "LINKS_FP32", "LINKS_BF16",
-           "HW_ADJOINT", "HW_PACKED", "FORM_A2", "FORM_A", "sign_apply", "SignApply"]
+           "HW_ADJOINT", "HW_PACKED", "FORM_A2", "FORM_A", "METHOD_FOM", "METHOD_GMRES", "sign_apply", "SignApply"]
 
 
 def kenney_laub(s: int, c: float = 1.0):
@@ -116,6 +116,10 @@ class SignContext:
     def set_formulation(self, form=FORM_A2):
         """FORM_A2: s systems in K(A^2) (eq. 6.2 as written); FORM_A: 2s systems in K(A)."""
         check(lib().sgn_set_formulation(self._h, int(form)))
+
+    def set_method(self, method=METHOD_FOM):
+        """METHOD_FOM: FOM-LR (Algorithm 1); METHOD_GMRES: GMRES-LR (restarted multishift GMRES)."""
+        check(lib().sgn_set_method(self._h, int(method)))
 
     def set_refinement(self, k_refine=0, max_batch=0):
         """Mixed form: restart length and batch size of the correction solves (0: defaults)."""
@@ -254,6 +258,37 @@ class SignContext:
         check(lib().sgn_hw_apply(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()), nrhs,
                                  int(precision), flags))
         return out
+
+    def overlap(self, b):
+        """D_ov b = b + gamma5 sign(H_W(mu)) b for CUDA fields of shape (nrhs, n) or (n,)."""
+        torch = _torch()
+        x = b.to(torch.complex128).contiguous()
+        out = torch.empty_like(x)
+        check(lib().sgn_overlap_apply(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()),
+                                      x.numel() // self.n))
+        return out
+
+    def overlap_solve(self, b, tol=1e-8, k=30, max_restarts=50):
+        """x = D_ov^{-1} b by restarted GMRES; returns (x, applications of D_ov, relative residual)."""
+        torch = _torch()
+        x = b.to(torch.complex128).contiguous()
+        out = torch.empty_like(x)
+        its, rr = C.c_int(0), C.c_double(0)
+        check(lib().sgn_overlap_solve(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()),
+                                      x.numel() // self.n, float(tol), int(k), int(max_restarts), C.byref(its),
+                                      C.byref(rr)))
+        return out, its.value, rr.value
+
+    def apply_direct(self, b, k, adjoint=False):
+        """Direct projection of eq. (6.3): x_P + ||r|| V_k sign(H_k) e_1 with k Arnoldi steps on A
+        (no rational function, no restarts).  Returns (x, Krylov dimension used)."""
+        torch = _torch()
+        x = b.to(torch.complex128).contiguous()
+        out = torch.empty_like(x)
+        ku = C.c_int(0)
+        check(lib().sgn_apply_direct(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()),
+                                     x.numel() // self.n, int(k), APPLY_ADJOINT if adjoint else 0, C.byref(ku)))
+        return out, ku.value
 
     def _layout(self, fn, psi, precision):
         torch = _torch()

@@ -16,6 +16,7 @@ LINKS_FP32, LINKS_BF16 = 0, 1
 APPLY_HOST_BUFFERS, APPLY_ADJOINT, APPLY_NO_A = 1, 2, 4
 HW_ADJOINT, HW_PACKED = 1, 2
 FORM_A2, FORM_A = 0, 1
+METHOD_FOM, METHOD_GMRES = 0, 1
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
@@ -47,6 +48,7 @@ SIGNATURES = {
     "sgn_set_precision": (C.c_int, [P, C.c_int, C.c_double, C.c_int]),
     "sgn_set_refinement": (C.c_int, [P, C.c_int, C.c_int]),
     "sgn_set_formulation": (C.c_int, [P, C.c_int]),
+    "sgn_set_method": (C.c_int, [P, C.c_int]),
     "sgn_set_deflation": (C.c_int, [P, C.c_int, P, P, P, C.c_int]),
     "sgn_set_deflation_extra": (C.c_int, [P, C.c_int, P, P, P, C.c_int]),
     "sgn_build_deflation": (C.c_int, [P, C.c_int, C.c_int, C.c_double, P]),
@@ -54,6 +56,10 @@ SIGNATURES = {
     "sgn_apply": (C.c_int, [P, P, P, C.c_int, C.c_int, C.POINTER(Report)]),
     "sgn_apply_shifts": (C.c_int, [P, P, P, P, C.c_int, C.c_int, C.POINTER(Report)]),
     "sgn_hw_apply": (C.c_int, [P, P, P, C.c_int, C.c_int, C.c_int]),
+    "sgn_apply_direct": (C.c_int, [P, P, P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)]),
+    "sgn_overlap_apply": (C.c_int, [P, P, P, C.c_int]),
+    "sgn_overlap_solve": (C.c_int, [P, P, P, C.c_int, C.c_double, C.c_int, C.c_int, C.POINTER(C.c_int),
+                                    C.POINTER(C.c_double)]),
     "sgn_pack_fields": (C.c_int, [P, P, P, C.c_int, C.c_int]),
     "sgn_unpack_fields": (C.c_int, [P, P, P, C.c_int, C.c_int]),
     "sgn_inner_products": (C.c_int, [P, P, C.c_int, P, C.c_int, P]),

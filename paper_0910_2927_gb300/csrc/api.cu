@@ -248,6 +248,13 @@ SGN_API int sgn_set_formulation(sgn_ctx* c, int form) {
     return SGN_OK;
 }
 
+SGN_API int sgn_set_method(sgn_ctx* c, int method) {
+    if (!c || (method != SGN_METHOD_FOM && method != SGN_METHOD_GMRES))
+        return fail(SGN_ERR_ARG, "sgn_set_method: bad argument");
+    c->method = method;
+    return SGN_OK;
+}
+
 SGN_API int sgn_set_refinement(sgn_ctx* c, int k_refine, int max_batch) {
     if (!c || k_refine < 0 || k_refine > 64 || max_batch < 0 || max_batch > 4096)
         return fail(SGN_ERR_ARG, "sgn_set_refinement: need 0 <= k_refine <= 64, 0 <= max_batch <= 4096");
@@ -471,6 +478,55 @@ SGN_API int sgn_hw_apply(sgn_ctx* c, const void* in, void* out, int nrhs, int pr
     }
     SGN_CHECK(leave(c));
     return SGN_OK;
+}
+
+SGN_API int sgn_overlap_apply(sgn_ctx* c, const double* b, double* y, int nrhs) {
+    if (!c || !b || !y || nrhs < 1 || b == y) return fail(SGN_ERR_ARG, "sgn_overlap_apply: bad argument");
+    if (!c->have_gauge || c->sigma.empty()) return fail(SGN_ERR_STATE, "sgn_overlap_apply: gauge field and rational function needed");
+    SGN_CHECK(enter(c));
+    const size_t nn = (size_t)c->n * nrhs;
+    SGN_CHECK(dev_alloc(c, c->stage, 2 * nn * sizeof(double2)));
+    double2* t = as<double2>(c->stage);
+    SGN_CUDA(pack_fields<double2>(reinterpret_cast<const double2*>(b), t, c->vol, nrhs, c->work));
+    int st = overlap_apply(c, t, t + nn, nrhs, nullptr);
+    if (st == SGN_OK) SGN_CUDA(unpack_fields<double2>(t + nn, reinterpret_cast<double2*>(y), c->vol, nrhs, c->work));
+    SGN_CHECK(leave(c));
+    return st;
+}
+
+SGN_API int sgn_overlap_solve(sgn_ctx* c, const double* b, double* x, int nrhs, double tol, int k, int max_restarts,
+                              int* iterations, double* relres) {
+    if (!c || !b || !x || nrhs < 1 || b == x || !(tol > 0) || k < 1 || k > 64 || max_restarts < 0)
+        return fail(SGN_ERR_ARG, "sgn_overlap_solve: need tol > 0, 1 <= k <= 64, max_restarts >= 0");
+    if (!c->have_gauge || c->sigma.empty()) return fail(SGN_ERR_STATE, "sgn_overlap_solve: gauge field and rational function needed");
+    SGN_CHECK(enter(c));
+    const size_t nn = (size_t)c->n * nrhs;
+    SGN_CHECK(dev_alloc(c, c->stage, 2 * nn * sizeof(double2)));
+    double2* t = as<double2>(c->stage);
+    SGN_CUDA(pack_fields<double2>(reinterpret_cast<const double2*>(b), t, c->vol, nrhs, c->work));
+    SGN_CUDA(cudaMemsetAsync(t + nn, 0, nn * sizeof(double2), c->work));  // initial guess 0
+    int st = overlap_solve(c, t, t + nn, nrhs, tol, k, max_restarts, iterations, relres);
+    if (st == SGN_OK || st == SGN_ERR_NOT_CONVERGED)
+        SGN_CUDA(unpack_fields<double2>(t + nn, reinterpret_cast<double2*>(x), c->vol, nrhs, c->work));
+    SGN_CHECK(leave(c));
+    return st;
+}
+
+SGN_API int sgn_apply_direct(sgn_ctx* c, const double* b, double* x, int nrhs, int k, int flags, int* k_used) {
+    if (!c || !b || !x || nrhs < 1 || b == x || k < 1 || k > 4096)
+        return fail(SGN_ERR_ARG, "sgn_apply_direct: need b != x, nrhs >= 1, 1 <= k <= 4096");
+    if (flags & ~SGN_APPLY_ADJOINT) return fail(SGN_ERR_ARG, "sgn_apply_direct: unknown flag");
+    if (!c->have_gauge) return fail(SGN_ERR_STATE, "sgn_apply_direct: load the gauge field first");
+    SGN_CHECK(enter(c));
+    const size_t nn = (size_t)c->n * nrhs;
+    SGN_CHECK(dev_alloc(c, c->stage, 2 * nn * sizeof(double2)));
+    double2* t = as<double2>(c->stage);
+    SGN_CUDA(pack_fields<double2>(reinterpret_cast<const double2*>(b), t, c->vol, nrhs, c->work));
+    SGN_CHECK(tune_stencil(c, 0, nrhs, t, t + nn));
+    int st = direct_projection(c, t, t + nn, nrhs, k, (flags & SGN_APPLY_ADJOINT) != 0, k_used);
+    if (st == SGN_OK) SGN_CUDA(unpack_fields<double2>(t + nn, reinterpret_cast<double2*>(x), c->vol, nrhs, c->work));
+    SGN_CHECK(leave(c));
+    return st;
 }
 
 SGN_API int sgn_pack_fields(sgn_ctx* c, const void* in, void* out, int nfield, int precision) {

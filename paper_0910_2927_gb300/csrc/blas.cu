@@ -1186,6 +1186,19 @@ __global__ void k_correct_residuals(double2* __restrict__ r, const long long* __
     }
 }
 
+// y_f = a_f + beta gamma5 s_f for nfield packed complex128 fields of vol sites: gamma5 =
+// diag(1, 1, -1, -1) in spin negates spins 2 and 3, i.e. planes 3..5 of the packed
+// field, its second half.
+__global__ void k_gamma5_axpy(double2* __restrict__ y, const double2* __restrict__ a, const double2* __restrict__ sv,
+                              double beta, int64_t half, int64_t total) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = i % (2 * half);
+        const double g = e < half ? beta : -beta;
+        const double2 av = a[i], v = sv[i];
+        y[i] = make_double2(av.x + g * v.x, av.y + g * v.y);
+    }
+}
+
 inline unsigned grid_for(int64_t count) {
     int64_t g = (count + 255) / 256;
     if (g > 152 * 16) g = 152 * 16;
@@ -1372,6 +1385,15 @@ template cudaError_t dcgs_update<double2>(Basis<double2>, int, const double2*, i
                                           double2*, int64_t, int64_t, int, const int*, cudaStream_t);
 template cudaError_t dcgs_update<float2>(Basis<float2>, int, const double2*, int, float2*, const float2*, float2*,
                                          int64_t, int64_t, int, const int*, cudaStream_t);
+
+cudaError_t gamma5_axpy(double2* y, const double2* a, const double2* s, double beta, int64_t vol, int nfield,
+                        cudaStream_t st) {
+    const int64_t total = (int64_t)nfield * 12 * vol;
+    if (total <= 0) return cudaSuccess;
+    k_gamma5_axpy<<<grid_for(total), NT, 0, st>>>(y, a, s, beta, 6 * vol, total);
+    count_launch();
+    return cudaGetLastError();
+}
 
 cudaError_t correct_residuals(double2* r, const long long* roff, const double* sig, const float2* w,
                               const double2* d, int64_t n, int nb, cudaStream_t st) {

@@ -102,6 +102,10 @@ cudaError_t shifted_solves(const DevState& S, int ncol, cudaStream_t st);
 cudaError_t shifted_lsq(const DevState& S, int ncol, cudaStream_t st);
 cudaError_t combine_shifts(const DevState& S, int ncol, cudaStream_t st);
 
+// y = a + beta gamma5 s for nfield packed complex128 fields (gamma5: spins 2, 3 negated).
+cudaError_t gamma5_axpy(double2* y, const double2* a, const double2* s, double beta, int64_t vol, int nfield,
+                        cudaStream_t st);
+
 // Refinement residual update r_j += sigma_j d_j - w_j (w_j = A^2 d_j in FP32) for nb
 // systems: r_j at r + roff[j], w_j and d_j at j * n.
 cudaError_t correct_residuals(double2* r, const long long* roff, const double* sig, const float2* w,

@@ -87,6 +87,7 @@ struct sgn_ctx {
     double target = 1e-8;
     int link_storage = SGN_LINKS_FP32;
     int form = SGN_FORM_A2;  // Krylov space of the partial fractions (sgn_formulation)
+    int method = SGN_METHOD_FOM;  // multishift FOM-LR or GMRES-LR (sgn_method)
     int k_refine = 0;    // restart length of the mixed form's correction solves (0: min(k, 16))
     int refine_batch = 0;  // shifted systems per correction batch (0: min(s nrhs, 4 nrhs), memory-bounded)
 
@@ -138,7 +139,14 @@ int solve(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int ncol, 
 int tune_stencil(sgn_ctx* c, int prec, int ncol, void* in, void* out);
 // Dot products <a_c, b_c> of ncol pairs of FP64 fields (host result, FP64 reductions).
 int field_dots(sgn_ctx* c, const double2* a, const double2* b, int ncol, std::vector<std::complex<double>>& out);
+// overlap operator D_ov = 1 + gamma5 F(A) (overlap.cu), packed fields
+int overlap_apply(sgn_ctx* c, const double2* b, double2* y, int ncol, sgn_report* rep);
+int overlap_solve(sgn_ctx* c, const double2* b, double2* x, int ncol, double tol, int k, int max_restarts,
+                  int* iterations, double* relres);
 // (A^2 - shift_col)^{-1} (I - Rp Lp^dag) rhs_col, one complex shift per column, restarted GMRES (FP64)
+// x = x_P + ||r|| V_k sign(H_k) e_1 (eq. (6.3)) on packed FP64 fields; *kk_out = the
+// largest Krylov dimension used (smaller than k only at a breakdown)
+int direct_projection(sgn_ctx* c, const double2* b, double2* x, int ncol, int k, bool adjoint, int* kk_out);
 int solve_columns_gmres(sgn_ctx* c, const double2* rhs, int ncol, const std::vector<std::complex<double>>& shift,
                         bool adjoint, double2* out, const double2* Rp, const double2* Lp, int mp);
 int build_deflation(sgn_ctx* c, int m, int extra, double eig_tol, double* lambda_out);

@@ -129,9 +129,9 @@ int tune_stencil(sgn_ctx* c, int prec, int ncol, void* in, void* out) {
     cudaStream_t st = c->work;
     const StencilParams p = stencil_params(c, false);
     std::vector<StencilShape> cands;
-    for (int pipe = 0; pipe <= (prec == 0 ? 0 : 1); ++pipe)
+    for (int pipe = 0; pipe <= (prec == 0 ? 0 : 2); ++pipe)
         for (int nr : {1, 2, 3}) {
-            if (nr > ncol || (prec == 0 && nr > 1) || (pipe && nr > 2)) continue;
+            if (nr > ncol || (prec == 0 && nr > 1) || (pipe == 1 && nr > 2) || (pipe == 2 && nr != 2)) continue;
             const int groups = (ncol + nr - 1) / nr;
             const int maxt = nr == 1 && !pipe ? 384 : 256;
             for (int rb : {1, 2, 3, 4, 6, 8, 12, 16}) {
@@ -611,6 +611,15 @@ int run_engine(sgn_ctx* c, Engine& E, const CycleArgs& a, double tol, int max_cy
     }
     int cyc = 0;
     bool all_done = false;
+    // kernel timing: the bytes of a cycle count only the columns still active in it
+    // (converged columns skip their work in every kernel)
+    int active = ncol;
+    if (c->timing) {
+        SGN_CUDA(cudaMemcpyAsync(E.h_done, E.S.done, ncol * sizeof(int), cudaMemcpyDeviceToHost, st));
+        SGN_CUDA(cudaStreamSynchronize(st));
+        active = 0;
+        for (int i = 0; i < ncol; ++i) active += E.h_done[i] == 0;
+    }
     for (; cyc < max_cycles; ++cyc) {
         if (E.graph) {
             SGN_CUDA(cudaGraphLaunch(E.graph, st));
@@ -629,8 +638,12 @@ int run_engine(sgn_ctx* c, Engine& E, const CycleArgs& a, double tol, int max_cy
                 const int cls = E.tmarks[i].first;
                 c->t_ms[cls] += ms;
                 c->t_launches[cls] += 1;
-                c->t_bytes[cls] += E.tmarks[i].second;
+                c->t_bytes[cls] += E.tmarks[i].second * active / ncol;
             }
+        if (c->timing) {
+            active = 0;
+            for (int i = 0; i < ncol; ++i) active += E.h_done[i] == 0;
+        }
         if (debug_log() && (cyc < 30 || cyc % 50 == 0)) {
             SGN_CUDA(cudaMemcpy(E.h_resest, E.S.resest, ncol * sizeof(double), cudaMemcpyDeviceToHost));
             double mx = 0;
@@ -1016,6 +1029,20 @@ int solve(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int ncol, 
         return SGN_ERR_STATE;
     }
     if (split) no_a = true;
+    // GMRES-LR: restarted multishift GMRES; the seed (minimal residual) is the shift of
+    // smallest modulus, the slowest to converge, moved to position 0
+    const bool gm = !cshift && c->method == SGN_METHOD_GMRES;
+    if (gm && (split || c->precision == SGN_PREC_MIXED)) {
+        set_error("solve: GMRES-LR runs in the FP64 form of the A^2 formulation");
+        return SGN_ERR_STATE;
+    }
+    int seed = 0;
+    if (gm) {
+        for (int i = 1; i < (int)sh.size(); ++i)
+            if (std::abs(sh[i]) < std::abs(sh[seed])) seed = i;
+        std::swap(sh[0], sh[seed]);
+        std::swap(wt[0], wt[seed]);
+    }
     if (c->precision == SGN_PREC_MIXED && !cshift) return solve_mixed(c, b, x, x_shift, ncol, adjoint, no_a, rep);
     if (s < 1) {
         set_error("solve: no shifts");
@@ -1080,11 +1107,20 @@ int solve(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int ncol, 
     a.xs_shift = (int64_t)ncol * n;
     a.xs_col = n;
     a.op_a = split;
+    a.gmres = gm;
     RunResult rr;
     int status = run_engine<double2>(c, *E, a, c->tol, c->max_cycles, &rr);
     if (status == SGN_OK) {
         SGN_CUDA(cudaMemcpyAsync(x, xacc, field * ncol, cudaMemcpyDeviceToDevice, st));
-        if (x_shift) SGN_CUDA(cudaMemcpyAsync(x_shift, xs, field * ncol * s, cudaMemcpyDeviceToDevice, st));
+        if (x_shift && seed == 0) SGN_CUDA(cudaMemcpyAsync(x_shift, xs, field * ncol * s, cudaMemcpyDeviceToDevice, st));
+        if (x_shift && seed != 0) {  // undo the seed's move: engine slots 0 and seed trade places
+            const size_t blk = field * ncol;
+            char* dst = reinterpret_cast<char*>(x_shift);
+            const char* src = reinterpret_cast<const char*>(xs);
+            SGN_CUDA(cudaMemcpyAsync(dst, src, blk * s, cudaMemcpyDeviceToDevice, st));
+            SGN_CUDA(cudaMemcpyAsync(dst, src + blk * seed, blk, cudaMemcpyDeviceToDevice, st));
+            SGN_CUDA(cudaMemcpyAsync(dst + blk * seed, src, blk, cudaMemcpyDeviceToDevice, st));
+        }
         if (!rr.converged) {
             status = SGN_ERR_NOT_CONVERGED;
             set_error("max_cycles reached before every shifted system met the tolerance");

@@ -342,6 +342,192 @@ __global__ void __launch_bounds__(NR == 1 ? 384 : 256)
     }
 }
 
+// ---- paired FP32 form --------------------------------------------------------
+// Two fields per thread with their arithmetic paired: every real quantity is a
+// float2 (field 0, field 1), so one packed FP32 instruction (FFMA2 on sm_100 and
+// later) does the work of two.  The link entries are the same for both fields,
+// so each complex multiply-add of the link products and the reconstruction is two
+// paired FMAs instead of four scalar ones.  The spin projection stays scalar per
+// field (its results land in the halves of the pairs).
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+template <class LinkT, int NU, int S>
+__device__ __forceinline__ void hop_x2(float2 (&ar)[12], float2 (&ai)[12], const float2* __restrict__ in,
+                                       int64_t stride_rhs, const bool (&act)[2], const LinkT* __restrict__ U,
+                                       int64_t link_site, int64_t nb, float coef, int64_t vol) {
+    float2 hr0[3], hi0[3], hr1[3], hi1[3];  // the two projected colour vectors, paired over fields
+    {
+        Cx<float> pa[12], pb[12], ha0[3], ha1[3], hb0[3], hb1[3];
+        if (act[0]) {
+            Field<float>::load(in, nb, 2 * vol, pa);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) pa[k] = {0.f, 0.f};
+        }
+        if (act[1]) {
+            Field<float>::load(in + stride_rhs, nb, 2 * vol, pb);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) pb[k] = {0.f, 0.f};
+        }
+        project<float, NU, S>(pa, ha0, ha1);
+        project<float, NU, S>(pb, hb0, hb1);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            hr0[c] = f2(ha0[c].x, hb0[c].x);
+            hi0[c] = f2(ha0[c].y, hb0[c].y);
+            hr1[c] = f2(ha1[c].x, hb1[c].x);
+            hi1[c] = f2(ha1[c].y, hb1[c].y);
+        }
+    }
+    const LinkT* lb = U + (int64_t)NU * 9 * vol + link_site;
+    const float2 cc = f2s(coef), cs = f2s(coef * float(S)), ncs = f2s(-coef * float(S));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float2 g0r = f2s(0.f), g0i = f2s(0.f), g1r = f2s(0.f), g1i = f2s(0.f);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const Cx<float> u = Link<float, LinkT>::ld(lb, (S < 0 ? a * 3 + b : b * 3 + a) * vol);
+            const float2 ux = f2s(u.x), uy = f2s(u.y), nuy = f2s(-u.y);
+            if constexpr (S < 0) {  // g += u h
+                g0r = pfma(ux, hr0[b], g0r);
+                g0r = pfma(nuy, hi0[b], g0r);
+                g0i = pfma(ux, hi0[b], g0i);
+                g0i = pfma(uy, hr0[b], g0i);
+                g1r = pfma(ux, hr1[b], g1r);
+                g1r = pfma(nuy, hi1[b], g1r);
+                g1i = pfma(ux, hi1[b], g1i);
+                g1i = pfma(uy, hr1[b], g1i);
+            } else {  // g += conj(u) h
+                g0r = pfma(ux, hr0[b], g0r);
+                g0r = pfma(uy, hi0[b], g0r);
+                g0i = pfma(ux, hi0[b], g0i);
+                g0i = pfma(nuy, hr0[b], g0i);
+                g1r = pfma(ux, hr1[b], g1r);
+                g1r = pfma(uy, hi1[b], g1r);
+                g1i = pfma(ux, hi1[b], g1i);
+                g1i = pfma(nuy, hr1[b], g1i);
+            }
+        }
+        ar[a] = pfma(cc, g0r, ar[a]);
+        ai[a] = pfma(cc, g0i, ai[a]);
+        ar[3 + a] = pfma(cc, g1r, ar[3 + a]);
+        ai[3 + a] = pfma(cc, g1i, ai[3 + a]);
+        if constexpr (NU == 0) {  // lower = (i g1, i g0) cs
+            ar[6 + a] = pfma(ncs, g1i, ar[6 + a]);
+            ai[6 + a] = pfma(cs, g1r, ai[6 + a]);
+            ar[9 + a] = pfma(ncs, g0i, ar[9 + a]);
+            ai[9 + a] = pfma(cs, g0r, ai[9 + a]);
+        } else if constexpr (NU == 1) {  // (g1, -g0) cs
+            ar[6 + a] = pfma(cs, g1r, ar[6 + a]);
+            ai[6 + a] = pfma(cs, g1i, ai[6 + a]);
+            ar[9 + a] = pfma(ncs, g0r, ar[9 + a]);
+            ai[9 + a] = pfma(ncs, g0i, ai[9 + a]);
+        } else if constexpr (NU == 2) {  // (i g0, -i g1) cs
+            ar[6 + a] = pfma(ncs, g0i, ar[6 + a]);
+            ai[6 + a] = pfma(cs, g0r, ai[6 + a]);
+            ar[9 + a] = pfma(cs, g1i, ar[9 + a]);
+            ai[9 + a] = pfma(ncs, g1r, ai[9 + a]);
+        } else {  // (g0, g1) cs
+            ar[6 + a] = pfma(cs, g0r, ar[6 + a]);
+            ai[6 + a] = pfma(cs, g0i, ai[6 + a]);
+            ar[9 + a] = pfma(cs, g1r, ar[9 + a]);
+            ai[9 + a] = pfma(cs, g1i, ai[9 + a]);
+        }
+    }
+}
+
+template <class LinkT, int NU>
+__device__ __forceinline__ void both_hops_x2(float2 (&ar)[12], float2 (&ai)[12], const float2* __restrict__ in,
+                                             const bool (&act)[2], const LinkT* __restrict__ U, int64_t site,
+                                             const int co[4], const StencilParams& P) {
+    int64_t stride = 1;
+#pragma unroll
+    for (int d = 0; d < NU; ++d) stride *= P.L[d];
+    const int L = P.L[NU];
+    int64_t fw = site + stride;
+    float cf = P.cf32[NU];
+    if (co[NU] == L - 1) {
+        fw = site - (int64_t)(L - 1) * stride;
+        if (P.ap[NU]) cf = -cf;
+    }
+    int64_t bw = site - stride;
+    float cb = P.cb32[NU];
+    if (co[NU] == 0) {
+        bw = site + (int64_t)(L - 1) * stride;
+        if (P.ap[NU]) cb = -cb;
+    }
+    hop_x2<LinkT, NU, -1>(ar, ai, in, P.stride_rhs, act, U, site, fw, cf, P.vol);
+    hop_x2<LinkT, NU, +1>(ar, ai, in, P.stride_rhs, act, U, bw, bw, cb, P.vol);
+}
+
+// Grid and thread layout as k_hw with NR = 2.
+template <class LinkT, bool CS>
+__global__ void __launch_bounds__(256)
+    k_hw_x2(float2* __restrict__ out, const float2* __restrict__ in, const LinkT* __restrict__ U, int nrhs,
+            StencilParams P, const int* __restrict__ skip, int ngrp) {
+    const int64_t tile = blockIdx.x / (unsigned)ngrp;
+    const int grp = (int)(blockIdx.x - tile * ngrp);
+    const int64_t site = tile * blockDim.x + threadIdx.x;
+    const int rhs0 = (grp * blockDim.y + threadIdx.y) * 2;
+    if (site >= P.vol || rhs0 >= nrhs) return;
+    bool act[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) act[i] = rhs0 + i < nrhs && !(skip && skip[rhs0 + i]);
+    if (!act[0] && !act[1]) return;
+    const float2* fin = in + rhs0 * P.stride_rhs;
+    int co[4];
+    {
+        const uint32_t s0 = (uint32_t)site;
+        const uint32_t q0 = P.div[0].div(s0);
+        co[0] = (int)(s0 - q0 * (uint32_t)P.L[0]);
+        const uint32_t q1 = P.div[1].div(q0);
+        co[1] = (int)(q0 - q1 * (uint32_t)P.L[1]);
+        const uint32_t q2 = P.div[2].div(q1);
+        co[2] = (int)(q1 - q2 * (uint32_t)P.L[2]);
+        co[3] = (int)q2;
+    }
+    float2 ar[12], ai[12];
+    {
+        Cx<float> pa[12], pb[12];
+        if (act[0]) {
+            Field<float>::load(fin, site, 2 * P.vol, pa);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) pa[k] = {0.f, 0.f};
+        }
+        if (act[1]) {
+            Field<float>::load(fin + P.stride_rhs, site, 2 * P.vol, pb);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) pb[k] = {0.f, 0.f};
+        }
+        const float d = P.diag32;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            ar[k] = f2(d * pa[k].x, d * pb[k].x);
+            ai[k] = f2(d * pa[k].y, d * pb[k].y);
+        }
+    }
+    both_hops_x2<LinkT, 0>(ar, ai, fin, act, U, site, co, P);
+    both_hops_x2<LinkT, 1>(ar, ai, fin, act, U, site, co, P);
+    both_hops_x2<LinkT, 2>(ar, ai, fin, act, U, site, co, P);
+    both_hops_x2<LinkT, 3>(ar, ai, fin, act, U, site, co, P);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        if (!act[i]) continue;
+        Cx<float> o[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const float g5 = k < 6 ? 1.f : -1.f;  // gamma5 = diag(1, 1, -1, -1)
+            o[k] = {g5 * (i ? ar[k].y : ar[k].x), g5 * (i ? ai[k].y : ai[k].x)};
+        }
+        Field<float>::template store<CS>(out + (rhs0 + i) * P.stride_rhs, site, 2 * P.vol, o);
+    }
+}
+
 // ---- pipelined FP32 form ------------------------------------------------------
 // The same stencil with the neighbour spinors staged through shared memory:
 // each thread copies its own next stage (the site itself, then the 8 hops)
@@ -608,10 +794,35 @@ cudaError_t launch_pipe(float2* out, const float2* in, const LinkT* U, int nrhs,
     return cudaGetLastError();
 }
 
+template <class LinkT>
+cudaError_t launch_x2(float2* out, const float2* in, const LinkT* U, int nrhs, const StencilParams& p,
+                      const int* skip, cudaStream_t st, int sx, int rb) {
+    const int groups = (nrhs + 1) / 2;
+    const int ngrp = (groups + rb - 1) / rb;
+    const int64_t tiles = (p.vol + sx - 1) / sx;
+    if (tiles * ngrp > 0x7fffffffLL) return cudaErrorInvalidValue;
+    dim3 block(sx, rb);
+    const bool cs = (double)nrhs * (double)p.vol * 12.0 * sizeof(float2) > 256.0 * (1 << 20);
+    if (cs)
+        k_hw_x2<LinkT, true><<<(unsigned)(tiles * ngrp), block, 0, st>>>(out, in, U, nrhs, p, skip, ngrp);
+    else
+        k_hw_x2<LinkT, false><<<(unsigned)(tiles * ngrp), block, 0, st>>>(out, in, U, nrhs, p, skip, ngrp);
+    count_launch();
+    return cudaGetLastError();
+}
+
 template <class R, class LinkT>
 cudaError_t launch(typename Field<R>::T* out, const typename Field<R>::T* in, const LinkT* U, int nrhs,
                    const StencilParams& p, const int* skip, cudaStream_t st, StencilShape sh) {
     if (nrhs <= 0 || p.vol <= 0) return cudaSuccess;
+    if (sh.pipe == 2) {  // the paired FP32 kernel: two fields per thread, up to 256 threads per CTA
+        if constexpr (sizeof(R) == 4) {
+            if (sh.sx % 32 != 0 || sh.rb < 1 || sh.sx * sh.rb > 256 || sh.nr != 2) return cudaErrorInvalidValue;
+            return launch_x2<LinkT>(out, in, U, nrhs, p, skip, st, sh.sx, sh.rb);
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
     if (sh.pipe) {  // the pipelined FP32 kernel: 1 or 2 fields per thread, up to 256 threads per CTA
         if constexpr (sizeof(R) == 4) {
             if (sh.sx % 32 != 0 || sh.rb < 1 || sh.sx * sh.rb > 256 || sh.nr < 1 || sh.nr > 2)

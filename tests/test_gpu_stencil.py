@@ -104,10 +104,12 @@ def test_packed_layout_roundtrip_and_stencil():
 
 
 @pytest.mark.parametrize("shape", ["32,4,3", "64,2,2", "32,2,3", "64,3,1", "128,1,2",
-                                   "32,4,1,1", "64,2,2,1", "128,1,2,1", "256,1,1,1"])
+                                   "32,4,1,1", "64,2,2,1", "128,1,2,1", "256,1,1,1",
+                                   "32,4,2,2", "64,2,2,2", "128,1,2,2", "256,1,2,2"])
 def test_fp32_stencil_launch_shapes(shape, monkeypatch):
-    """Every launch shape (sites per CTA, thread rows, fields per thread, and the
-    kernel that stages neighbours through shared memory with cp.async) gives
+    """Every launch shape (sites per CTA, thread rows, fields per thread, the kernel
+    that stages neighbours through shared memory with cp.async, and the kernel with
+    paired FP32 arithmetic over two fields) gives
     the oracle's result, including field counts that leave the last thread's
     group of fields ragged (5 fields, 2 or 3 per thread)."""
     import paper_0910_2927_gb300 as pkg
@@ -126,10 +128,12 @@ def test_fp32_stencil_launch_shapes(shape, monkeypatch):
         assert np.linalg.norm(outa[r] - refa) / np.linalg.norm(refa) < 2e-6
 
 
-def test_invalid_launch_shape_is_an_error(monkeypatch):
-    """A shape outside the kernel's limits is refused with an error, not launched."""
+@pytest.mark.parametrize("shape", ["32,12,3", "64,2,1,2", "128,4,2,2"])
+def test_invalid_launch_shape_is_an_error(shape, monkeypatch):
+    """A shape outside the kernel's limits (384 threads with 3 fields each; the paired
+    kernel with one field per thread, or with 512 threads) is refused with an error."""
     import paper_0910_2927_gb300 as pkg
-    monkeypatch.setenv("SGN_STENCIL_SHAPE", "32,12,3")  # 384 threads with 3 fields each
+    monkeypatch.setenv("SGN_STENCIL_SHAPE", shape)
     dims = (4, 4, 4, 4)
     U = si.random_su3_links(dims, 0.7, 33)
     b = si.gaussian_block(dims, 12, 34)
@@ -139,7 +143,7 @@ def test_invalid_launch_shape_is_an_error(monkeypatch):
             ctx.hw(torch.from_numpy(b).cuda(), precision=pkg.PREC_MIXED)
 
 
-@pytest.mark.parametrize("shape", ["64,2,2,1", "32,4,1,1"])
+@pytest.mark.parametrize("shape", ["64,2,2,1", "32,4,1,1", "64,2,2,2"])
 def test_pipelined_stencil_bf16_links_and_many_fields(shape, monkeypatch):
     """The shared-memory staged kernel with BF16 links and 13 fields (several CTAs
     per site tile) matches the oracle within the BF16 rounding of the links."""
