@@ -884,25 +884,37 @@ __device__ void reduce_tail(const double2* sums, int col, int nslot, int mode, i
             const double2 alpha = sums[fin ? j : 2 * j];
             __shared__ double rho_sh;
             __shared__ int broke_sh;
-            if (threadIdx.x == 0) {
-                double s2 = 0;
-                for (int l = 0; l < j; ++l) s2 += cabs2(sums[l]);
-                double r2 = alpha.x - s2;
-                double rho = r2 > 0 ? sqrt(r2) : 0.0;
-                int broke = 0;
-                if (j == 0) {
-                    S.beta[col] = rho;
-                    broke = !(rho > 0);
-                } else {
-                    broke = !(rho > S.bd_tol * S.norm0[col]);
-                    H[(int64_t)j * km + (j - 1)] = make_double2(rho, 0);
+            __shared__ double2 st_sh;
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            if (warp == 0) {
+                // s2 = sum_l |s_l|^2 and st = sum_l conj(s_l) t_l, l < j: lanes over l, fixed-order tree
+                double2 s2v = make_double2(0, 0), st = make_double2(0, 0);
+                for (int l = lane; l < j; l += 32) {
+                    s2v.x += cabs2(sums[l]);
+                    if (!fin) st = cadd(st, cconjmul(sums[l], sums[j + l]));
                 }
-                if (!isfinite(r2)) {
-                    atomicOr(S.err, 2);
-                    broke = 1;
+                s2v = warp_sum(s2v);
+                st = warp_sum(st);
+                if (lane == 0) {
+                    st_sh = st;
+                    const double s2 = s2v.x;
+                    double r2 = alpha.x - s2;
+                    double rho = r2 > 0 ? sqrt(r2) : 0.0;
+                    int broke = 0;
+                    if (j == 0) {
+                        S.beta[col] = rho;
+                        broke = !(rho > 0);
+                    } else {
+                        broke = !(rho > S.bd_tol * S.norm0[col]);
+                        H[(int64_t)j * km + (j - 1)] = make_double2(rho, 0);
+                    }
+                    if (!isfinite(r2)) {
+                        atomicOr(S.err, 2);
+                        broke = 1;
+                    }
+                    rho_sh = rho;
+                    broke_sh = broke;
                 }
-                rho_sh = rho;
-                broke_sh = broke;
             }
             __syncthreads();
             // correct column j-1: H[0:j, j-1] += s
@@ -928,11 +940,33 @@ __device__ void reduce_tail(const double2* sums, int col, int nslot, int mode, i
                 break;
             }
             for (int l = threadIdx.x; l < j; l += NT) S.red[cr + l] = sums[l];  // s
-            // g = Hbar s, Hbar = H[0:j+1, 0:j]
-            for (int i = threadIdx.x; i <= j; i += NT) {
-                double2 g = make_double2(0, 0);
-                for (int l = (i > 0 ? i - 1 : 0); l < j; ++l) g = cadd(g, cmul(H[(int64_t)i * km + l], sums[l]));
-                gsh[i] = g;
+            // g = Hbar s, Hbar = H[0:j+1, 0:j]: warp w takes rows w, w + 8, ...; lanes split the
+            // row (l = lane, lane + 32); every H load of the warp is issued before the sums
+            if (j <= 64) {
+                constexpr int RPW = (65 + NWARP - 1) / NWARP;
+                double2 hv[RPW][2];
+#pragma unroll
+                for (int r = 0; r < RPW; ++r)
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const int i = warp + r * NWARP, l = lane + 32 * q;
+                        hv[r][q] = (i <= j && l < j && l >= i - 1) ? H[(int64_t)i * km + l] : make_double2(0, 0);
+                    }
+                const double2 s0 = lane < j ? sums[lane] : make_double2(0, 0);
+                const double2 s1 = lane + 32 < j ? sums[lane + 32] : make_double2(0, 0);
+#pragma unroll
+                for (int r = 0; r < RPW; ++r) {
+                    const int i = warp + r * NWARP;
+                    if (i > j) break;  // uniform over the warp
+                    const double2 g = warp_sum(cadd(cmul(hv[r][0], s0), cmul(hv[r][1], s1)));
+                    if (lane == 0) gsh[i] = g;
+                }
+            } else {
+                for (int i = threadIdx.x; i <= j; i += NT) {
+                    double2 g = make_double2(0, 0);
+                    for (int l = (i > 0 ? i - 1 : 0); l < j; ++l) g = cadd(g, cmul(H[(int64_t)i * km + l], sums[l]));
+                    gsh[i] = g;
+                }
             }
             __syncthreads();
             const double ir = 1.0 / rho;
@@ -943,8 +977,7 @@ __device__ void reduce_tail(const double2* sums, int col, int nslot, int mode, i
                 S.red[cr + j + i] = make_double2(gsh[i].x * ir + hp.x, gsh[i].y * ir + hp.y);  // c
             }
             if (threadIdx.x == 0) {
-                double2 st = make_double2(0, 0);
-                for (int l = 0; l < j; ++l) st = cadd(st, cconjmul(sums[l], sums[j + l]));
+                const double2 st = st_sh;
                 double2 beta = sums[2 * j + 1];
                 double2 hjj = make_double2(((beta.x - st.x) * ir - gsh[j].x) * ir, ((beta.y - st.y) * ir - gsh[j].y) * ir);
                 H[(int64_t)j * km + j] = hjj;
