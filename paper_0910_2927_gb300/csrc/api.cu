@@ -39,6 +39,22 @@ int leave(sgn_ctx* c) {
     return SGN_OK;
 }
 
+// One entry point's use of the work stream: close() orders the caller's stream after
+// the work queued so far; an early error return does the same from the destructor, so
+// the caller never runs ahead of kernels that still use its buffers.
+struct Session {
+    sgn_ctx* c;
+    bool open = true;
+    explicit Session(sgn_ctx* ctx) : c(ctx) {}
+    ~Session() {
+        if (open) leave(c);
+    }
+    int close() {
+        open = false;
+        return leave(c);
+    }
+};
+
 int drop_deflation(sgn_ctx* c) {
     c->m = 0;
     c->lam.clear();
@@ -155,6 +171,7 @@ SGN_API int sgn_load_gauge(sgn_ctx* c, const double* links, int on_device) {
     if (!on_device && !finite_host(links, 2 * count))
         return fail(SGN_ERR_NONFINITE, "sgn_load_gauge: non-finite link entry");
     SGN_CHECK(enter(c));
+    Session ses(c);
     SGN_CHECK(dev_alloc(c, c->U64, count * sizeof(double2)));
     SGN_CHECK(dev_alloc(c, c->U32, count * sizeof(float2)));
     SGN_CHECK(dev_alloc(c, c->U16, count * sizeof(__nv_bfloat162)));
@@ -168,7 +185,7 @@ SGN_API int sgn_load_gauge(sgn_ctx* c, const double* links, int on_device) {
     SGN_CUDA(convert_f64_to_f32(as<double2>(c->U64), as<float2>(c->U32), (int64_t)count, c->work));
     SGN_CUDA(links_f64_to_bf16(as<double2>(c->U64), as<__nv_bfloat162>(c->U16), (int64_t)count, c->work));
     SGN_CUDA(cudaStreamSynchronize(c->work));
-    SGN_CHECK(leave(c));
+    SGN_CHECK(ses.close());
     c->have_gauge = true;
     drop_deflation(c);
     return SGN_OK;
@@ -282,6 +299,7 @@ SGN_API int sgn_set_deflation(sgn_ctx* c, int m, const double* R, const double* 
         if (lam[2 * j] == 0.0)
             return fail(SGN_ERR_DEFLATION, "sgn_set_deflation: an eigenvalue on the imaginary axis has no sign");
     SGN_CHECK(enter(c));
+    Session ses(c);
     SGN_CHECK(dev_alloc(c, c->R64, cnt * sizeof(double2)));
     SGN_CHECK(dev_alloc(c, c->L64, cnt * sizeof(double2)));
     SGN_CHECK(dev_alloc(c, c->R32, cnt * sizeof(float2)));
@@ -297,7 +315,7 @@ SGN_API int sgn_set_deflation(sgn_ctx* c, int m, const double* R, const double* 
     SGN_CUDA(cudaMemcpyAsync(c->lam_dev.p, lam.data(), sizeof(double) * 2 * m, cudaMemcpyHostToDevice, c->work));
     SGN_CUDA(cudaMemcpyAsync(c->lamc_dev.p, lamc.data(), sizeof(double) * 2 * m, cudaMemcpyHostToDevice, c->work));
     SGN_CUDA(cudaStreamSynchronize(c->work));
-    SGN_CHECK(leave(c));
+    SGN_CHECK(ses.close());
     c->lam.resize(m);
     for (int j = 0; j < m; ++j) c->lam[j] = {lam[2 * j], lam[2 * j + 1]};
     c->m = m;
@@ -324,12 +342,13 @@ SGN_API int sgn_set_deflation_extra(sgn_ctx* c, int e, const double* R, const do
     }
     if (!finite_host(lam.data(), 2 * (size_t)e)) return fail(SGN_ERR_NONFINITE, "sgn_set_deflation_extra: bad lambda");
     SGN_CHECK(enter(c));
+    Session ses(c);
     SGN_CHECK(dev_alloc(c, c->Rx64, cnt * sizeof(double2)));
     SGN_CHECK(dev_alloc(c, c->Lx64, cnt * sizeof(double2)));
     SGN_CHECK(fields_in(c, as<double2>(c->Rx64), R, e, on_device));
     SGN_CHECK(fields_in(c, as<double2>(c->Lx64), L, e, on_device));
     SGN_CUDA(cudaStreamSynchronize(c->work));
-    SGN_CHECK(leave(c));
+    SGN_CHECK(ses.close());
     c->lamx.resize(e);
     for (int j = 0; j < e; ++j) c->lamx[j] = {lam[2 * j], lam[2 * j + 1]};
     c->mx = e;
@@ -342,6 +361,7 @@ SGN_API int sgn_get_deflation(sgn_ctx* c, int* m, double* R, double* L, double* 
     if (c->m == 0) return SGN_OK;
     const size_t cnt = (size_t)c->n * c->m;
     SGN_CHECK(enter(c));
+    Session ses(c);
     SGN_CHECK(dev_alloc(c, c->stage, cnt * sizeof(double2)));
     for (int side = 0; side < 2; ++side) {
         double* dst = side == 0 ? R : L;
@@ -351,7 +371,7 @@ SGN_API int sgn_get_deflation(sgn_ctx* c, int* m, double* R, double* L, double* 
         SGN_CUDA(cudaMemcpyAsync(dst, c->stage.p, cnt * sizeof(double2), cudaMemcpyDeviceToHost, c->work));
         SGN_CUDA(cudaStreamSynchronize(c->work));
     }
-    SGN_CHECK(leave(c));
+    SGN_CHECK(ses.close());
     if (lambda)
         for (int j = 0; j < c->m; ++j) {
             lambda[2 * j] = c->lam[j].real();
@@ -365,8 +385,9 @@ SGN_API int sgn_build_deflation(sgn_ctx* c, int m, int extra, double eig_tol, do
         return fail(SGN_ERR_ARG, "sgn_build_deflation: need 1 <= m, m + extra <= 64, eig_tol > 0");
     if (!c->have_gauge) return fail(SGN_ERR_STATE, "sgn_build_deflation: load the gauge field first");
     SGN_CHECK(enter(c));
+    Session ses(c);
     int st = build_deflation(c, m, extra, eig_tol, lambda_out);
-    SGN_CHECK(leave(c));
+    SGN_CHECK(ses.close());
     return st;
 }
 
@@ -384,6 +405,7 @@ int apply_common(sgn_ctx* c, const double* b, double* x, double* x_shift, int nr
     if (host && !finite_host(b, 2 * (size_t)c->n * nrhs))
         return fail(SGN_ERR_NONFINITE, "sgn_apply: non-finite entry in b");
     SGN_CHECK(enter(c));
+    Session ses(c);
     const long long launches0 = g_launches;
     SGN_CUDA(cudaEventRecord(c->ev_t0, c->work));
     // staging: [b packed][x packed][x_shift packed]
@@ -420,7 +442,7 @@ int apply_common(sgn_ctx* c, const double* b, double* x, double* x_shift, int nr
         rep->ms = ms;
         rep->kernels = g_launches - launches0;
     }
-    SGN_CHECK(leave(c));
+    SGN_CHECK(ses.close());
     return status;
 }
 
@@ -446,6 +468,7 @@ SGN_API int sgn_hw_apply(sgn_ctx* c, const void* in, void* out, int nrhs, int pr
     const bool adjoint = flags & SGN_HW_ADJOINT;
     const bool packed = flags & SGN_HW_PACKED;
     SGN_CHECK(enter(c));
+    Session ses(c);
     const size_t nn = (size_t)c->n * nrhs;
     if (precision == SGN_PREC_FP64) {
         const double2* pi = reinterpret_cast<const double2*>(in);
@@ -476,7 +499,7 @@ SGN_API int sgn_hw_apply(sgn_ctx* c, const void* in, void* out, int nrhs, int pr
         if (!packed)
             SGN_CUDA(unpack_fields<float2>(po, reinterpret_cast<float2*>(out), c->vol, nrhs, c->work));
     }
-    SGN_CHECK(leave(c));
+    SGN_CHECK(ses.close());
     return SGN_OK;
 }
 
@@ -484,13 +507,14 @@ SGN_API int sgn_overlap_apply(sgn_ctx* c, const double* b, double* y, int nrhs) 
     if (!c || !b || !y || nrhs < 1 || b == y) return fail(SGN_ERR_ARG, "sgn_overlap_apply: bad argument");
     if (!c->have_gauge || c->sigma.empty()) return fail(SGN_ERR_STATE, "sgn_overlap_apply: gauge field and rational function needed");
     SGN_CHECK(enter(c));
+    Session ses(c);
     const size_t nn = (size_t)c->n * nrhs;
     SGN_CHECK(dev_alloc(c, c->stage, 2 * nn * sizeof(double2)));
     double2* t = as<double2>(c->stage);
     SGN_CUDA(pack_fields<double2>(reinterpret_cast<const double2*>(b), t, c->vol, nrhs, c->work));
     int st = overlap_apply(c, t, t + nn, nrhs, nullptr);
     if (st == SGN_OK) SGN_CUDA(unpack_fields<double2>(t + nn, reinterpret_cast<double2*>(y), c->vol, nrhs, c->work));
-    SGN_CHECK(leave(c));
+    SGN_CHECK(ses.close());
     return st;
 }
 
@@ -500,6 +524,7 @@ SGN_API int sgn_overlap_solve(sgn_ctx* c, const double* b, double* x, int nrhs, 
         return fail(SGN_ERR_ARG, "sgn_overlap_solve: need tol > 0, 1 <= k <= 64, max_restarts >= 0");
     if (!c->have_gauge || c->sigma.empty()) return fail(SGN_ERR_STATE, "sgn_overlap_solve: gauge field and rational function needed");
     SGN_CHECK(enter(c));
+    Session ses(c);
     const size_t nn = (size_t)c->n * nrhs;
     SGN_CHECK(dev_alloc(c, c->stage, 2 * nn * sizeof(double2)));
     double2* t = as<double2>(c->stage);
@@ -508,7 +533,7 @@ SGN_API int sgn_overlap_solve(sgn_ctx* c, const double* b, double* x, int nrhs, 
     int st = overlap_solve(c, t, t + nn, nrhs, tol, k, max_restarts, iterations, relres);
     if (st == SGN_OK || st == SGN_ERR_NOT_CONVERGED)
         SGN_CUDA(unpack_fields<double2>(t + nn, reinterpret_cast<double2*>(x), c->vol, nrhs, c->work));
-    SGN_CHECK(leave(c));
+    SGN_CHECK(ses.close());
     return st;
 }
 
@@ -518,6 +543,7 @@ SGN_API int sgn_apply_direct(sgn_ctx* c, const double* b, double* x, int nrhs, i
     if (flags & ~SGN_APPLY_ADJOINT) return fail(SGN_ERR_ARG, "sgn_apply_direct: unknown flag");
     if (!c->have_gauge) return fail(SGN_ERR_STATE, "sgn_apply_direct: load the gauge field first");
     SGN_CHECK(enter(c));
+    Session ses(c);
     const size_t nn = (size_t)c->n * nrhs;
     SGN_CHECK(dev_alloc(c, c->stage, 2 * nn * sizeof(double2)));
     double2* t = as<double2>(c->stage);
@@ -525,7 +551,7 @@ SGN_API int sgn_apply_direct(sgn_ctx* c, const double* b, double* x, int nrhs, i
     SGN_CHECK(tune_stencil(c, 0, nrhs, t, t + nn));
     int st = direct_projection(c, t, t + nn, nrhs, k, (flags & SGN_APPLY_ADJOINT) != 0, k_used);
     if (st == SGN_OK) SGN_CUDA(unpack_fields<double2>(t + nn, reinterpret_cast<double2*>(x), c->vol, nrhs, c->work));
-    SGN_CHECK(leave(c));
+    SGN_CHECK(ses.close());
     return st;
 }
 
@@ -535,13 +561,14 @@ SGN_API int sgn_pack_fields(sgn_ctx* c, const void* in, void* out, int nfield, i
     if (precision != SGN_PREC_FP64 && precision != SGN_PREC_MIXED)
         return fail(SGN_ERR_ARG, "sgn_pack_fields: unknown precision");
     SGN_CHECK(enter(c));
+    Session ses(c);
     if (precision == SGN_PREC_FP64)
         SGN_CUDA(pack_fields<double2>(reinterpret_cast<const double2*>(in), reinterpret_cast<double2*>(out), c->vol,
                                       nfield, c->work));
     else
         SGN_CUDA(pack_fields<float2>(reinterpret_cast<const float2*>(in), reinterpret_cast<float2*>(out), c->vol,
                                      nfield, c->work));
-    SGN_CHECK(leave(c));
+    SGN_CHECK(ses.close());
     return SGN_OK;
 }
 
@@ -552,13 +579,14 @@ SGN_API int sgn_unpack_fields(sgn_ctx* c, const void* in, void* out, int nfield,
     if (precision != SGN_PREC_FP64 && precision != SGN_PREC_MIXED)
         return fail(SGN_ERR_ARG, "sgn_unpack_fields: unknown precision");
     SGN_CHECK(enter(c));
+    Session ses(c);
     if (precision == SGN_PREC_FP64)
         SGN_CUDA(unpack_fields<double2>(reinterpret_cast<const double2*>(in), reinterpret_cast<double2*>(out),
                                         c->vol, nfield, c->work));
     else
         SGN_CUDA(unpack_fields<float2>(reinterpret_cast<const float2*>(in), reinterpret_cast<float2*>(out), c->vol,
                                        nfield, c->work));
-    SGN_CHECK(leave(c));
+    SGN_CHECK(ses.close());
     return SGN_OK;
 }
 
@@ -567,13 +595,14 @@ SGN_API int sgn_dhw_dmu_apply(sgn_ctx* c, const double* in, double* out, int nrh
     if (in == out) return fail(SGN_ERR_ARG, "sgn_dhw_dmu_apply: in and out must differ");
     if (!c->have_gauge) return fail(SGN_ERR_STATE, "sgn_dhw_dmu_apply: load the gauge field first");
     SGN_CHECK(enter(c));
+    Session ses(c);
     const size_t nn = (size_t)c->n * nrhs;
     SGN_CHECK(dev_alloc(c, c->stage, 2 * nn * sizeof(double2)));
     double2* t = as<double2>(c->stage);
     SGN_CUDA(pack_fields<double2>(reinterpret_cast<const double2*>(in), t, c->vol, nrhs, c->work));
     SGN_CUDA(apply_dhw_dmu64(c, t + nn, t, nrhs, c->work));
     SGN_CUDA(unpack_fields<double2>(t + nn, reinterpret_cast<double2*>(out), c->vol, nrhs, c->work));
-    SGN_CHECK(leave(c));
+    SGN_CHECK(ses.close());
     return SGN_OK;
 }
 
@@ -582,13 +611,14 @@ SGN_API int sgn_grad_mu(sgn_ctx* c, const double* b, const double* g, int nrhs, 
     if (!c->have_gauge || c->sigma.empty()) return fail(SGN_ERR_STATE, "sgn_grad_mu: gauge field and rational function needed");
     if (c->form != SGN_FORM_A2) return fail(SGN_ERR_STATE, "sgn_grad_mu: needs the A^2 formulation (per-shift iterates)");
     SGN_CHECK(enter(c));
+    Session ses(c);
     const size_t nn = (size_t)c->n * nrhs;
     SGN_CHECK(dev_alloc(c, c->stage, 2 * nn * sizeof(double2)));
     double2* t = as<double2>(c->stage);
     SGN_CUDA(pack_fields<double2>(reinterpret_cast<const double2*>(b), t, c->vol, nrhs, c->work));
     SGN_CUDA(pack_fields<double2>(reinterpret_cast<const double2*>(g), t + nn, c->vol, nrhs, c->work));
     int st = grad_mu(c, t, t + nn, nrhs, dmu);
-    SGN_CHECK(leave(c));
+    SGN_CHECK(ses.close());
     return st;
 }
 
@@ -596,6 +626,7 @@ SGN_API int sgn_inner_products(sgn_ctx* c, const double* V, int J, const double*
     if (!c || !V || !w || !out || J < 1 || J > 64 || nrhs < 1)
         return fail(SGN_ERR_ARG, "sgn_inner_products: need 1 <= J <= 64, nrhs >= 1 and non-NULL pointers");
     SGN_CHECK(enter(c));
+    Session ses(c);
     const int64_t n = c->n;
     const int nblk = reduce_blocks<double2>(n);
     const int rs = (J + 8) & ~7;
@@ -616,7 +647,7 @@ SGN_API int sgn_inner_products(sgn_ctx* c, const double* V, int J, const double*
     std::vector<double2> h((size_t)nrhs * rs);
     SGN_CUDA(cudaMemcpyAsync(h.data(), S.red, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost, c->work));
     SGN_CUDA(cudaStreamSynchronize(c->work));
-    SGN_CHECK(leave(c));
+    SGN_CHECK(ses.close());
     for (int col = 0; col < nrhs; ++col)
         for (int j = 0; j < J; ++j) {
             out[2 * ((size_t)col * J + j)] = h[(size_t)col * rs + j].x;

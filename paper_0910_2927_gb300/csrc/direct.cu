@@ -196,11 +196,20 @@ int direct_projection(sgn_ctx* c, const double2* b, double2* x, int ncol, int k,
     {
         const int nt = std::max(1, std::min<int>(ncol, (int)std::thread::hardware_concurrency()));
         std::vector<std::thread> pool;
-        for (int t = 0; t < nt; ++t)
-            pool.emplace_back([&, t]() {
-                for (int col = t; col < ncol; col += nt) work(col);
-            });
+        bool serial = false;
+        try {
+            for (int t = 1; t < nt; ++t)
+                pool.emplace_back([&, t]() {
+                    for (int col = t; col < ncol; col += nt) work(col);
+                });
+        } catch (...) {  // a thread could not be started: every column runs here (work is idempotent)
+            serial = true;
+        }
+        if (!serial)
+            for (int col = 0; col < ncol; col += nt) work(col);
         for (auto& th : pool) th.join();
+        if (serial)
+            for (int col = 0; col < ncol; ++col) work(col);
     }
     if (std::any_of(fail.begin(), fail.end(), [](int f) { return f != 0; })) {
         set_error("apply_direct: Newton iteration for sign(H_k) failed (singular iterate or no convergence)");
