@@ -67,3 +67,24 @@ def test_direct_projection_errors():
             ctx.apply_direct(b, 0)
         with pytest.raises(pkg.SignError):
             ctx.apply_direct(b, 5000)
+
+
+def test_direct_projection_zero_column_and_k1():
+    """A zero column gives x = 0 (no Krylov work) beside a normal one; k = 1 is the
+    one-dimensional projection x = ||b|| sign(h_11) v_1 with h_11 = v_1^dag A v_1."""
+    dims, mu = (2, 2, 2, 3), 0.3
+    U = si.random_su3_links(dims, 0.6, 83)
+    A = O.dense_hw(dims, U, mu)
+    b1 = si.gaussian_field(dims, 84)
+    b = np.stack([np.zeros_like(b1), b1])
+    with _ctx(dims, U, mu) as ctx:
+        x, ku = ctx.apply_direct(torch.from_numpy(b).cuda(), 7)
+        x1, k1 = ctx.apply_direct(torch.from_numpy(b1).cuda(), 1)
+    x = x.cpu().numpy()
+    assert ku == 7 and k1 == 1
+    assert float(np.abs(x[0]).max()) == 0.0
+    assert _rel(x[1], O.direct_projection(A, b1, 7)) < 1e-10
+    v = b1 / np.linalg.norm(b1)
+    h = np.vdot(v, A @ v)
+    ref1 = np.linalg.norm(b1) * np.sign(h.real) * v
+    assert _rel(x1.cpu().numpy(), ref1) < 1e-12

@@ -94,3 +94,21 @@ def test_gmres_refuses_mixed_and_split(small):
         assert rep["status"] == 0
         with pytest.raises(pkg.SignError):
             ctx.set_method(7)
+
+
+def test_single_shift_and_deflated_subspace(small):
+    """s = 1 (no bordered systems: plain restarted GMRES on one shifted system) against the
+    oracle; a right-hand side inside the deflated subspace gives x = x_P exactly."""
+    d = small
+    sigma, omega = np.array([-0.35]), np.array([0.8])
+    b = si.gaussian_field(d["dims"], 26)
+    with _ctx(d, sigma, omega, k=10, tol=1e-12, max_cycles=2000) as ctx:
+        x, rep = ctx.apply(torch.from_numpy(b).cuda())
+        ctx.set_deflation(d["R"], d["L"], d["lam"])
+        bP = d["R"] @ np.arange(1, 7)
+        xp, repp = ctx.apply(torch.from_numpy(bP).cuda())
+    xo, cyc, _ = O.gmres_lr(d["A"], b, sigma, omega, 10, tol=1e-12, max_cycles=2000)
+    assert rep["status"] == 0 and rep["cycles"] == cyc
+    assert _rel(x.cpu().numpy(), xo) < TOL_FP64
+    xP = d["R"] @ (np.sign(d["lam"].real) * np.arange(1, 7))
+    assert _rel(xp.cpu().numpy(), xP) < 1e-10

@@ -50,3 +50,24 @@ def test_overlap_apply_and_solve(lattice4):
         assert np.linalg.norm(D @ x[r] - b[r]) < 2e-10 * np.linalg.norm(b[r])
         assert np.linalg.norm(x[r] - xr) < 1e-7 * np.linalg.norm(xr)
     assert rr <= 1e-10 and its > 0
+
+
+def test_overlap_apply_mixed_form(lattice4):
+    """D_ov b through the mixed form (FP32 Krylov basis and stencil, FP64 refinement to 1e-9)
+    agrees with the dense operator to the refinement's accuracy."""
+    import paper_0910_2927_gb300 as pkg
+    d = lattice4
+    c = O.scale_from_bounds(abs(d["lam_next"][0]), 6.0)
+    sigma, omega = O.kenney_laub(16, c)
+    D = _dense_overlap(d, sigma, omega)
+    b = np.stack([d["b"], si.gaussian_field(d["dims"], 92), si.gaussian_field(d["dims"], 93)])
+    with pkg.SignContext(d["dims"], mu=d["mu"]) as ctx:
+        ctx.load_gauge(torch.from_numpy(d["U"]).cuda())
+        ctx.set_rational(sigma, omega)
+        ctx.set_restart(k=30, tol=1e-10, max_cycles=2000)
+        ctx.set_deflation(d["R"], d["L"], d["lam"])
+        ctx.set_precision(pkg.PREC_MIXED, 1e-9)
+        y = ctx.overlap(torch.from_numpy(b).cuda()).cpu().numpy()
+    for r in range(3):
+        yr = D @ b[r]
+        assert np.linalg.norm(y[r] - yr) < 1e-7 * np.linalg.norm(yr)
