@@ -98,7 +98,8 @@ cudaError_t pack_links(const double2* natural, double2* packed, int64_t vol, cud
 // fields of its site (nr <= 3 FP32, 1 FP64); {0, 0, 1} picks the default.
 // pipe = 1 selects the FP32 kernel that stages neighbour spinors through shared
 // memory with cp.async (a stage ahead of the computation; nr <= 2); pipe = 2 the
-// FP32 kernel with paired (FFMA2) arithmetic over two fields (nr = 2).
+// FP32 kernel with paired (FFMA2) arithmetic over two fields (nr = 2), pipe = 3 the
+// same kernel capped at 128 registers.
 struct StencilShape {
     int sx = 0;
     int rb = 0;

@@ -129,9 +129,9 @@ int tune_stencil(sgn_ctx* c, int prec, int ncol, void* in, void* out) {
     cudaStream_t st = c->work;
     const StencilParams p = stencil_params(c, false);
     std::vector<StencilShape> cands;
-    for (int pipe = 0; pipe <= (prec == 0 ? 0 : 2); ++pipe)
+    for (int pipe = 0; pipe <= (prec == 0 ? 0 : 3); ++pipe)
         for (int nr : {1, 2, 3}) {
-            if (nr > ncol || (prec == 0 && nr > 1) || (pipe == 1 && nr > 2) || (pipe == 2 && nr != 2)) continue;
+            if (nr > ncol || (prec == 0 && nr > 1) || (pipe == 1 && nr > 2) || (pipe >= 2 && nr != 2)) continue;
             const int groups = (ncol + nr - 1) / nr;
             const int maxt = nr == 1 && !pipe ? 384 : 256;
             for (int rb : {1, 2, 3, 4, 6, 8, 12, 16}) {

@@ -465,9 +465,9 @@ __device__ __forceinline__ void both_hops_x2(float2 (&ar)[12], float2 (&ai)[12],
 
 // Grid and thread layout as k_hw with NR = 2.
 template <class LinkT, bool CS>
-__global__ void __launch_bounds__(256)
-    k_hw_x2(float2* __restrict__ out, const float2* __restrict__ in, const LinkT* __restrict__ U, int nrhs,
-            StencilParams P, const int* __restrict__ skip, int ngrp) {
+__device__ __forceinline__ void hw_x2_body(float2* __restrict__ out, const float2* __restrict__ in,
+                                           const LinkT* __restrict__ U, int nrhs, const StencilParams& P,
+                                           const int* __restrict__ skip, int ngrp) {
     const int64_t tile = blockIdx.x / (unsigned)ngrp;
     const int grp = (int)(blockIdx.x - tile * ngrp);
     const int64_t site = tile * blockDim.x + threadIdx.x;
@@ -526,6 +526,21 @@ __global__ void __launch_bounds__(256)
         }
         Field<float>::template store<CS>(out + (rhs0 + i) * P.stride_rhs, site, 2 * P.vol, o);
     }
+}
+
+// The kernel as the compiler sizes it (144 registers: 12 warps per SM), and capped at 128
+// registers (16 warps per SM, a few values spilled to local memory).
+template <class LinkT, bool CS>
+__global__ void __launch_bounds__(256)
+    k_hw_x2(float2* __restrict__ out, const float2* __restrict__ in, const LinkT* __restrict__ U, int nrhs,
+            StencilParams P, const int* __restrict__ skip, int ngrp) {
+    hw_x2_body<LinkT, CS>(out, in, U, nrhs, P, skip, ngrp);
+}
+template <class LinkT, bool CS>
+__global__ void __launch_bounds__(256, 2)
+    k_hw_x2_r128(float2* __restrict__ out, const float2* __restrict__ in, const LinkT* __restrict__ U, int nrhs,
+                 StencilParams P, const int* __restrict__ skip, int ngrp) {
+    hw_x2_body<LinkT, CS>(out, in, U, nrhs, P, skip, ngrp);
 }
 
 // ---- pipelined FP32 form ------------------------------------------------------
@@ -794,7 +809,7 @@ cudaError_t launch_pipe(float2* out, const float2* in, const LinkT* U, int nrhs,
     return cudaGetLastError();
 }
 
-template <class LinkT>
+template <class LinkT, int MINB>
 cudaError_t launch_x2(float2* out, const float2* in, const LinkT* U, int nrhs, const StencilParams& p,
                       const int* skip, cudaStream_t st, int sx, int rb) {
     const int groups = (nrhs + 1) / 2;
@@ -803,10 +818,17 @@ cudaError_t launch_x2(float2* out, const float2* in, const LinkT* U, int nrhs, c
     if (tiles * ngrp > 0x7fffffffLL) return cudaErrorInvalidValue;
     dim3 block(sx, rb);
     const bool cs = (double)nrhs * (double)p.vol * 12.0 * sizeof(float2) > 256.0 * (1 << 20);
-    if (cs)
-        k_hw_x2<LinkT, true><<<(unsigned)(tiles * ngrp), block, 0, st>>>(out, in, U, nrhs, p, skip, ngrp);
-    else
-        k_hw_x2<LinkT, false><<<(unsigned)(tiles * ngrp), block, 0, st>>>(out, in, U, nrhs, p, skip, ngrp);
+    const unsigned grid = (unsigned)(tiles * ngrp);
+    if (MINB == 2) {
+        if (cs)
+            k_hw_x2_r128<LinkT, true><<<grid, block, 0, st>>>(out, in, U, nrhs, p, skip, ngrp);
+        else
+            k_hw_x2_r128<LinkT, false><<<grid, block, 0, st>>>(out, in, U, nrhs, p, skip, ngrp);
+    } else if (cs) {
+        k_hw_x2<LinkT, true><<<grid, block, 0, st>>>(out, in, U, nrhs, p, skip, ngrp);
+    } else {
+        k_hw_x2<LinkT, false><<<grid, block, 0, st>>>(out, in, U, nrhs, p, skip, ngrp);
+    }
     count_launch();
     return cudaGetLastError();
 }
@@ -815,10 +837,11 @@ template <class R, class LinkT>
 cudaError_t launch(typename Field<R>::T* out, const typename Field<R>::T* in, const LinkT* U, int nrhs,
                    const StencilParams& p, const int* skip, cudaStream_t st, StencilShape sh) {
     if (nrhs <= 0 || p.vol <= 0) return cudaSuccess;
-    if (sh.pipe == 2) {  // the paired FP32 kernel: two fields per thread, up to 256 threads per CTA
+    if (sh.pipe == 2 || sh.pipe == 3) {  // the paired FP32 kernel (3: capped at 128 registers)
         if constexpr (sizeof(R) == 4) {
             if (sh.sx % 32 != 0 || sh.rb < 1 || sh.sx * sh.rb > 256 || sh.nr != 2) return cudaErrorInvalidValue;
-            return launch_x2<LinkT>(out, in, U, nrhs, p, skip, st, sh.sx, sh.rb);
+            if (sh.pipe == 3) return launch_x2<LinkT, 2>(out, in, U, nrhs, p, skip, st, sh.sx, sh.rb);
+            return launch_x2<LinkT, 1>(out, in, U, nrhs, p, skip, st, sh.sx, sh.rb);
         } else {
             return cudaErrorInvalidValue;
         }

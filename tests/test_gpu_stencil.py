@@ -105,7 +105,8 @@ def test_packed_layout_roundtrip_and_stencil():
 
 @pytest.mark.parametrize("shape", ["32,4,3", "64,2,2", "32,2,3", "64,3,1", "128,1,2",
                                    "32,4,1,1", "64,2,2,1", "128,1,2,1", "256,1,1,1",
-                                   "32,4,2,2", "64,2,2,2", "128,1,2,2", "256,1,2,2"])
+                                   "32,4,2,2", "64,2,2,2", "128,1,2,2", "256,1,2,2",
+                                   "64,2,2,3", "128,1,2,3"])
 def test_fp32_stencil_launch_shapes(shape, monkeypatch):
     """Every launch shape (sites per CTA, thread rows, fields per thread, the kernel
     that stages neighbours through shared memory with cp.async, and the kernel with
@@ -128,7 +129,7 @@ def test_fp32_stencil_launch_shapes(shape, monkeypatch):
         assert np.linalg.norm(outa[r] - refa) / np.linalg.norm(refa) < 2e-6
 
 
-@pytest.mark.parametrize("shape", ["32,12,3", "64,2,1,2", "128,4,2,2"])
+@pytest.mark.parametrize("shape", ["32,12,3", "64,2,1,2", "128,4,2,2", "64,2,3,3"])
 def test_invalid_launch_shape_is_an_error(shape, monkeypatch):
     """A shape outside the kernel's limits (384 threads with 3 fields each; the paired
     kernel with one field per thread, or with 512 threads) is refused with an error."""
@@ -143,7 +144,7 @@ def test_invalid_launch_shape_is_an_error(shape, monkeypatch):
             ctx.hw(torch.from_numpy(b).cuda(), precision=pkg.PREC_MIXED)
 
 
-@pytest.mark.parametrize("shape", ["64,2,2,1", "32,4,1,1", "64,2,2,2"])
+@pytest.mark.parametrize("shape", ["64,2,2,1", "32,4,1,1", "64,2,2,2", "128,1,2,3"])
 def test_pipelined_stencil_bf16_links_and_many_fields(shape, monkeypatch):
     """The shared-memory staged kernel with BF16 links and 13 fields (several CTAs
     per site tile) matches the oracle within the BF16 rounding of the links."""
