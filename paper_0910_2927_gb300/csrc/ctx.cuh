@@ -26,6 +26,9 @@ inline T* as(DevBuf& b) {
     return reinterpret_cast<T*>(b.p);
 }
 
+// Sub-buffer offsets within one allocation are rounded up to 256 bytes.
+inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
 // Workspace of one FOM-LR engine configuration (columns, restart length,
 // number of shifts, storage precision).  Carved out of one allocation.
 struct Engine {

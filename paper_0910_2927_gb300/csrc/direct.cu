@@ -15,7 +15,6 @@
 namespace sgn {
 
 namespace {
-size_t al256d(size_t b) { return (b + 255) & ~size_t(255); }
 constexpr int GS_BLOCK = 128;
 
 // sign(M) of a small dense matrix (row-major kk x kk) by Roberts' Newton iteration:
@@ -51,12 +50,12 @@ int direct_projection(sgn_ctx* c, const double2* b, double2* x, int ncol, int k,
     const size_t field = (size_t)n * sizeof(double2);
     const int rs = GS_BLOCK + 8;
     const int nblk = reduce_blocks<double2>(n);
-    const size_t oV = 0, ow = oV + al256d(field * (size_t)(k + 1) * ncol);
-    const size_t op = ow + al256d(field * ncol);
-    const size_t ored = op + al256d(sizeof(double2) * (size_t)ncol * rs * nblk);
-    const size_t ocoef = ored + al256d(sizeof(double2) * (size_t)ncol * rs);
-    const size_t oflag = ocoef + al256d(sizeof(double2) * (size_t)ncol * rs);
-    const size_t total = oflag + al256d(sizeof(int) * 2 * (size_t)ncol);
+    const size_t oV = 0, ow = oV + align256(field * (size_t)(k + 1) * ncol);
+    const size_t op = ow + align256(field * ncol);
+    const size_t ored = op + align256(sizeof(double2) * (size_t)ncol * rs * nblk);
+    const size_t ocoef = ored + align256(sizeof(double2) * (size_t)ncol * rs);
+    const size_t oflag = ocoef + align256(sizeof(double2) * (size_t)ncol * rs);
+    const size_t total = oflag + align256(sizeof(int) * 2 * (size_t)ncol);
     DevBuf buf;
     SGN_CHECK(dev_alloc(c, buf, total));
     char* base = reinterpret_cast<char*>(buf.p);

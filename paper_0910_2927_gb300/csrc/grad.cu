@@ -43,8 +43,6 @@ namespace {
 
 using cd = std::complex<double>;
 
-size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
-
 // Inner products and combinations with a small set of fields X (nx <= 64), FP64.
 struct Small {
     sgn_ctx* c;

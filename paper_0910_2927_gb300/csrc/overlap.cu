@@ -10,10 +10,6 @@
 
 namespace sgn {
 
-namespace {
-size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
-}  // namespace
-
 // y = b + gamma5 F(A) b on ncol packed FP64 fields (y and b may not overlap)
 int overlap_apply(sgn_ctx* c, const double2* b, double2* y, int ncol, sgn_report* rep) {
     cudaStream_t st = c->work;
@@ -42,12 +38,12 @@ int overlap_solve(sgn_ctx* c, const double2* b, double2* x, int ncol, double tol
     const size_t field = (size_t)n * sizeof(double2);
     const int rs = ((k + 2) + 7) & ~7;
     const int nblk = reduce_blocks<double2>(n);
-    const size_t oV = 0, ow = oV + al256(field * (size_t)(k + 1) * ncol);
-    const size_t op = ow + al256(field * ncol);
-    const size_t ored = op + al256(sizeof(double2) * (size_t)ncol * rs * nblk);
-    const size_t ocoef = ored + al256(sizeof(double2) * (size_t)ncol * rs);
-    const size_t oflag = ocoef + al256(sizeof(double2) * (size_t)ncol * rs);
-    const size_t total = oflag + al256(sizeof(int) * 2 * (size_t)ncol);
+    const size_t oV = 0, ow = oV + align256(field * (size_t)(k + 1) * ncol);
+    const size_t op = ow + align256(field * ncol);
+    const size_t ored = op + align256(sizeof(double2) * (size_t)ncol * rs * nblk);
+    const size_t ocoef = ored + align256(sizeof(double2) * (size_t)ncol * rs);
+    const size_t oflag = ocoef + align256(sizeof(double2) * (size_t)ncol * rs);
+    const size_t total = oflag + align256(sizeof(int) * 2 * (size_t)ncol);
     DevBuf buf;
     SGN_CHECK(dev_alloc(c, buf, total));
     char* base = reinterpret_cast<char*>(buf.p);

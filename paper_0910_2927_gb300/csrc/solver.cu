@@ -202,8 +202,6 @@ cudaError_t apply_hw<float2>(const sgn_ctx* c, float2* out, const float2* in, in
         if (_e != cudaSuccess) return _e;         \
     } while (0)
 
-inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
-
 uint64_t mix(uint64_t h, uint64_t v) {
     h ^= v + 0x9e3779b97f4a7c15ULL + (h << 6) + (h >> 2);
     return h;
