@@ -318,6 +318,33 @@ def gmres_lr(A, b, sigma, omega, k, tol, max_cycles=1000, R=None, L=None, lam=No
     return xP + omega @ X, cycles, res
 
 
+def gamma5_diag(vol):
+    """gamma5 = gamma1 gamma2 gamma3 gamma4 = diag(1, 1, -1, -1) in the chiral basis of Sec. 1's
+    H_W = gamma5 D_W, as the diagonal of the natural [site][spin][colour] layout."""
+    return np.tile(np.repeat([1.0, 1.0, -1.0, -1.0], 3), vol)
+
+
+def deflated_sign_matrix(A, sigma, omega, m=0, decomposition=None):
+    """Dense F(A) = X f(Lambda) X^{-1} of the deflated rational sign function (eqs. (4.2)-(4.3)
+    with (6.2)): f = sign(Re lambda) on the m critical eigenvalues (smallest |lambda|, the order
+    of critical_eigenpairs) and f(t) = t sum_i omega_i / (t^2 - sigma_i) on the rest, so that
+    F b = deflated_target(A, b, sigma, omega, R, L, lam) with those m pairs."""
+    w, X, Xinv = decomposition if decomposition is not None else eig(A)
+    order = np.lexsort((w.imag, w.real, np.abs(w)))
+    w, X, Xinv = w[order], X[:, order], Xinv[order, :]
+    sigma = np.asarray(sigma, dtype=np.float64)
+    omega = np.asarray(omega, dtype=np.float64)
+    f = w * np.sum(omega[None, :] / (w[:, None] ** 2 - sigma[None, :]), axis=1)
+    f[:m] = np.where(w[:m].real > 0, 1.0, -1.0)
+    return X @ (f[:, None] * Xinv)
+
+
+def overlap_dense(F, vol):
+    """The overlap operator D_ov = 1 + gamma5 F (Sec. 1: the operator the sign function is
+    computed for), F a dense sign matrix (exact, or the deflated rational approximation)."""
+    return np.eye(F.shape[0]) + gamma5_diag(vol)[:, None] * F
+
+
 def sign_eig(A, decomposition=None):
     """Exact sign(A) = X sign(Re Lambda) X^{-1} (spectral definition, Sec. 1 footnote)."""
     w, X, Xinv = decomposition if decomposition is not None else eig(A)

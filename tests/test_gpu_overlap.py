@@ -14,16 +14,9 @@ torch = pytest.importorskip("torch")
 
 
 def _dense_overlap(d, sigma, omega):
-    w, X, Xi = d["eig"]
-    order = np.lexsort((w.imag, w.real, np.abs(w)))
-    w, X, Xi = w[order], X[:, order], Xi[order, :]
-    f = w * np.sum(omega[None, :] / (w[:, None] ** 2 - sigma[None, :]), axis=1)
-    m = len(d["lam"])
-    f[:m] = np.sign(w[:m].real)
-    F = X @ (f[:, None] * Xi)
-    vol = int(np.prod(d["dims"]))
-    g5 = np.tile(np.array([1.0] * 6 + [-1.0] * 6), vol)
-    return np.eye(F.shape[0]) + g5[:, None] * F
+    """I + gamma5 F(A), F the deflated rational sign function with the fixture's m pairs."""
+    F = O.deflated_sign_matrix(d["A"], sigma, omega, m=len(d["lam"]), decomposition=d["eig"])
+    return O.overlap_dense(F, int(np.prod(d["dims"])))
 
 
 def test_overlap_apply_and_solve(lattice4):

@@ -108,3 +108,45 @@ def test_sites_subset_matches_full():
     full = O.hw(dims, U, psi, 0.3).reshape(-1, 12)
     sites = np.array([0, 7, 33, 119])
     np.testing.assert_array_equal(O.hw_sites(dims, U, psi, sites, 0.3), full[sites])
+
+
+def test_overlap_ginsparg_wilson_and_circle():
+    """D_ov = 1 + gamma5 sign(H_W) with the exact sign satisfies the Ginsparg-Wilson relation
+    gamma5 D + D gamma5 = D gamma5 D at any mu (it needs only sign^2 = 1); at mu = 0 (H_W
+    Hermitian) D_ov is normal with its spectrum on the circle |z - 1| = 1.  A wrong gamma5
+    (another spin order or sign) breaks both."""
+    dims = (2, 2, 2, 2)
+    vol = 16
+    U = si.random_su3_links(dims, 0.6, 71)
+    g5 = np.diag(O.gamma5_diag(vol))
+    for mu in (0.0, 0.35):
+        A = O.dense_hw(dims, U, mu)
+        D = O.overlap_dense(O.sign_eig(A), vol)
+        lhs = g5 @ D + D @ g5
+        assert np.linalg.norm(lhs - D @ g5 @ D) < 1e-10 * np.linalg.norm(lhs)
+        if mu == 0.0:
+            assert np.linalg.norm(D @ D.conj().T - D.conj().T @ D) < 1e-10 * np.linalg.norm(D) ** 2
+            z = np.linalg.eigvals(D)
+            assert np.max(np.abs(np.abs(z - 1.0) - 1.0)) < 1e-10
+    # gamma5 H_W is D_W: its hermiticity at mu = 0 fixes the gamma5 of H_W = gamma5 D_W
+    A0 = O.dense_hw(dims, U, 0.0)
+    assert np.linalg.norm(A0 - A0.conj().T) < 1e-12 * np.linalg.norm(A0)
+    Dw = g5 @ A0
+    assert np.linalg.norm(g5 @ Dw @ g5 - Dw.conj().T) < 1e-12 * np.linalg.norm(Dw)
+
+
+def test_deflated_sign_matrix_matches_deflated_target():
+    """The dense F(A) applied to b equals the deflated target built by shifted LU solves."""
+    dims, mu = (2, 2, 2, 2), 0.3
+    U = si.random_su3_links(dims, 0.6, 72)
+    A = O.dense_hw(dims, U, mu)
+    b = si.gaussian_field(dims, 73)
+    sigma, omega = O.kenney_laub(8, 0.5)
+    dec = O.eig(A)
+    R, L, lam, _ = O.critical_eigenpairs(A, 5, decomposition=dec)
+    F = O.deflated_sign_matrix(A, sigma, omega, m=5, decomposition=dec)
+    xt = O.deflated_target(A, b, sigma, omega, R, L, lam)
+    assert np.linalg.norm(F @ b - xt) < 1e-10 * np.linalg.norm(xt)
+    F0 = O.deflated_sign_matrix(A, sigma, omega, m=0, decomposition=dec)
+    xt0 = O.deflated_target(A, b, sigma, omega)
+    assert np.linalg.norm(F0 @ b - xt0) < 1e-10 * np.linalg.norm(xt0)
