@@ -345,6 +345,53 @@ def overlap_dense(F, vol):
     return np.eye(F.shape[0]) + gamma5_diag(vol)[:, None] * F
 
 
+def dense_dhw_dmu(dims, links, mu, mass=-1.6, antiperiodic=(0, 0, 0, 1), h=1e-3):
+    """Dense A' = dH_W/dmu.  H_W(mu) = H_0 + e^{mu} T_+ + e^{-mu} T_- (the chemical potential
+    enters only the forward and backward time hops, Sec. 1), so
+    H_W(mu + h) - H_W(mu - h) = 2 sinh(h) (e^{mu} T_+ - e^{-mu} T_-) = 2 sinh(h) A' exactly."""
+    Hp = dense_hw(dims, links, mu + h, mass, antiperiodic)
+    Hm = dense_hw(dims, links, mu - h, mass, antiperiodic)
+    return (Hp - Hm) / (2.0 * math.sinh(h))
+
+
+def rational_g(t, sigma, omega):
+    """g(t) = t sum_i omega_i / (t^2 - sigma_i) (eq. (6.2) with the scale folded in) and g'(t)."""
+    t = np.asarray(t)
+    sigma = np.asarray(sigma, dtype=np.float64)
+    omega = np.asarray(omega, dtype=np.float64)
+    q = t[:, None] ** 2 - sigma[None, :]
+    g = t * np.sum(omega[None, :] / q, axis=1)
+    gp = np.sum(omega[None, :] * (-(t[:, None] ** 2) - sigma[None, :]) / q ** 2, axis=1)
+    return g, gp
+
+
+def frechet_dense(E, fvals, fprime, decomposition):
+    """Frechet derivative of a matrix function of a diagonalisable A = X diag(w) X^{-1} along E
+    (Daleckii-Krein): X (F ∘ (X^{-1} E X)) X^{-1}, F_jk the divided difference
+    (f(w_j) - f(w_k)) / (w_j - w_k), and f'(w_j) on the diagonal and for equal eigenvalues."""
+    w, X, Xinv = decomposition
+    D = w[:, None] - w[None, :]
+    same = np.abs(D) < 1e-12
+    F = np.where(same, 0, (fvals[:, None] - fvals[None, :]) / np.where(same, 1, D))
+    F[np.arange(len(w)), np.arange(len(w))] = fprime
+    return X @ (F * (Xinv @ E @ X)) @ Xinv
+
+
+def deflated_sign_derivative(A, E, sigma, omega, m=0, decomposition=None):
+    """Derivative along E of the deflated rational sign function F(A) of deflated_sign_matrix:
+    f = sign(Re lambda) on the m critical eigenvalues (derivative 0 there) and g elsewhere; the
+    motion of the deflated eigenvectors enters through the divided differences between
+    deflated and undeflated eigenvalues.  Returns (F, dF[E])."""
+    w, X, Xinv = decomposition if decomposition is not None else eig(A)
+    order = np.lexsort((w.imag, w.real, np.abs(w)))
+    w, X, Xinv = w[order], X[:, order], Xinv[order, :]
+    f, fp = rational_g(w, sigma, omega)
+    f[:m] = np.where(w[:m].real > 0, 1.0, -1.0)
+    fp[:m] = 0.0
+    F = X @ (f[:, None] * Xinv)
+    return F, frechet_dense(E, f, fp, (w, X, Xinv))
+
+
 def sign_eig(A, decomposition=None):
     """Exact sign(A) = X sign(Re Lambda) X^{-1} (spectral definition, Sec. 1 footnote)."""
     w, X, Xinv = decomposition if decomposition is not None else eig(A)

@@ -36,8 +36,9 @@ def test_dhw_dmu_matches_central_difference():
 
 
 def test_gradients_match_dense_daleckii_krein():
-    """Dense reference: A = X diag(l) X^{-1}, F(A) = X f(l) X^{-1} with f(t) = t sum omega/(t^2 - sigma);
-    dF[E] = X (F^ o (X^{-1} E X)) X^{-1}, F^_jk = divided differences of f."""
+    """Dense reference (oracle deflated_sign_derivative with m = 0): A = X diag(l) X^{-1},
+    F(A) = X f(l) X^{-1} with f(t) = t sum omega/(t^2 - sigma); dF[E] = X (F^ o (X^{-1} E X)) X^{-1},
+    F^_jk = divided differences of f, along E = A' (oracle dense_dhw_dmu)."""
     from paper_0910_2927_gb300.autograd import SignApply
     dims, mu = (3, 2, 3, 4), 0.5
     U = si.random_su3_links(dims, 0.7, 53)
@@ -45,19 +46,9 @@ def test_gradients_match_dense_daleckii_krein():
     c = si.gaussian_field(dims, 55)
     sigma, omega = O.kenney_laub(12, 0.4)
     A = O.dense_hw(dims, U, mu)
-    h = 1e-6
-    Ad = (O.dense_hw(dims, U, mu + h) - O.dense_hw(dims, U, mu - h)) / (2 * h)   # A' (linear in e^{+-mu})
-    w, X, Xi = O.eig(A)
-    f = lambda t: t * np.sum(omega[None, :] / (t[:, None] ** 2 - sigma[None, :]), axis=1)
-    fp = lambda t: np.sum(omega[None, :] * (-(t[:, None] ** 2) - sigma[None, :]) / (t[:, None] ** 2 - sigma[None, :]) ** 2, axis=1)
-    fw = f(w)
-    D = w[:, None] - w[None, :]
-    same = np.abs(D) < 1e-12
-    Fh = np.where(same, 0, (fw[:, None] - fw[None, :]) / np.where(same, 1, D))
-    Fh[np.arange(len(w)), np.arange(len(w))] = fp(w)
-    dF = X @ (Fh * (Xi @ Ad @ X)) @ Xi
+    F, dF = O.deflated_sign_derivative(A, O.dense_dhw_dmu(dims, U, mu), sigma, omega, m=0)
     dmu_ref = np.real(np.vdot(c, dF @ b))
-    gb_ref = (X @ (fw[:, None] * Xi)).conj().T @ c
+    gb_ref = F.conj().T @ c
     bt = torch.from_numpy(b).cuda().requires_grad_(True)
     mut = torch.tensor(mu, dtype=torch.float64, requires_grad=True)
     with _ctx(dims, U, mu, sigma, omega) as ctx:
@@ -115,29 +106,13 @@ def test_deflated_gradient_matches_dense_daleckii_krein(mu, m):
     c = si.gaussian_field(dims, 59)
     sigma, omega = O.kenney_laub(12, 0.4)
     A = O.dense_hw(dims, U, mu)
-    h = 1e-6
-    Ad = (O.dense_hw(dims, U, mu + h) - O.dense_hw(dims, U, mu - h)) / (2 * h)   # A' (linear in e^{+-mu})
     dec = O.eig(A)
     e = 4  # the next eigenpairs, kept for the reduced resolvents of the derivative
     Ra, La, lama, _ = O.critical_eigenpairs(A, m + e, decomposition=dec)
     R, L, lam = Ra[:, :m], La[:, :m], lama[:m]
-    w, X, Xi = dec
-    order = np.lexsort((w.imag, w.real, np.abs(w)))
-    w, X, Xi = w[order], X[:, order], Xi[order, :]
-    g = lambda t: t * np.sum(omega[None, :] / (t[:, None] ** 2 - sigma[None, :]), axis=1)
-    gp = lambda t: np.sum(omega[None, :] * (-(t[:, None] ** 2) - sigma[None, :]) / (t[:, None] ** 2 - sigma[None, :]) ** 2,
-                          axis=1)
-    fw = g(w)
-    fpw = gp(w)
-    fw[:m] = np.sign(w[:m].real)
-    fpw[:m] = 0.0
-    D = w[:, None] - w[None, :]
-    same = np.abs(D) < 1e-12
-    Fh = np.where(same, 0, (fw[:, None] - fw[None, :]) / np.where(same, 1, D))
-    Fh[np.arange(len(w)), np.arange(len(w))] = fpw
-    dF = X @ (Fh * (Xi @ Ad @ X)) @ Xi
+    F, dF = O.deflated_sign_derivative(A, O.dense_dhw_dmu(dims, U, mu), sigma, omega, m=m, decomposition=dec)
     dmu_ref = np.real(np.vdot(c, dF @ b))
-    x_ref = X @ (fw * (Xi @ b))
+    x_ref = F @ b
     bt = torch.from_numpy(b).cuda().requires_grad_(True)
     mut = torch.tensor(mu, dtype=torch.float64, requires_grad=True)
     with _ctx(dims, U, mu, sigma, omega) as ctx:
@@ -146,6 +121,6 @@ def test_deflated_gradient_matches_dense_daleckii_krein(mu, m):
         assert np.linalg.norm(x.detach().cpu().numpy() - x_ref) < 1e-9 * np.linalg.norm(x_ref)
         loss = torch.vdot(torch.from_numpy(c).cuda(), x).real
         loss.backward()
-    gb_ref = (X @ (fw[:, None] * Xi)).conj().T @ c
+    gb_ref = F.conj().T @ c
     assert np.linalg.norm(bt.grad.cpu().numpy() - gb_ref) < 1e-9 * np.linalg.norm(gb_ref)
     assert abs(float(mut.grad) - dmu_ref) < 1e-7 * max(1.0, abs(dmu_ref)), (float(mut.grad), dmu_ref)

@@ -150,3 +150,56 @@ def test_deflated_sign_matrix_matches_deflated_target():
     F0 = O.deflated_sign_matrix(A, sigma, omega, m=0, decomposition=dec)
     xt0 = O.deflated_target(A, b, sigma, omega)
     assert np.linalg.norm(F0 @ b - xt0) < 1e-10 * np.linalg.norm(xt0)
+
+
+def test_dense_dhw_dmu_against_richardson_difference():
+    """A' from the exact sinh form against a fourth-order central difference of the C stencil
+    (no shared arithmetic: the stencil is the oracle's C code, the dense matrix its NumPy build)."""
+    dims, mu = (2, 2, 3, 2), 0.45
+    U = si.random_su3_links(dims, 0.6, 74)
+    v = si.gaussian_field(dims, 75)
+    Ad = O.dense_dhw_dmu(dims, U, mu)
+    h = 1e-2
+    d1 = (O.hw(dims, U, v, mu + h) - O.hw(dims, U, v, mu - h)) / (2 * h)
+    d2 = (O.hw(dims, U, v, mu + 2 * h) - O.hw(dims, U, v, mu - 2 * h)) / (4 * h)
+    rich = (4 * d1 - d2) / 3
+    assert np.linalg.norm(Ad @ v - rich) < 1e-8 * np.linalg.norm(rich)
+    # the sinh form is exact, so the step does not matter (a plain central difference would
+    # change by O(h^2) between these steps)
+    assert np.linalg.norm(O.dense_dhw_dmu(dims, U, mu) - O.dense_dhw_dmu(dims, U, mu, h=0.3)) \
+        < 1e-12 * np.linalg.norm(Ad)
+
+
+def test_frechet_closed_forms():
+    """Daleckii-Krein with f(t) = t^2 gives A E + E A, with f(t) = t^3 gives A^2 E + A E A + E A^2."""
+    rng = np.random.default_rng(7)
+    A = rng.standard_normal((9, 9)) + 1j * rng.standard_normal((9, 9))
+    E = rng.standard_normal((9, 9)) + 1j * rng.standard_normal((9, 9))
+    dec = O.eig(A)
+    w = dec[0]
+    d2 = O.frechet_dense(E, w ** 2, 2 * w, dec)
+    assert np.linalg.norm(d2 - (A @ E + E @ A)) < 1e-10 * np.linalg.norm(A @ E)
+    d3 = O.frechet_dense(E, w ** 3, 3 * w ** 2, dec)
+    ref3 = A @ A @ E + A @ E @ A + E @ A @ A
+    assert np.linalg.norm(d3 - ref3) < 1e-10 * np.linalg.norm(ref3)
+
+
+def test_deflated_sign_derivative_against_mu_difference():
+    """d/dmu of the dense deflated sign matrix (eigendecompositions recomputed at mu +- h, the m
+    critical pairs re-selected) equals the Daleckii-Krein derivative along A', undeflated and
+    deflated; F is the same matrix deflated_sign_matrix builds."""
+    dims, mu = (2, 2, 2, 3), 0.4
+    U = si.random_su3_links(dims, 0.6, 76)
+    sigma, omega = O.kenney_laub(8, 0.5)
+    A = O.dense_hw(dims, U, mu)
+    Ad = O.dense_dhw_dmu(dims, U, mu)
+    dec = O.eig(A)
+    h = 1e-5
+    for m in (0, 5):
+        F, dF = O.deflated_sign_derivative(A, Ad, sigma, omega, m=m, decomposition=dec)
+        assert np.linalg.norm(F - O.deflated_sign_matrix(A, sigma, omega, m=m, decomposition=dec)) \
+            < 1e-13 * np.linalg.norm(F)
+        Fp = O.deflated_sign_matrix(O.dense_hw(dims, U, mu + h), sigma, omega, m=m)
+        Fm = O.deflated_sign_matrix(O.dense_hw(dims, U, mu - h), sigma, omega, m=m)
+        fd = (Fp - Fm) / (2 * h)
+        assert np.linalg.norm(dF - fd) < 1e-6 * np.linalg.norm(fd)
