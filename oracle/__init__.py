@@ -56,12 +56,19 @@ def lib():
                                  C.POINTER(_Report)]
         L.orc_fom_lr.restype = C.c_int
         L.orc_num_threads.restype = C.c_int
+        L.orc_set_num_threads.argtypes = [C.c_int]
+        L.orc_set_num_threads.restype = C.c_int
         _LIB = L
     return _LIB
 
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(n: int) -> int:
+    """Threads of the oracle's later OpenMP regions; returns the count now in force."""
+    return int(lib().orc_set_num_threads(int(n)))
 
 
 def _lat(dims, mu, mass, antiperiodic):

@@ -53,5 +53,6 @@ int orc_fom_lr(const orc_lattice* lat, const orc_c* U,
                const orc_c* b, orc_c* x, orc_c* x_shift, orc_report* rep);
 
 int orc_num_threads(void);
+int orc_set_num_threads(int n);
 
 #endif

@@ -80,6 +80,17 @@ int orc_num_threads(void) {
 #endif
 }
 
+/* Threads of the later parallel regions (n >= 1); returns the count now in force. */
+int orc_set_num_threads(int n) {
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 /* Neighbour of site (coordinates c) one step in direction nu, forward (+1) or
  * backward (-1); *phase becomes -1 when the hop wraps an antiperiodic edge. */
 static int64_t hop(const orc_lattice* lat, const int c[4], int nu, int dir, double* phase) {
