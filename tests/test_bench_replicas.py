@@ -92,3 +92,23 @@ def test_reference_arm_line_on_rank_zero(monkeypatch):
     assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
     assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_roofline_entry_arithmetic():
+    """The roofline entry picks the bandwidth class with the largest summed event time (never the
+    latency-bound second-stage reduction), divides bytes per launch by the average duration, and
+    scales the measured DRAM ratio by the average launch's bytes (null where none was measured)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    kt = {"k_reduce": {"ms": 99.0, "launches": 10, "bytes": 1e6},
+          "k_dcgs_update<float2>": {"ms": 20.0, "launches": 10, "bytes": 10 * 6.8e7},
+          "k_hw<float,float2>": {"ms": 15.0, "launches": 30, "bytes": 30 * 1e7}}
+    r = bench.roofline(kt, 6800.0, "measured", 0.1)
+    assert r["kernel"] == "k_dcgs_update<float2>" and r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["achieved"] == pytest.approx(6.8e7 / 2e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6800.0)
+    assert r["traffic"] == pytest.approx(bench.DRAM_PER_ALGORITHMIC_BYTE["k_dcgs_update<float2>"] * 6.8e7)
+    assert r["share_of_timed"] == pytest.approx(0.2)
+    kt["k_hw<float,float2>"]["ms"] = 50.0
+    r = bench.roofline(kt, 6800.0, "measured", 0.1)
+    assert r["kernel"] == "k_hw<float,float2>" and r["traffic"] is None
