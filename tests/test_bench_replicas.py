@@ -112,3 +112,19 @@ def test_roofline_entry_arithmetic():
     kt["k_hw<float,float2>"]["ms"] = 50.0
     r = bench.roofline(kt, 6800.0, "measured", 0.1)
     assert r["kernel"] == "k_hw<float,float2>" and r["traffic"] is None
+
+
+def test_clock_summary_parses_samples():
+    """Median SM clock under load, the maximum, and the throttle reasons seen in any sample."""
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.ClockSampler(0)
+    c.lines = ["2070, 2070, 712.3, Not Active, Not Active, Not Active, Not Active",
+               "1980, 2070, 1399.0, Not Active, Not Active, Not Active, Active",
+               "2070, 2070, 900.1, Not Active, Not Active, Not Active, Not Active",
+               "[N/A], garbage"]
+    s = c.summary()
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    c.lines = []
+    assert c.summary()["reasons"] == ["unsampled"]
