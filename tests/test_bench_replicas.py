@@ -128,3 +128,17 @@ def test_clock_summary_parses_samples():
     assert s["reasons"] == ["sw_power_cap"]
     c.lines = []
     assert c.summary()["reasons"] == ["unsampled"]
+
+
+def test_workload_inputs():
+    """The default workload's sources are the 12 spin-colour point sources at site 0 (column
+    3 spin + colour is the unit vector of that component), and its name states the sizes."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import numpy as np
+    w = bench.WORKLOADS["10^4"]
+    B = bench.sources(w)
+    assert B.shape == (12, 12 * 10 ** 4)
+    assert np.array_equal(B[:, :12], np.eye(12)) and not np.any(B[:, 12:])
+    name = bench.workload_name(w, "10^4")
+    assert "lattice 10x10x10x10" in name and "FOM-LR(30,40)" in name and "12 point sources" in name
