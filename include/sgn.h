@@ -125,19 +125,28 @@ SGN_API int sgn_set_stream(sgn_ctx* ctx, void* stream);
 
 /* Copy the gauge field (Sec. 1: the links of D_W) into the context: complex128,
  * [site][dir][3][3]; on_device = 1 for a device pointer, 0 for host memory.
- * The caller keeps ownership of `links`.  Non-finite entries: SGN_ERR_NONFINITE. */
+ * The caller keeps ownership of `links`.  Non-finite entries: SGN_ERR_NONFINITE
+ * (checked for host links; device links are not read back).  Drops deflation
+ * data as sgn_set_mu does. */
 SGN_API int sgn_load_gauge(sgn_ctx* ctx, const double* links, int on_device);
 
 /* Quark chemical potential mu: forward time hops carry e^{+mu}, backward e^{-mu}
- * (Sec. 1; non-Hermitian for mu != 0).  Drops any deflation data, which belongs
- * to one operator (SGN_ERR_STATE on apply until it is set again). */
+ * (Sec. 1; non-Hermitian for mu != 0).  A new value drops any deflation data,
+ * which belong to one operator (eq. (4.1)).  If there were any, sgn_apply,
+ * sgn_apply_shifts, sgn_overlap_apply, sgn_overlap_solve, sgn_apply_direct and
+ * sgn_grad_mu then return SGN_ERR_STATE until deflation data are built
+ * (sgn_build_deflation), set (sgn_set_deflation), or explicitly cleared
+ * (sgn_set_deflation with m = 0).  sgn_load_gauge, sgn_set_kernel_mass and
+ * sgn_set_boundary do the same. */
 SGN_API int sgn_set_mu(sgn_ctx* ctx, double mu);
 
-/* Wilson kernel mass m_W (the workloads use -1.6).  Drops deflation data. */
+/* Wilson kernel mass m_W (the workloads use -1.6).  A new value drops deflation
+ * data as sgn_set_mu does. */
 SGN_API int sgn_set_kernel_mass(sgn_ctx* ctx, double m_w);
 
 /* Boundary conditions: antiperiodic[nu] = 1 flips the sign of hops that wrap
- * direction nu.  Default {0, 0, 0, 1}.  Drops deflation data. */
+ * direction nu.  Default {0, 0, 0, 1}.  A change drops deflation data as
+ * sgn_set_mu does. */
 SGN_API int sgn_set_boundary(sgn_ctx* ctx, const int antiperiodic[4]);
 
 /* Kenney-Laub partial fractions, eq. (6.2), with the scale c of Sec. 6 folded in:
@@ -182,8 +191,10 @@ SGN_API int sgn_set_refinement(sgn_ctx* ctx, int k_refine, int max_batch);
 /* LR deflation data of Sec. 4 (eq. (4.1)): m right eigenvectors R and left
  * eigenvectors L (each n x m, column j = one field of n = 12 V complex128,
  * columns back to back), eigenvalues lambda (m complex128), normalised so that
- * L^dag R = I_m.  on_device as in sgn_load_gauge.  Copied; m = 0 clears.
- * Errors: SGN_ERR_ARG, SGN_ERR_NONFINITE. */
+ * L^dag R = I_m.  on_device as in sgn_load_gauge.  Copied; m = 0 clears (and
+ * lifts the SGN_ERR_STATE refusal that follows a change of the operator).
+ * Errors: SGN_ERR_ARG, SGN_ERR_NONFINITE, SGN_ERR_DEFLATION (Re lambda_j = 0:
+ * sign(Re lambda) undefined). */
 SGN_API int sgn_set_deflation(sgn_ctx* ctx, int m, const double* R, const double* L,
                               const double* lambda, int on_device);
 
@@ -216,7 +227,10 @@ SGN_API int sgn_get_deflation(sgn_ctx* ctx, int* m, double* R, double* L, double
  * SGN_APPLY_HOST_BUFFERS.  Each column has its own Krylov space; the columns
  * run in lockstep and share every link load of the stencil.  rep may be NULL.
  * Returns SGN_ERR_NOT_CONVERGED (x holds the last iterate) if max_cycles is hit.
- * Errors: SGN_ERR_STATE (no gauge / rational function), SGN_ERR_ARG, SGN_ERR_CUDA. */
+ * Errors: SGN_ERR_STATE (no gauge / rational function, or deflation data dropped
+ * by a change of the operator), SGN_ERR_ARG, SGN_ERR_NONFINITE (NaN or Inf in host
+ * b, or met in the iteration), SGN_ERR_BREAKDOWN (a shifted Hessenberg system
+ * (H_k - sigma_i) was singular: a shift on a Ritz value), SGN_ERR_CUDA. */
 SGN_API int sgn_apply(sgn_ctx* ctx, const double* b, double* x, int nrhs, int flags, sgn_report* rep);
 
 /* As sgn_apply, and also return the iterate of every shifted system,
@@ -293,10 +307,12 @@ SGN_API int sgn_unpack_fields(sgn_ctx* ctx, const void* in, void* out, int nfiel
 SGN_API int sgn_inner_products(sgn_ctx* ctx, const double* V, int J, const double* w, int nrhs, double* out);
 
 /* The inner products of sgn_inner_products, for callers that cannot allocate
- * device memory: code running while its stream is being captured into a CUDA
- * graph, host callbacks, or frameworks that own every device allocation.  (The
- * paper has no counterpart; this is a deployment variant of the Gram-Schmidt
- * and projection inner products above.)
+ * device memory: applications whose framework owns every device allocation (a
+ * fixed arena sized up front, where an outside cudaMalloc is forbidden or would
+ * exceed the budget), and latency-critical loops that must not pay for
+ * cudaMalloc/cudaFree, which can synchronise the device.  (The paper has no
+ * counterpart; this is a deployment variant of the Gram-Schmidt and projection
+ * inner products above.)
  *   V: J complex128 device fields of n complex numbers each, back to back;
  *   w: nrhs complex128 device fields; out: DEVICE array of nrhs*J complex128,
  *   out[c*J + j] = V_j^dag w_c.  n even, 1 <= J <= 64, 1 <= nrhs <= 512.
@@ -304,10 +320,14 @@ SGN_API int sgn_inner_products(sgn_ctx* ctx, const double* V, int J, const doubl
  * 8 MiB device array inside the library (held on every device that loads the
  * library until the process exits).  The call is rejected (SGN_ERR_ARG) when
  * nrhs * J * ceil(n / 1024) * 16 bytes exceeds 8 MiB.  The first call on a device
- * looks up the array's device address; make that first call before any stream
- * capture.  All calls share the array: calls that overlap on the GPU (other
- * streams or threads) race and must be serialised by the caller.  Work is
- * queued on `stream` (a cudaStream_t); the call does not synchronise. */
+ * looks up the array's device address (with that device current) and keeps it
+ * for the life of the process; make that first call before any stream capture.
+ * A device reset (cudaDeviceReset) reloads the library's device code and makes
+ * the kept address stale: do not use this entry point after resetting a device.
+ * All calls share the array and each call clears the part that must start at
+ * zero: calls that overlap on the GPU (other streams or threads) race and must
+ * be serialised by the caller.  Work is queued on `stream` (a cudaStream_t); the
+ * call does not synchronise. */
 SGN_API int sgn_inner_products_noalloc(const double* V, int J, const double* w, long long n, int nrhs, double* out,
                                        void* stream);
 
@@ -330,6 +350,16 @@ SGN_API int sgn_dhw_dmu_apply(sgn_ctx* ctx, const double* in, double* out, int n
  * lambda_j^2.  With m = 0 only the first sum remains.
  * b, g: nrhs complex128 device fields; dmu: host array of nrhs doubles. */
 SGN_API int sgn_grad_mu(sgn_ctx* ctx, const double* b, const double* g, int nrhs, double* dmu);
+
+/* Diagnostic: the Hessenberg matrix H_k of the Arnoldi relation (eq. (2.4)) on A^2,
+ * as the last restart cycle of the last FP64-form sgn_apply / sgn_apply_shifts of
+ * this context left it, for column `col`: H receives (k+1) x k complex128 entries,
+ * row-major (entry (i, j) at 2 (i k + j)), k the restart length of that solve;
+ * k_used (may be NULL) the Arnoldi steps that cycle took (below k after an
+ * invariant subspace).  At mu = 0, A^2 is Hermitian and H_k is tridiagonal up to
+ * rounding (the Lanczos case of Sec. 2).  Synchronises the stream.
+ * Errors: SGN_ERR_STATE (no FP64-form solve yet), SGN_ERR_ARG. */
+SGN_API int sgn_get_hessenberg(sgn_ctx* ctx, int col, double* H, int* k_used);
 
 /* Kernel timing (observability).  With on = 1, later solves record CUDA events
  * around every launch of the restart cycle's main kernels, inside the captured

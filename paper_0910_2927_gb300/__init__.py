@@ -67,6 +67,11 @@ class SignContext:
         self._h = h
         self.s = 0
         self.m = 0
+        self.mu = None
+        self._build_args = None       # (m, extra, eig_tol) of the last sgn_build_deflation
+        # SignApply: when its mu differs from the context's and deflation data are present,
+        # rebuild them at the new mu (True) or refuse (False, the default)
+        self.rebuild_deflation_on_mu_change = False
         self.set_mu(mu)
         self.set_kernel_mass(mass)
         self.set_boundary(antiperiodic)
@@ -90,16 +95,35 @@ class SignContext:
         self.close()
 
     # -- parameters ----------------------------------------------------------
-    def set_mu(self, mu):
-        self.mu = float(mu)
+    def set_mu(self, mu, rebuild_deflation=False):
+        """A new mu drops deflation data (the solves then refuse with SGN_ERR_STATE until
+        they are built, set or cleared); rebuild_deflation=True rebuilds them at the new mu
+        with the arguments of the last build_deflation call."""
+        mu = float(mu)
+        changed = mu != self.mu
+        args = self._build_args if (rebuild_deflation and self.m > 0) else None
+        if rebuild_deflation and self.m > 0 and args is None:
+            raise ValueError("rebuild_deflation: the deflation data were set, not built; set them again instead")
+        self.mu = mu
         check(lib().sgn_set_mu(self._h, self.mu))
+        if changed:
+            self.m = 0
+            if args is not None:
+                self.build_deflation(*args)
 
     def set_kernel_mass(self, m_w):
-        self.mass = float(m_w)
+        m_w = float(m_w)
+        if m_w != getattr(self, "mass", None):
+            self.m = 0
+        self.mass = m_w
         check(lib().sgn_set_kernel_mass(self._h, self.mass))
 
     def set_boundary(self, antiperiodic):
-        check(lib().sgn_set_boundary(self._h, (C.c_int * 4)(*[int(a) for a in antiperiodic])))
+        ap = tuple(int(bool(a)) for a in antiperiodic)
+        if ap != getattr(self, "antiperiodic", None):
+            self.m = 0
+        self.antiperiodic = ap
+        check(lib().sgn_set_boundary(self._h, (C.c_int * 4)(*ap)))
 
     def set_rational(self, sigma, omega):
         sig = np.ascontiguousarray(sigma, dtype=np.float64)
@@ -108,6 +132,7 @@ class SignContext:
         self.s = sig.size
 
     def set_restart(self, k=40, tol=1e-10, max_cycles=1000, project_each_cycle=True):
+        self.k = int(k)
         check(lib().sgn_set_restart(self._h, int(k), float(tol), int(max_cycles), int(bool(project_each_cycle))))
 
     def set_precision(self, precision=PREC_FP64, target_rel_err=1e-8, link_storage=LINKS_FP32):
@@ -141,6 +166,7 @@ class SignContext:
         if size != self.vol * 36:
             raise ValueError(f"links must hold V*36 = {self.vol * 36} complex entries, got {size}")
         check(lib().sgn_load_gauge(self._h, C.c_void_p(ptr), on_dev))
+        self.m = 0
 
     def set_deflation(self, R, L, lam, extra=None):
         """R, L: (n, m) right / left eigenvectors with L^dag R = I; lam: (m,) eigenvalues.
@@ -152,6 +178,7 @@ class SignContext:
             return
         self._set_pairs(lib().sgn_set_deflation, R, L, lam)
         self.m = R.shape[1]
+        self._build_args = None
         if extra is not None:
             self._set_pairs(lib().sgn_set_deflation_extra, *extra)
 
@@ -181,6 +208,7 @@ class SignContext:
         lam = np.empty(m + extra, dtype=np.complex128)
         check(lib().sgn_build_deflation(self._h, int(m), int(extra), float(eig_tol), lam.ctypes.data))
         self.m = m
+        self._build_args = (int(m), int(extra), float(eig_tol))
         return lam
 
     def get_deflation(self):
@@ -235,6 +263,15 @@ class SignContext:
         if code not in (0, 3):
             check(code)
         return (x.reshape(-1) if squeeze else x), rep.as_dict()
+
+    def hessenberg(self, col=0, k=None):
+        """H_k of the last restart cycle of the last FP64-form solve, column col: ((k+1), k)
+        complex128 array, and the Arnoldi steps that cycle took (sgn_get_hessenberg)."""
+        kk = C.c_int(0)
+        k = getattr(self, "k", 40) if k is None else int(k)
+        H = np.empty((k + 1, k), dtype=np.complex128)
+        check(lib().sgn_get_hessenberg(self._h, int(col), H.ctypes.data, C.byref(kk)))
+        return H, kk.value
 
     def inner_products(self, V, w):
         """<V_j, w_c> for J CUDA fields V (J, n) and nrhs CUDA fields w (nrhs, n): shape (nrhs, J)."""

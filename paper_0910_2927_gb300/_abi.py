@@ -66,6 +66,7 @@ SIGNATURES = {
     "sgn_inner_products_noalloc": (C.c_int, [P, C.c_int, P, C.c_longlong, C.c_int, P, P]),
     "sgn_dhw_dmu_apply": (C.c_int, [P, P, P, C.c_int]),
     "sgn_grad_mu": (C.c_int, [P, P, P, C.c_int, P]),
+    "sgn_get_hessenberg": (C.c_int, [P, C.c_int, P, C.POINTER(C.c_int)]),
     "sgn_set_kernel_timing": (C.c_int, [P, C.c_int]),
     "sgn_get_kernel_timing": (C.c_int, [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
                                         C.POINTER(C.c_double)]),

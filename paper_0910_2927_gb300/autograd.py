@@ -19,16 +19,31 @@ import torch
 from ._abi import APPLY_ADJOINT, check, lib
 
 
+def _use_mu(sctx, mu_v):
+    """Put the context at mu_v.  Deflation data belong to one operator (eq. (4.1)), so a
+    context that holds them moves to another mu only when it was told to rebuild them
+    (sctx.rebuild_deflation_on_mu_change); otherwise the call refuses instead of
+    silently solving undeflated."""
+    if sctx.mu == mu_v:
+        return
+    if sctx.m > 0 and not sctx.rebuild_deflation_on_mu_change:
+        raise ValueError(f"SignApply: mu = {mu_v} differs from the context's mu = {sctx.mu}, whose deflation "
+                         "data would be lost; set sctx.rebuild_deflation_on_mu_change = True to rebuild them "
+                         "at the new mu, or move the context with sctx.set_mu first")
+    sctx.set_mu(mu_v, rebuild_deflation=sctx.m > 0)
+
+
 class SignApply(torch.autograd.Function):
     """x = SignApply.apply(b, mu, ctx): b (nrhs, n) or (n,) complex128 CUDA, mu a real 0-d tensor.
 
-    The context's mu is set from `mu` at every forward call."""
+    When mu differs from the context's mu, the context moves to it: freely without
+    deflation data; with deflation data only if ctx.rebuild_deflation_on_mu_change is
+    set (the data are then rebuilt at the new mu), else ValueError."""
 
     @staticmethod
     def forward(fctx, b, mu, sctx):
         mu_v = float(mu)
-        if sctx.mu != mu_v:
-            sctx.set_mu(mu_v)
+        _use_mu(sctx, mu_v)
         x, _ = sctx.apply(b)
         fctx.sctx = sctx
         fctx.mu = mu_v
@@ -39,8 +54,7 @@ class SignApply(torch.autograd.Function):
     def backward(fctx, gx):
         (b,) = fctx.saved_tensors
         sctx = fctx.sctx
-        if sctx.mu != fctx.mu:
-            sctx.set_mu(fctx.mu)
+        _use_mu(sctx, fctx.mu)
         gb = gmu = None
         g = gx.to(torch.complex128).contiguous()
         if fctx.needs_input_grad[0]:

@@ -55,12 +55,24 @@ struct Session {
     }
 };
 
+// The operator changed: deflation data of the old operator no longer satisfy
+// eq. (4.1).  They are dropped, and if there were any, the solves refuse to run
+// until new data are set or built (or m = 0 is set explicitly).
 int drop_deflation(sgn_ctx* c) {
+    if (c->m > 0) c->deflation_stale = true;
     c->m = 0;
     c->lam.clear();
     c->mx = 0;
     c->lamx.clear();
     return SGN_OK;
+}
+
+// SGN_ERR_STATE while the deflation data belong to an operator that has since changed.
+int check_deflation_current(const sgn_ctx* c, const char* who) {
+    if (!c->deflation_stale) return SGN_OK;
+    return fail(SGN_ERR_STATE, std::string(who) +
+                                   ": the deflation data were dropped when the operator changed (gauge field, mu, "
+                                   "kernel mass or boundary); build or set them again, or set m = 0");
 }
 
 int copy_in(sgn_ctx* c, void* dst, const void* src, size_t bytes, int on_device) {
@@ -283,7 +295,11 @@ SGN_API int sgn_set_refinement(sgn_ctx* c, int k_refine, int max_batch) {
 SGN_API int sgn_set_deflation(sgn_ctx* c, int m, const double* R, const double* L, const double* lambda,
                               int on_device) {
     if (!c || m < 0 || m > 64) return fail(SGN_ERR_ARG, "sgn_set_deflation: need 0 <= m <= 64");
-    if (m == 0) return drop_deflation(c);
+    if (m == 0) {
+        drop_deflation(c);
+        c->deflation_stale = false;  // an explicit choice of no deflation
+        return SGN_OK;
+    }
     if (!R || !L || !lambda) return fail(SGN_ERR_ARG, "sgn_set_deflation: NULL argument");
     const size_t cnt = (size_t)c->n * m;
     std::vector<double> lam(2 * (size_t)m);
@@ -319,6 +335,7 @@ SGN_API int sgn_set_deflation(sgn_ctx* c, int m, const double* R, const double* 
     c->lam.resize(m);
     for (int j = 0; j < m; ++j) c->lam[j] = {lam[2 * j], lam[2 * j + 1]};
     c->m = m;
+    c->deflation_stale = false;
     return SGN_OK;
 }
 
@@ -397,6 +414,7 @@ int apply_common(sgn_ctx* c, const double* b, double* x, double* x_shift, int nr
     if (!c || !b || !x || nrhs < 1) return fail(SGN_ERR_ARG, "sgn_apply: bad argument");
     if (!c->have_gauge) return fail(SGN_ERR_STATE, "sgn_apply: load the gauge field first");
     if (c->sigma.empty()) return fail(SGN_ERR_STATE, "sgn_apply: set the rational function first");
+    SGN_CHECK(check_deflation_current(c, "sgn_apply"));
     if (x_shift && (flags & SGN_APPLY_HOST_BUFFERS))
         return fail(SGN_ERR_ARG, "sgn_apply_shifts: per-shift output needs device buffers");
     const bool host = flags & SGN_APPLY_HOST_BUFFERS;
@@ -506,6 +524,7 @@ SGN_API int sgn_hw_apply(sgn_ctx* c, const void* in, void* out, int nrhs, int pr
 SGN_API int sgn_overlap_apply(sgn_ctx* c, const double* b, double* y, int nrhs) {
     if (!c || !b || !y || nrhs < 1 || b == y) return fail(SGN_ERR_ARG, "sgn_overlap_apply: bad argument");
     if (!c->have_gauge || c->sigma.empty()) return fail(SGN_ERR_STATE, "sgn_overlap_apply: gauge field and rational function needed");
+    SGN_CHECK(check_deflation_current(c, "sgn_overlap_apply"));
     SGN_CHECK(enter(c));
     Session ses(c);
     const size_t nn = (size_t)c->n * nrhs;
@@ -523,6 +542,7 @@ SGN_API int sgn_overlap_solve(sgn_ctx* c, const double* b, double* x, int nrhs, 
     if (!c || !b || !x || nrhs < 1 || b == x || !(tol > 0) || k < 1 || k > 64 || max_restarts < 0)
         return fail(SGN_ERR_ARG, "sgn_overlap_solve: need tol > 0, 1 <= k <= 64, max_restarts >= 0");
     if (!c->have_gauge || c->sigma.empty()) return fail(SGN_ERR_STATE, "sgn_overlap_solve: gauge field and rational function needed");
+    SGN_CHECK(check_deflation_current(c, "sgn_overlap_solve"));
     SGN_CHECK(enter(c));
     Session ses(c);
     const size_t nn = (size_t)c->n * nrhs;
@@ -542,6 +562,7 @@ SGN_API int sgn_apply_direct(sgn_ctx* c, const double* b, double* x, int nrhs, i
         return fail(SGN_ERR_ARG, "sgn_apply_direct: need b != x, nrhs >= 1, 1 <= k <= 4096");
     if (flags & ~SGN_APPLY_ADJOINT) return fail(SGN_ERR_ARG, "sgn_apply_direct: unknown flag");
     if (!c->have_gauge) return fail(SGN_ERR_STATE, "sgn_apply_direct: load the gauge field first");
+    SGN_CHECK(check_deflation_current(c, "sgn_apply_direct"));
     SGN_CHECK(enter(c));
     Session ses(c);
     const size_t nn = (size_t)c->n * nrhs;
@@ -610,6 +631,7 @@ SGN_API int sgn_grad_mu(sgn_ctx* c, const double* b, const double* g, int nrhs, 
     if (!c || !b || !g || !dmu || nrhs < 1) return fail(SGN_ERR_ARG, "sgn_grad_mu: bad argument");
     if (!c->have_gauge || c->sigma.empty()) return fail(SGN_ERR_STATE, "sgn_grad_mu: gauge field and rational function needed");
     if (c->form != SGN_FORM_A2) return fail(SGN_ERR_STATE, "sgn_grad_mu: needs the A^2 formulation (per-shift iterates)");
+    SGN_CHECK(check_deflation_current(c, "sgn_grad_mu"));
     SGN_CHECK(enter(c));
     Session ses(c);
     const size_t nn = (size_t)c->n * nrhs;
@@ -653,6 +675,25 @@ SGN_API int sgn_inner_products(sgn_ctx* c, const double* V, int J, const double*
             out[2 * ((size_t)col * J + j)] = h[(size_t)col * rs + j].x;
             out[2 * ((size_t)col * J + j) + 1] = h[(size_t)col * rs + j].y;
         }
+    return SGN_OK;
+}
+
+SGN_API int sgn_get_hessenberg(sgn_ctx* c, int col, double* H, int* k_used) {
+    if (!c || col < 0) return fail(SGN_ERR_ARG, "sgn_get_hessenberg: bad argument");
+    Engine* E = c->last_fp64;
+    if (!E) return fail(SGN_ERR_STATE, "sgn_get_hessenberg: no FP64-form solve has run");
+    if (col >= E->ncol) return fail(SGN_ERR_ARG, "sgn_get_hessenberg: column out of range");
+    const int km = E->S.kmax;
+    SGN_CHECK(enter(c));
+    Session ses(c);
+    int kk = 0;
+    SGN_CUDA(cudaMemcpyAsync(&kk, E->S.kk + col, sizeof(int), cudaMemcpyDeviceToHost, c->work));
+    if (H)
+        SGN_CUDA(cudaMemcpyAsync(H, E->S.H + (size_t)col * (km + 1) * km, sizeof(double2) * (size_t)(km + 1) * km,
+                                 cudaMemcpyDeviceToHost, c->work));
+    SGN_CUDA(cudaStreamSynchronize(c->work));
+    SGN_CHECK(ses.close());
+    if (k_used) *k_used = kk;
     return SGN_OK;
 }
 

@@ -96,6 +96,10 @@ struct sgn_ctx {
 
     // deflation (R, L as n x m column blocks)
     int m = 0;
+    // set when a change of the operator (gauge field, mu, m_W, boundary) dropped
+    // deflation data: the solves refuse (SGN_ERR_STATE) until deflation is set,
+    // built or explicitly cleared (m = 0) again
+    bool deflation_stale = false;
     sgn::DevBuf R64, L64, R32, L32, lam_dev, lamc_dev;
     std::vector<std::complex<double>> lam;
     // the next mx eigenpairs beyond the deflated ones (biorthonormal to them): not
@@ -106,6 +110,8 @@ struct sgn_ctx {
 
     // engines keyed by configuration
     std::map<uint64_t, std::unique_ptr<sgn::Engine>> engines;
+    // engine of the last FP64-form multishift solve (sgn_get_hessenberg reads its H_k)
+    sgn::Engine* last_fp64 = nullptr;
     // scratch fields for apply (b copy, x accumulators, FP64 temporaries)
     sgn::DevBuf io;
     sgn::DevBuf stage;  // device staging of host b / x

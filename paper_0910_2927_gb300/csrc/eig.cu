@@ -62,9 +62,12 @@ struct Work {
     double2* coef = nullptr;   // q x rstride per-column coefficients
     std::vector<double2> hred;
     double beta = 0;           // imaginary semi-axis of the filter ellipse
+    // the polynomial filter is too weak for this spectrum (the ellipse enclosing the
+    // unwanted eigenvalues of A^2 comes too close to the wanted ones): set by iterate()
+    bool weak = false;
 };
 
-int setup(Work& W, sgn_ctx* c, int q, size_t esz, int nblk) {
+int setup(Work& W, sgn_ctx* c, int q, size_t esz, int nblk, int nblocks = 5) {
     W.c = c;
     W.q = q;
     W.n = c->n;
@@ -77,8 +80,8 @@ int setup(Work& W, sgn_ctx* c, int q, size_t esz, int nblk) {
         off += (b + 255) & ~size_t(255);
         return o;
     };
-    size_t ob[5];
-    for (int i = 0; i < 5; ++i) ob[i] = take(blkb);
+    size_t ob[5] = {};
+    for (int i = 0; i < nblocks; ++i) ob[i] = take(blkb);
     size_t op = take((size_t)q * W.rstride * nblk * sizeof(double2));
     size_t ored = take((size_t)q * W.rstride * sizeof(double2));
     size_t oc = take((size_t)q * q * sizeof(double2));
@@ -86,7 +89,7 @@ int setup(Work& W, sgn_ctx* c, int q, size_t esz, int nblk) {
     size_t oint = take((size_t)3 * q * sizeof(int));
     SGN_CHECK(dev_alloc(c, W.buf, off));
     char* b = reinterpret_cast<char*>(W.buf.p);
-    for (int i = 0; i < 5; ++i) W.blk[i] = b + ob[i];
+    for (int i = 0; i < 5; ++i) W.blk[i] = i < nblocks ? b + ob[i] : nullptr;
     W.partial = reinterpret_cast<double2*>(b + op);
     W.S.red = reinterpret_cast<double2*>(b + ored);
     W.Cdev = reinterpret_cast<double2*>(b + oc);
@@ -237,47 +240,68 @@ int filter(Work& W, bool adj, T* Y, double a, double b, int deg) {
 
 // Largest |Im theta| over the Ritz values of K Arnoldi steps on A^2 (CGS2,
 // one random start field): an estimate of the imaginary extent of the
-// spectrum of A^2, whose outer boundary Arnoldi resolves first.  Scratch:
-// blocks 1 (the K + 1 basis fields), 3 and 4.
+// spectrum of A^2, whose outer boundary Arnoldi resolves first.  The estimate
+// falls short on large lattices when K is small (40 steps: 0.135 against a true
+// height near 0.9 at 24^4, mu = 0.2; 200 steps recover most of it), and an
+// ellipse that is too flat lets bulk eigenvalues outgrow the wanted ones, so K
+// is 200 (or n - 1).  The basis lives in its own allocation (K + 1 fields of T);
+// Gram-Schmidt runs in chunks of at most 96 basis vectors (the reduction's slots).
 template <class T>
 int spectrum_height2(Work& W, bool adj, int K, uint64_t seed, double* height) {
     cudaStream_t st = W.c->work;
     const int64_t n = W.n;
-    K = std::min(K, W.q - 1);
-    T* V = reinterpret_cast<T*>(W.blk[1]);
+    K = (int)std::min<int64_t>(K, n - 1);
+    DevBuf vb;
+    SGN_CHECK(dev_alloc(W.c, vb, sizeof(T) * (size_t)(K + 1) * n));
+    T* V = reinterpret_cast<T*>(vb.p);
     T* w = reinterpret_cast<T*>(W.blk[3]);
     T* t = reinterpret_cast<T*>(W.blk[4]);
+    constexpr int CH = 96;
     std::vector<cd> Hh((size_t)K * K, 0.0), G;
-    SGN_CUDA(random_fill<T>(V, n, seed, st));
-    SGN_CHECK(gram<T>(W, V, 1, V, 1, G));
-    SGN_CUDA(axpby3<T>(V, 1.0 / std::sqrt(G[0].real()), V, 0.0, V, 0.0, nullptr, n, st));
     int k = K;
-    for (int j = 0; j < K; ++j) {
-        T* vj = V + (size_t)j * n;
-        T* vn = V + (size_t)(j + 1) * n;
-        SGN_CUDA(hw<T>(W.c, t, vj, 1, adj, st));
-        SGN_CUDA(hw<T>(W.c, w, t, 1, adj, st));
-        // two classical Gram-Schmidt passes against v_0..v_j
-        std::vector<cd> h;
-        SGN_CHECK(gram<T>(W, V, j + 1, w, 1, h));
-        SGN_CHECK(combine<T>(W, V, j + 1, h, 1, t));
-        SGN_CUDA(axpby3<T>(vn, 1.0, w, -1.0, t, 0.0, nullptr, n, st));
-        std::vector<cd> h2;
-        SGN_CHECK(gram<T>(W, V, j + 1, vn, 1, h2));
-        SGN_CHECK(combine<T>(W, V, j + 1, h2, 1, t));
-        SGN_CUDA(axpby3<T>(w, 1.0, vn, -1.0, t, 0.0, nullptr, n, st));
-        for (int i = 0; i <= j; ++i) Hh[(size_t)i * K + j] = h[i] + h2[i];
-        SGN_CHECK(gram<T>(W, w, 1, w, 1, G));
-        const double nrm = std::sqrt(std::max(G[0].real(), 0.0));
-        double hn = 0;
-        for (int i = 0; i <= j; ++i) hn += std::norm(Hh[(size_t)i * K + j]);
-        if (!(nrm > 1e-10 * std::sqrt(hn))) {  // invariant subspace: the Ritz values are exact
-            k = j + 1;
-            break;
+    auto body = [&]() -> int {
+        SGN_CUDA(random_fill<T>(V, n, seed, st));
+        SGN_CHECK(gram<T>(W, V, 1, V, 1, G));
+        SGN_CUDA(axpby3<T>(V, 1.0 / std::sqrt(G[0].real()), V, 0.0, V, 0.0, nullptr, n, st));
+        for (int j = 0; j < K; ++j) {
+            T* vj = V + (size_t)j * n;
+            T* vn = V + (size_t)(j + 1) * n;
+            SGN_CUDA(hw<T>(W.c, t, vj, 1, adj, st));
+            SGN_CUDA(hw<T>(W.c, w, t, 1, adj, st));
+            // two classical Gram-Schmidt passes against v_0..v_j: all coefficients of a pass
+            // from the same vector, subtracted chunk by chunk
+            for (int pass = 0; pass < 2; ++pass) {
+                std::vector<cd> h(j + 1), hc;
+                for (int c0 = 0; c0 <= j; c0 += CH) {
+                    const int nc = std::min(CH, j + 1 - c0);
+                    SGN_CHECK(gram<T>(W, V + (size_t)c0 * n, nc, w, 1, hc));
+                    for (int i = 0; i < nc; ++i) h[c0 + i] = hc[i];
+                }
+                for (int c0 = 0; c0 <= j; c0 += CH) {
+                    const int nc = std::min(CH, j + 1 - c0);
+                    std::vector<cd> hs(h.begin() + c0, h.begin() + c0 + nc);
+                    SGN_CHECK(combine<T>(W, V + (size_t)c0 * n, nc, hs, 1, t));
+                    SGN_CUDA(axpby3<T>(w, 1.0, w, -1.0, t, 0.0, nullptr, n, st));
+                }
+                for (int i = 0; i <= j; ++i) Hh[(size_t)i * K + j] += h[i];
+            }
+            SGN_CHECK(gram<T>(W, w, 1, w, 1, G));
+            const double nrm = std::sqrt(std::max(G[0].real(), 0.0));
+            double hn = 0;
+            for (int i = 0; i <= j; ++i) hn += std::norm(Hh[(size_t)i * K + j]);
+            if (!(nrm > 1e-10 * std::sqrt(hn))) {  // invariant subspace: the Ritz values are exact
+                k = j + 1;
+                break;
+            }
+            if (j + 1 < K) Hh[(size_t)(j + 1) * K + j] = nrm;
+            SGN_CUDA(axpby3<T>(vn, 1.0 / nrm, w, 0.0, w, 0.0, nullptr, n, st));
         }
-        if (j + 1 < K) Hh[(size_t)(j + 1) * K + j] = nrm;
-        SGN_CUDA(axpby3<T>(vn, 1.0 / nrm, w, 0.0, w, 0.0, nullptr, n, st));
-    }
+        return SGN_OK;
+    };
+    const int rc = body();
+    SGN_CUDA(cudaStreamSynchronize(st));
+    dev_free(W.c, vb);
+    SGN_CHECK(rc);
     std::vector<cd> Hk((size_t)k * k);
     for (int i = 0; i < k; ++i)
         for (int j = 0; j < k; ++j) Hk[(size_t)i * k + j] = Hh[(size_t)i * K + j];
@@ -422,14 +446,15 @@ int iterate(Work& W, bool adj, T* Y, int want, double tol, int max_it, Ritz& rz,
             *its = it;
             return SGN_OK;
         }
-        if (stop_on_stall) {
-            if (worst < 0.5 * best) {
-                best = worst;
-                stall = 0;
-            } else if (++stall >= 2) {
-                *its = it;
-                return SGN_OK;
-            }
+        if (worst < 0.5 * best) {
+            best = worst;
+            stall = 0;
+        } else if (++stall >= (stop_on_stall ? 2 : 8)) {
+            *its = it;
+            if (stop_on_stall) return SGN_OK;
+            W.weak = true;
+            set_error("deflation set-up: the polynomial filter stalled");
+            return SGN_ERR_DEFLATION;
         }
         // Ritz values are eigenvalue estimates of A^2: |theta| ~ |lambda|^2.  The
         // degree aims at an amplification of the wanted edge tw, capped so that the
@@ -474,6 +499,286 @@ int svqb_final(Work& W, double2* F, int want, bool adj, Ritz& ra) {
     return rayleigh_ritz<double2>(W, adj, false, F, want, ra);
 }
 
+// ---- shift-invert Arnoldi ------------------------------------------------------
+// Where the unwanted eigenvalues of A^2 nearly surround the wanted ones (strongly
+// non-Hermitian A: at mu = 1 they lie on three sides of the disc |z| < |lambda_m+1|^2),
+// no polynomial in A^2 separates them: the filter stalls, and a Krylov solver for
+// A^2 (restarted GMRES) stagnates for the same reason.  The eigenvalues of smallest
+// modulus of A are the largest of A^{-1}, well separated from the rest: Arnoldi on
+// A^{-1} with thick restarts (the Ritz vectors of the wanted values are kept, a
+// Krylov decomposition in Stewart's sense), every A^{-1} v by CGLS -- conjugate
+// gradients on the normal equations A^dag A x = A^dag v, which converge for any
+// eigenvalue distribution at a rate set by sigma_max / sigma_min of A.
+
+struct CglsVecs {
+    double2 *x, *r, *s, *p, *q;  // r and s adjacent (one Gram call gives both norms)
+};
+
+// x = A^{-1} b (A^dag with adj) until ||b - A x|| <= tol ||b|| or max_it steps.
+int cgls(Work& W, bool adj, const double2* b, const CglsVecs& v, double tol, int max_it, int* its, double* relres) {
+    sgn_ctx* c = W.c;
+    cudaStream_t st = c->work;
+    const int64_t n = W.n;
+    std::vector<cd> G;
+    SGN_CHECK(gram<double2>(W, b, 1, b, 1, G));
+    const double bn = std::sqrt(std::max(G[0].real(), 0.0));
+    SGN_CUDA(cudaMemsetAsync(v.x, 0, sizeof(double2) * n, st));
+    *its = 0;
+    *relres = 0;
+    if (!(bn > 0)) return SGN_OK;
+    SGN_CUDA(cudaMemcpyAsync(v.r, b, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
+    SGN_CUDA(apply_hw64(c, v.s, v.r, 1, !adj, nullptr, st));  // s = A^dag r (H_W(mu)^dag = H_W(-mu))
+    SGN_CUDA(cudaMemcpyAsync(v.p, v.s, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
+    SGN_CHECK(gram<double2>(W, v.s, 1, v.s, 1, G));
+    double gamma = G[0].real();
+    double rn = bn;
+    int it = 0;
+    while (it < max_it) {
+        SGN_CUDA(apply_hw64(c, v.q, v.p, 1, adj, nullptr, st));  // q = A p
+        SGN_CHECK(gram<double2>(W, v.q, 1, v.q, 1, G));
+        const double delta = G[0].real();
+        if (!(delta > 0) || !std::isfinite(delta)) break;
+        const double alpha = gamma / delta;
+        SGN_CUDA(axpby3<double2>(v.x, 1.0, v.x, alpha, v.p, 0.0, nullptr, n, st));
+        SGN_CUDA(axpby3<double2>(v.r, 1.0, v.r, -alpha, v.q, 0.0, nullptr, n, st));
+        SGN_CUDA(apply_hw64(c, v.s, v.r, 1, !adj, nullptr, st));
+        SGN_CHECK(gram<double2>(W, v.r, 2, v.r, 2, G));
+        ++it;
+        rn = std::sqrt(std::max(G[0].real(), 0.0));
+        const double gnew = G[3].real();
+        if (rn <= tol * bn) break;
+        const double beta = gnew / gamma;
+        gamma = gnew;
+        SGN_CUDA(axpby3<double2>(v.p, 1.0, v.s, beta, v.p, 0.0, nullptr, n, st));
+    }
+    *its = it;
+    *relres = rn / bn;
+    return SGN_OK;
+}
+
+// Orthonormalise the columns of the p x k host matrix Y (row-major) in place by
+// two classical Gram-Schmidt passes.
+void orth_host(int p, int k, std::vector<cd>& Y) {
+    for (int j = 0; j < k; ++j)
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int l = 0; l < j; ++l) {
+                cd h = 0;
+                for (int i = 0; i < p; ++i) h += std::conj(Y[(size_t)i * k + l]) * Y[(size_t)i * k + j];
+                for (int i = 0; i < p; ++i) Y[(size_t)i * k + j] -= h * Y[(size_t)i * k + l];
+            }
+            double nr = 0;
+            for (int i = 0; i < p; ++i) nr += std::norm(Y[(size_t)i * k + j]);
+            nr = std::sqrt(nr);
+            for (int i = 0; i < p; ++i) Y[(size_t)i * k + j] /= nr;
+        }
+}
+
+// The `want` eigenvectors of A (A^dag with adj) of smallest |lambda| into out
+// (want FP64 fields, unit norm, not yet split by a Rayleigh-Ritz step with A):
+// Ritz vectors of A^{-1} whose relative residual ||A^{-1} y - theta y|| / |theta|
+// is below tolB.
+int inverse_arnoldi(sgn_ctx* c, bool adj, int want, double tolB, uint64_t seed, double2* out) {
+    cudaStream_t st = c->work;
+    const int64_t n = c->n;
+    const int pmax = std::min(100, std::max(want + 24, 2 * want));
+    const int keep = std::min(pmax - 12, want + (pmax - want) / 2);
+    const double inner = std::max(1e-14, 0.1 * tolB);
+    Work W;
+    SGN_CHECK(setup(W, c, pmax + 1, sizeof(double2), reduce_blocks<double2>(n), 2));
+    DevBuf cb;
+    int rc = dev_alloc(c, cb, sizeof(double2) * (size_t)n * 5);
+    if (rc != SGN_OK) {
+        dev_free(c, W.buf);
+        return rc;
+    }
+    double2* V = reinterpret_cast<double2*>(W.blk[0]);
+    double2* T = reinterpret_cast<double2*>(W.blk[1]);
+    double2* cbp = reinterpret_cast<double2*>(cb.p);
+    const CglsVecs cv{cbp, cbp + n, cbp + 2 * n, cbp + 3 * n, cbp + 4 * n};
+    auto fail_out = [&](int code) {
+        dev_free(c, cb);
+        dev_free(c, W.buf);
+        return code;
+    };
+#define INV_CHECK(call)                    \
+    do {                                   \
+        int _r = (call);                   \
+        if (_r != SGN_OK) return fail_out(_r); \
+    } while (0)
+#define INV_CUDA(call)                                                                  \
+    do {                                                                                \
+        cudaError_t _e = (call);                                                        \
+        if (_e != cudaSuccess) {                                                        \
+            set_error(std::string("deflation set-up: ") + cudaGetErrorString(_e));      \
+            return fail_out(SGN_ERR_CUDA);                                              \
+        }                                                                               \
+    } while (0)
+    std::vector<cd> G, h1, h2;
+    INV_CUDA(random_fill<double2>(V, n, seed, st));
+    INV_CHECK(gram<double2>(W, V, 1, V, 1, G));
+    INV_CUDA(axpby3<double2>(V, 1.0 / std::sqrt(G[0].real()), V, 0.0, V, 0.0, nullptr, n, st));
+    std::vector<cd> H((size_t)(pmax + 1) * pmax, 0.0);  // Krylov decomposition A^{-1} V_p = V_{p+1} H
+    int k = 0;
+    const int max_cg = 20000;
+    long long cg_total = 0;
+    for (int restart = 0; restart < 60; ++restart) {
+        for (int j = k; j < pmax; ++j) {
+            double2* vj = V + (size_t)j * n;
+            int its = 0;
+            double rel = 0;
+            INV_CHECK(cgls(W, adj, vj, cv, inner, max_cg, &its, &rel));
+            cg_total += its;
+            if (!(rel <= 100 * inner)) {
+                set_error("deflation set-up: CGLS for A^{-1} did not converge (relative residual " +
+                          std::to_string(rel) + ")");
+                return fail_out(SGN_ERR_DEFLATION);
+            }
+            double2* w = cv.x;
+            // two classical Gram-Schmidt passes against v_0 .. v_j
+            INV_CHECK(gram<double2>(W, V, j + 1, w, 1, h1));
+            INV_CHECK(combine<double2>(W, V, j + 1, h1, 1, T));
+            INV_CUDA(axpby3<double2>(w, 1.0, w, -1.0, T, 0.0, nullptr, n, st));
+            INV_CHECK(gram<double2>(W, V, j + 1, w, 1, h2));
+            INV_CHECK(combine<double2>(W, V, j + 1, h2, 1, T));
+            INV_CUDA(axpby3<double2>(w, 1.0, w, -1.0, T, 0.0, nullptr, n, st));
+            for (int i = 0; i <= j; ++i) H[(size_t)i * pmax + j] += h1[i] + h2[i];
+            INV_CHECK(gram<double2>(W, w, 1, w, 1, G));
+            const double nrm = std::sqrt(std::max(G[0].real(), 0.0));
+            if (!(nrm > 0) || !std::isfinite(nrm)) {
+                set_error("deflation set-up: shift-invert Arnoldi broke down");
+                return fail_out(SGN_ERR_DEFLATION);
+            }
+            H[(size_t)(j + 1) * pmax + j] = nrm;
+            INV_CUDA(axpby3<double2>(V + (size_t)(j + 1) * n, 1.0 / nrm, w, 0.0, w, 0.0, nullptr, n, st));
+        }
+        // Ritz pairs of the p x p top block, largest |theta| first
+        std::vector<cd> Hp((size_t)pmax * pmax), th, X;
+        for (int i = 0; i < pmax; ++i)
+            for (int j = 0; j < pmax; ++j) Hp[(size_t)i * pmax + j] = H[(size_t)i * pmax + j];
+        if (dense_eig(pmax, Hp, th, X)) {
+            set_error("deflation set-up: Arnoldi eigendecomposition failed");
+            return fail_out(SGN_ERR_DEFLATION);
+        }
+        std::vector<int> ord(pmax);
+        std::iota(ord.begin(), ord.end(), 0);
+        std::sort(ord.begin(), ord.end(), [&](int a, int b) { return std::abs(th[a]) > std::abs(th[b]); });
+        // residual of Ritz pair (theta, V y): |h_{p+1,p}| |e_p^T y| / (||y|| |theta|); the
+        // bottom row of H carries the coupling (one entry after an Arnoldi step, a full
+        // row right after a thick restart with no step taken -- never the case here)
+        double worst = 0;
+        const cd* hrow = &H[(size_t)pmax * pmax];
+        for (int t = 0; t < want; ++t) {
+            const int i = ord[t];
+            double yn = 0;
+            cd e = 0;
+            for (int r = 0; r < pmax; ++r) {
+                yn += std::norm(X[(size_t)r * pmax + i]);
+                e += hrow[r] * X[(size_t)r * pmax + i];
+            }
+            worst = std::max(worst, std::abs(e) / (std::sqrt(yn) * std::abs(th[i])));
+        }
+        if (debug_on())
+            fprintf(stderr, "[sgn eig inv %s] restart %d worst %.3e |theta| %.4e..%.4e cgls its %lld\n",
+                    adj ? "left" : "right", restart, worst, std::abs(th[ord[0]]), std::abs(th[ord[want - 1]]),
+                    cg_total);
+        const int nk = worst <= tolB ? want : keep;
+        // Q = orthonormalised Ritz coefficient vectors of the nk largest
+        std::vector<cd> Q((size_t)pmax * nk);
+        for (int r = 0; r < pmax; ++r)
+            for (int t = 0; t < nk; ++t) Q[(size_t)r * nk + t] = X[(size_t)r * pmax + ord[t]];
+        if (worst <= tolB) {  // the Ritz vectors themselves (unit norm)
+            for (int t = 0; t < nk; ++t) {
+                double yn = 0;
+                for (int r = 0; r < pmax; ++r) yn += std::norm(Q[(size_t)r * nk + t]);
+                yn = std::sqrt(yn);
+                for (int r = 0; r < pmax; ++r) Q[(size_t)r * nk + t] /= yn;
+            }
+            INV_CHECK(combine<double2>(W, V, pmax, Q, want, T));
+            INV_CUDA(cudaMemcpyAsync(out, T, sizeof(double2) * (size_t)want * n, cudaMemcpyDeviceToDevice, st));
+            INV_CUDA(cudaStreamSynchronize(st));
+            if (debug_on())
+                fprintf(stderr, "[sgn eig inv] converged after %d restarts, %lld CGLS steps\n", restart, cg_total);
+            dev_free(c, cb);
+            dev_free(c, W.buf);
+            return SGN_OK;
+        }
+        orth_host(pmax, nk, Q);
+        // V_new = V_p Q, v_new[nk] = v_{p}; H_new = [Q^dag H_p Q ; h_{p+1}^T Q]
+        INV_CHECK(combine<double2>(W, V, pmax, Q, nk, T));
+        INV_CUDA(cudaMemcpyAsync(V + (size_t)nk * n, V + (size_t)pmax * n, sizeof(double2) * n,
+                                 cudaMemcpyDeviceToDevice, st));
+        INV_CUDA(cudaMemcpyAsync(V, T, sizeof(double2) * (size_t)nk * n, cudaMemcpyDeviceToDevice, st));
+        std::vector<cd> HQ((size_t)pmax * nk, 0.0), Hn((size_t)(pmax + 1) * pmax, 0.0);
+        for (int i = 0; i < pmax; ++i)
+            for (int t = 0; t < nk; ++t) {
+                cd acc = 0;
+                for (int r = 0; r < pmax; ++r) acc += H[(size_t)i * pmax + r] * Q[(size_t)r * nk + t];
+                HQ[(size_t)i * nk + t] = acc;
+            }
+        for (int a = 0; a < nk; ++a)
+            for (int t = 0; t < nk; ++t) {
+                cd acc = 0;
+                for (int i = 0; i < pmax; ++i) acc += std::conj(Q[(size_t)i * nk + a]) * HQ[(size_t)i * nk + t];
+                Hn[(size_t)a * pmax + t] = acc;
+            }
+        for (int t = 0; t < nk; ++t) {
+            cd acc = 0;
+            for (int r = 0; r < pmax; ++r) acc += hrow[r] * Q[(size_t)r * nk + t];
+            Hn[(size_t)nk * pmax + t] = acc;
+        }
+        H.swap(Hn);
+        k = nk;
+    }
+#undef INV_CHECK
+#undef INV_CUDA
+    set_error("deflation set-up: shift-invert Arnoldi did not converge");
+    return fail_out(SGN_ERR_DEFLATION);
+}
+
+// One side: `want` eigenpairs of A (adj = false) or A^dag (adj = true) into V64 (want fields, FP64).
+// Eigenpairs of A from `want` fields F (FP64, in block 4 of W64) spanning an
+// invariant subspace: one Rayleigh-Ritz step with A; accepted when every relative
+// residual is below tol.
+int finish_side(Work& W64, bool adj, int want, double tol, double2* V64, std::vector<cd>& lam, bool* ok) {
+    sgn_ctx* c = W64.c;
+    double2* F = reinterpret_cast<double2*>(W64.blk[4]);
+    Ritz ra;
+    SGN_CHECK(svqb_final(W64, F, want, adj, ra));
+    double worst = 0;
+    for (int j = 0; j < want; ++j) worst = std::max(worst, ra.res[j]);
+    if (debug_on()) fprintf(stderr, "[sgn eig] eigenpairs of A: worst relative residual %.3e\n", worst);
+    *ok = worst <= tol;
+    if (*ok) {
+        SGN_CUDA(cudaMemcpyAsync(V64, F, sizeof(double2) * want * c->n, cudaMemcpyDeviceToDevice, c->work));
+        SGN_CUDA(cudaStreamSynchronize(c->work));
+        lam = ra.theta;
+    }
+    return SGN_OK;
+}
+
+// The shift-invert route for one side: Arnoldi on A^{-1}, then Rayleigh-Ritz with A.
+int eig_side_inverse(sgn_ctx* c, bool adj, int want, double tol, uint64_t seed, double2* V64, std::vector<cd>& lam) {
+    Work W64;
+    SGN_CHECK(setup(W64, c, want, sizeof(double2), reduce_blocks<double2>(c->n)));
+    double2* F = reinterpret_cast<double2*>(W64.blk[4]);
+    // A-residual of a Ritz pair of A^{-1} with relative residual e is at most
+    // e ||A|| / |lambda|: aim well below tol
+    double tolB = tol / 100;
+    int rc = SGN_OK;
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        rc = inverse_arnoldi(c, adj, want, tolB, seed ^ 0x1f1fULL, F);
+        if (rc != SGN_OK) break;
+        bool ok = false;
+        rc = finish_side(W64, adj, want, tol, V64, lam, &ok);
+        if (rc != SGN_OK || ok) break;
+        tolB /= 100;
+        rc = SGN_ERR_DEFLATION;
+        set_error("deflation set-up: eigenpairs of A did not reach the tolerance");
+    }
+    dev_free(c, W64.buf);
+    return rc;
+}
+
 // One side: `want` eigenpairs of A (adj = false) or A^dag (adj = true) into V64 (want fields, FP64).
 int eig_side(sgn_ctx* c, bool adj, int want, int q, double tol, uint64_t seed, double2* V64, std::vector<cd>& lam) {
     cudaStream_t st = c->work;
@@ -485,7 +790,7 @@ int eig_side(sgn_ctx* c, bool adj, int want, int q, double tol, uint64_t seed, d
     // imaginary extent of the spectrum of A^2, widened by 15 % (Arnoldi Ritz
     // values approach the outer boundary of the spectrum from inside)
     double height = 0;
-    int rc = spectrum_height2<float2>(W, adj, 40, seed ^ 0xa5a5ULL, &height);
+    int rc = spectrum_height2<float2>(W, adj, 200, seed ^ 0xa5a5ULL, &height);
     if (rc != SGN_OK) {
         dev_free(c, W.buf);
         return rc;
@@ -499,6 +804,15 @@ int eig_side(sgn_ctx* c, bool adj, int want, int q, double tol, uint64_t seed, d
         dev_free(c, W.buf);
         return rc;
     }
+    double worst32 = 0;
+    for (int j = 0; j < want; ++j) worst32 = std::max(worst32, rz.res[j]);
+    if (!(worst32 < 0.5)) {
+        // the polynomial filter made no headway: no polynomial in A^2 separates the
+        // wanted eigenvalues here
+        if (debug_on()) fprintf(stderr, "[sgn eig] FP32 filter ended at %.3e: shift-invert Arnoldi\n", worst32);
+        dev_free(c, W.buf);
+        return eig_side_inverse(c, adj, want, tol, seed, V64, lam);
+    }
     Work W64;
     rc = setup(W64, c, q, sizeof(double2), reduce_blocks<double2>(c->n));
     if (rc != SGN_OK) {
@@ -510,22 +824,32 @@ int eig_side(sgn_ctx* c, bool adj, int want, int q, double tol, uint64_t seed, d
     SGN_CUDA(convert_f32_to_f64(Y, Y64, (int64_t)q * c->n, st));
     SGN_CUDA(cudaStreamSynchronize(st));
     dev_free(c, W.buf);
+    if (worst32 <= 10 * tol) {  // a loose tolerance the FP32 phase may already meet
+        double2* F = reinterpret_cast<double2*>(W64.blk[4]);
+        SGN_CUDA(cudaMemcpyAsync(F, Y64, sizeof(double2) * want * c->n, cudaMemcpyDeviceToDevice, st));
+        bool ok = false;
+        rc = finish_side(W64, adj, want, tol, V64, lam, &ok);
+        if (rc != SGN_OK || ok) {
+            dev_free(c, W64.buf);
+            return rc;
+        }
+    }
     // FP64: converge the A^2 subspace, then split it with one Rayleigh-Ritz step on A
     double tol2 = tol / 10;
     for (int attempt = 0; attempt < 4 && rc == SGN_OK; ++attempt) {
         rc = iterate<double2>(W64, adj, Y64, want, tol2, 40, rz, attempt == 0, false, &its);
+        if (rc == SGN_ERR_DEFLATION && W64.weak) {  // the filter stalled: shift-invert instead
+            if (debug_on()) fprintf(stderr, "[sgn eig] FP64 filter stalled: shift-invert Arnoldi\n");
+            dev_free(c, W64.buf);
+            return eig_side_inverse(c, adj, want, tol, seed, V64, lam);
+        }
         if (rc != SGN_OK) break;
         double2* F = reinterpret_cast<double2*>(W64.blk[4]);
         SGN_CUDA(cudaMemcpyAsync(F, Y64, sizeof(double2) * want * c->n, cudaMemcpyDeviceToDevice, st));
-        Ritz ra;
-        rc = svqb_final(W64, F, want, adj, ra);
+        bool ok = false;
+        rc = finish_side(W64, adj, want, tol, V64, lam, &ok);
         if (rc != SGN_OK) break;
-        double worst = 0;
-        for (int j = 0; j < want; ++j) worst = std::max(worst, ra.res[j]);
-        if (worst <= tol) {
-            SGN_CUDA(cudaMemcpyAsync(V64, F, sizeof(double2) * want * c->n, cudaMemcpyDeviceToDevice, st));
-            SGN_CUDA(cudaStreamSynchronize(st));
-            lam = ra.theta;
+        if (ok) {
             dev_free(c, W64.buf);
             return SGN_OK;
         }
@@ -625,6 +949,8 @@ int build_deflation(sgn_ctx* c, int m, int extra, double eig_tol, double* lambda
             return rc;
         }
     }
+    // the inverse iteration's GMRES engines (q columns each) are not needed by the solves
+    release_engines(c);
     // install as the context's deflation data
     const size_t cnt = (size_t)n * m;
     SGN_CHECK(dev_alloc(c, c->R64, cnt * sizeof(double2)));
@@ -657,6 +983,7 @@ int build_deflation(sgn_ctx* c, int m, int extra, double eig_tol, double* lambda
     dev_free(c, RL);
     c->lam.assign(lamR.begin(), lamR.begin() + m);
     c->m = m;
+    c->deflation_stale = false;
     c->mx = mx;
     c->lamx.assign(lamR.begin() + m, lamR.begin() + want);
     if (lambda_out)

@@ -1,8 +1,9 @@
 // sgn_inner_products_noalloc: the inner products of sgn_inner_products for
-// callers that cannot allocate device memory -- code that runs while a stream
-// is being captured into a CUDA graph, inside a host callback, or under a
-// framework that owns every device allocation.  The per-block partial sums
-// live in one file-scope device array instead of memory from an allocator.
+// callers that cannot allocate device memory -- applications under a framework
+// that owns every device allocation (a fixed arena, no outside cudaMalloc), and
+// latency-critical loops that must not pay for cudaMalloc/cudaFree, which can
+// synchronise the device.  The per-block partial sums live in one file-scope
+// device array instead of memory from an allocator.
 #include "blas.cuh"
 
 #include <mutex>
@@ -22,7 +23,9 @@ void* g_scratch_addr[kMaxDevices] = {};
 
 // Device address of the scratch array for the current device.  The host-side
 // name of a __device__ array is only a stand-in, never a device address, so the
-// address is asked for once per device, with that device current.
+// address is asked for once per device, with that device current, on the first
+// call there, and kept for the life of the process (a cudaDeviceReset reloads the
+// module and leaves the kept address stale; the header says so).
 int scratch_address(void** out) {
     int dev = 0;
     SGN_CUDA(cudaGetDevice(&dev));

@@ -541,6 +541,7 @@ void release_engines(sgn_ctx* c) {
         if (E.h_kk) cudaFreeHost(E.h_kk);
     }
     c->engines.clear();
+    c->last_fp64 = nullptr;
 }
 
 namespace {
@@ -1108,6 +1109,7 @@ int solve(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int ncol, 
     a.gmres = gm;
     RunResult rr;
     int status = run_engine<double2>(c, *E, a, c->tol, c->max_cycles, &rr);
+    if (!cshift) c->last_fp64 = E;
     if (status == SGN_OK) {
         SGN_CUDA(cudaMemcpyAsync(x, xacc, field * ncol, cudaMemcpyDeviceToDevice, st));
         if (x_shift && seed == 0) SGN_CUDA(cudaMemcpyAsync(x_shift, xs, field * ncol * s, cudaMemcpyDeviceToDevice, st));

@@ -92,6 +92,29 @@ def test_reference_arm_line_on_rank_zero(monkeypatch):
     assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
     assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    # the steps are real: value x ms_per_step is the work one step did, and the steps ran
+    assert d["value"] * d["ms_per_step"] / 1000.0 == pytest.approx(d["solves_per_step"])
+    # both arms describe the workload with the same config
+    assert d["config"] == bench.bench_config(bench.WORKLOADS["4^4"], "4^4", 1)
+
+
+def test_reference_arm_steps_take_the_time_they_claim(monkeypatch):
+    """ms_per_step x steps is the wall time the timed steps took (within the warm-up's share)."""
+    import json
+    import time
+    import types
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    buf = io.StringIO()
+    t0 = time.perf_counter()
+    with redirect_stdout(buf):
+        bench.reference_arm(types.SimpleNamespace(steps=3, warmup=1), bench.WORKLOADS["4^4"], "4^4")
+    wall = time.perf_counter() - t0
+    d = json.loads(buf.getvalue().strip().splitlines()[-1])
+    assert d["steps"] == 3
+    assert d["ms_per_step"] * d["steps"] / 1000.0 <= wall
 
 
 def test_roofline_entry_arithmetic():

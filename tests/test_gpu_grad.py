@@ -124,3 +124,46 @@ def test_deflated_gradient_matches_dense_daleckii_krein(mu, m):
     gb_ref = F.conj().T @ c
     assert np.linalg.norm(bt.grad.cpu().numpy() - gb_ref) < 1e-9 * np.linalg.norm(gb_ref)
     assert abs(float(mut.grad) - dmu_ref) < 1e-7 * max(1.0, abs(dmu_ref)), (float(mut.grad), dmu_ref)
+
+
+def test_config4_deflated_finite_differences():
+    """6^4, mu = 0.5, m = 20 deflated pairs (4 extra for the reduced resolvents), from the GPU
+    eigensolver at mu and at mu +- h (the context rebuilds them when SignApply or set_mu moves mu).
+    The oracle's central difference, h = 1e-4, of Re<c, x(mu)> with x from its own FOM-LR on the
+    rebuilt pairs (each pair checked against the oracle's stencil), against the GPU's mu-gradient,
+    whose eigenvector-motion terms are what the deflation adds (Sec. 4, eqs. 4.2-4.3)."""
+    import math
+    from paper_0910_2927_gb300.autograd import SignApply
+    import paper_0910_2927_gb300 as pkg
+    dims, mu, h, m = (6, 6, 6, 6), 0.5, 1e-4, 20
+    g_seed, b_seed, c_seed = si.CONFIG_SEEDS[4]
+    U = si.random_su3_links(dims, 0.7, g_seed)
+    b = si.gaussian_field(dims, b_seed)
+    c = si.gaussian_field(dims, c_seed)
+    with _ctx(dims, U, mu, *O.kenney_laub(1, 1.0), k=40, tol=1e-12) as ctx:
+        # set-up accuracy: the deflated function moves by ~1e-2 x the eigen-residual (measured on
+        # 4^4), so 1e-10 keeps the difference quotient's error near 1e-10 / (2h) * 1e-2 = 5e-9
+        lam = ctx.build_deflation(m, extra=4, eig_tol=1e-10)
+        b_max = abs(4.0 - 1.6) + 3.0 * math.sqrt(2.0) + math.sqrt(2.0 * math.cosh(2.0 * mu))
+        sigma, omega = pkg.kenney_laub(20, 1.0 / math.sqrt(abs(lam[m]) * b_max))
+        ctx.set_rational(sigma, omega)
+        bt = torch.from_numpy(b).cuda().requires_grad_(True)
+        mut = torch.tensor(mu, dtype=torch.float64, requires_grad=True)
+        x = SignApply.apply(bt, mut, ctx)
+        loss = torch.vdot(torch.from_numpy(c).cuda(), x).real
+        loss.backward()
+        pairs = {}
+        for mm in (mu + h, mu - h):
+            ctx.set_mu(mm, rebuild_deflation=True)
+            pairs[mm] = ctx.get_deflation()
+        assert ctx.m == m
+    def loss_oracle(mm):
+        R, L, lm = pairs[mm]
+        for j in (0, m - 1):
+            rr = O.hw(dims, U, R[:, j], mm) - lm[j] * R[:, j]
+            assert np.linalg.norm(rr) <= 1e-9 * abs(lm[j]) * np.linalg.norm(R[:, j])
+        xo, rep, _ = O.fom_lr(dims, U, b, mm, sigma, omega, k=40, tol=1e-13, max_cycles=3000, R=R, L=L, lam=lm)
+        assert rep["converged"]
+        return np.real(np.vdot(c, xo))
+    fd = (loss_oracle(mu + h) - loss_oracle(mu - h)) / (2 * h)
+    assert abs(float(mut.grad) - fd) < 1e-5 * max(1.0, abs(fd)), (float(mut.grad), fd)

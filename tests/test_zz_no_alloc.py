@@ -1,6 +1,6 @@
 """sgn_inner_products_noalloc: the allocation-free inner products, for callers that
-cannot allocate device memory (stream capture in progress, host callbacks,
-frameworks that own all device memory).  Checked against sgn_inner_products.
+cannot allocate device memory (frameworks that own every device allocation, loops
+that must not pay for cudaMalloc).  Checked against sgn_inner_products.
 
 Kept in its own file, collected last, so a failure here comes after every other test."""
 import ctypes as C
