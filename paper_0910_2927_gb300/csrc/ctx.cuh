@@ -44,6 +44,7 @@ struct Engine {
     double* sigma_dev = nullptr;  // [ncol][s]
     double* omega_dev = nullptr;
     double* sigma_im_dev = nullptr;  // [ncol][s] imaginary parts (zero unless complex shifts are set)
+    double* neg1 = nullptr;          // [ncol] -1.0 (scale of the FP32 minimal-residual restart vector)
     // host mirrors of the per-column flags (pinned)
     int* h_done = nullptr;
     double* h_resest = nullptr;

@@ -131,6 +131,7 @@ int tune_stencil(sgn_ctx* c, int prec, int ncol, void* in, void* out) {
     std::vector<StencilShape> cands;
     for (int pipe = 0; pipe <= (prec == 0 ? 0 : 3); ++pipe)
         for (int nr : {1, 2, 3}) {
+            if (pipe == 4) continue;  // the colour-split kernel has its own shapes below
             if (nr > ncol || (prec == 0 && nr > 1) || (pipe == 1 && nr > 2) || (pipe >= 2 && nr != 2)) continue;
             const int groups = (ncol + nr - 1) / nr;
             const int maxt = nr == 1 && !pipe ? 384 : 256;
@@ -140,6 +141,10 @@ int tune_stencil(sgn_ctx* c, int prec, int ncol, void* in, void* out) {
                     if (sx * rb <= maxt && sx * rb >= 64) cands.push_back({sx, rb, nr, pipe});
             }
         }
+    if (prec != 0)  // colour-split kernel: sg site groups of 10 sites x fw fields per CTA (<= 8 warps)
+        for (int fw : {1, 2, 3, 4, 6, 8})
+            for (int sg : {1, 2, 4, 8})
+                if (fw <= ncol && sg * fw <= 8 && sg * fw >= 2) cands.push_back({sg, fw, 1, 4});
     if (cands.empty()) cands.push_back({});
     auto run = [&](StencilShape sh) -> cudaError_t {
         if (prec == 0)
@@ -360,13 +365,15 @@ cudaError_t cycle_dcgs(const sgn_ctx* c, Engine& E, const CycleArgs& a, cudaStre
         CU(tm.end());
     }
     T* Vk = V + k * sj;
-    if constexpr (sizeof(T) == sizeof(double2)) {
-        if (a.gmres) {  // the minimal residual r = V_{k+1} c becomes the restart vector
-            T* tt = reinterpret_cast<T*>(E.t);
-            CU(cudaMemsetAsync(tt, 0, sizeof(T) * (size_t)ncol * n, st));
+    if (a.gmres) {  // the minimal residual r = V_{k+1} c becomes the restart vector
+        T* tt = reinterpret_cast<T*>(E.t);
+        CU(cudaMemsetAsync(tt, 0, sizeof(T) * (size_t)ncol * n, st));
+        if constexpr (sizeof(T) == sizeof(double2)) {
             CU(update_x<T>(VB, k + 1, S.gres, k + 1, reinterpret_cast<double2*>(tt), n, n, ncol, S.done, nullptr, st));
-            CU(cudaMemcpyAsync(Vk, tt, sizeof(T) * (size_t)ncol * n, cudaMemcpyDeviceToDevice, st));
+        } else {  // FP32 basis: (0 - V c) * (-1), accumulated in FP32 like every basis update
+            CU(maxpy_scale<T>(VB, k + 1, S.gres, k + 1, tt, n, tt, n, E.neg1, n, ncol, S.done, st));
         }
+        CU(cudaMemcpyAsync(Vk, tt, sizeof(T) * (size_t)ncol * n, cudaMemcpyDeviceToDevice, st));
     }
     if (a.project && a.m > 0) {
         const Basis<T> LB{reinterpret_cast<const T*>(a.L), n, 0};
@@ -481,6 +488,7 @@ int get_engine(sgn_ctx* c, int ncol, int k, int s, int prec, Engine** out) {
     size_t osums = take(nc * E->rstride * sizeof(double2));
     size_t ocnt = take(nc * sizeof(int));
     size_t ogres = take(nc * (size_t)(k + 1) * sizeof(double2));
+    size_t oneg = take(nc * sizeof(double));
     SGN_CHECK(dev_alloc(c, E->arena, off));
     char* base = reinterpret_cast<char*>(E->arena.p);
     E->V = base + oV;
@@ -516,8 +524,14 @@ int get_engine(sgn_ctx* c, int ncol, int k, int s, int prec, Engine** out) {
     S.s = s;
     S.rstride = E->rstride;
     S.bd_tol = prec == SGN_PREC_FP64 ? 1e-14 : 1e-6;
+    E->neg1 = reinterpret_cast<double*>(base + oneg);
     // zero the whole arena once so no kernel ever reads uninitialised memory
     SGN_CUDA(cudaMemsetAsync(E->arena.p, 0, off, c->work));
+    {
+        std::vector<double> m1(nc, -1.0);
+        SGN_CUDA(cudaMemcpyAsync(E->neg1, m1.data(), nc * sizeof(double), cudaMemcpyHostToDevice, c->work));
+        SGN_CUDA(cudaStreamSynchronize(c->work));  // m1 is released on return
+    }
     SGN_CUDA(cudaHostAlloc(&E->h_done, nc * sizeof(int), cudaHostAllocDefault));
     SGN_CUDA(cudaHostAlloc(&E->h_resest, nc * sizeof(double), cudaHostAllocDefault));
     SGN_CUDA(cudaHostAlloc(&E->h_err, sizeof(int), cudaHostAllocDefault));
@@ -851,6 +865,16 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
     a1.xs = d;
     a1.xs_shift = (int64_t)B * n;
     a1.xs_col = n;
+    // Correction solves by restarted FOM (Galerkin, like the multishift phase); a batch whose
+    // FOM does not converge within kFomCap cycles, or meets a non-finite value, is solved again
+    // from the same residuals with minimal-residual (GMRES) restarts.  Restarted FOM on a single
+    // strongly non-normal shifted system can diverge (at mu = 1 its residual grew without bound
+    // over 1,800 cycles); GMRES cannot.  GMRES corrections leave residuals along unrelated
+    // directions, whose errors add up less favourably: the retry aims at a third of the target
+    // (on the 10^4 workload at tol 1e-8, GMRES corrections gave a relative error of x of 1.4e-8
+    // at the target and 4.7e-9 at a third of it; FOM corrections 2.9e-9 at the target).
+    constexpr int kFomCap = 300;
+    const double rtol = c->tol;
     const int max_rounds = 8;
     std::vector<double> sig1(B), om1(B, 1.0);
     const int nall = s * ncol;  // every (shift, column) pair as one column of [i][col][n]
@@ -886,7 +910,7 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
                     return SGN_ERR_NONFINITE;
                 }
                 worst = std::max(worst, rel);
-                if (rel > c->tol) {
+                if (rel > rtol) {
                     todo.emplace_back(i, col);
                     todo_rel.push_back(rel);
                 }
@@ -922,26 +946,37 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
         for (size_t t0 = 0; t0 < todo.size(); t0 += B) {
             const int nb = (int)std::min<size_t>(B, todo.size() - t0);
             float2* V0 = reinterpret_cast<float2*>(E1->V);
-            SGN_CUDA(cudaMemsetAsync(V0, 0, sizeof(float2) * (size_t)B * n, st));
             for (int j = 0; j < B; ++j) sig1[j] = j < nb ? c->sigma[todo[t0 + j].first] : c->sigma[0];
             SGN_CHECK(fill_shift_tables(c, *E1, sig1.data(), om1.data()));
-            for (int j = 0; j < nb; ++j) {
-                const int i = todo[t0 + j].first, col = todo[t0 + j].second;
-                SGN_CUDA(convert_f64_to_f32(rsd + ((size_t)i * ncol + col) * n, V0 + (size_t)j * n, n, st));
-            }
-            SGN_CUDA(cudaMemsetAsync(d, 0, field * B, st));
             // the correction needs to reduce the worst residual of the batch to a third
             // of the tolerance, not further (FP32 bases reach about 1e-6 at best)
             double brel = 0;
             for (int j = 0; j < nb; ++j) brel = std::max(brel, todo_rel[t0 + j]);
-            const double inner = std::min(0.1, std::max(1e-5, c->tol / (3.0 * brel)));
+            int st1 = SGN_OK;
             RunResult r1;
-            int st1 = run_engine<float2>(c, *E1, a1, inner, c->max_cycles, &r1);
-            if (debug_log())
-                fprintf(stderr, "[sgn mixed]   batch at %zu (%d systems): inner tol %.1e status %d cycles %d resmax %.3e\n",
-                        t0, nb, inner, st1, r1.cycles, r1.resmax);
+            for (int attempt = 0; attempt < 2; ++attempt) {
+                a1.gmres = attempt == 1;
+                SGN_CUDA(cudaMemsetAsync(V0, 0, sizeof(float2) * (size_t)B * n, st));
+                for (int j = 0; j < nb; ++j) {
+                    const int i = todo[t0 + j].first, col = todo[t0 + j].second;
+                    SGN_CUDA(convert_f64_to_f32(rsd + ((size_t)i * ncol + col) * n, V0 + (size_t)j * n, n, st));
+                }
+                SGN_CUDA(cudaMemsetAsync(d, 0, field * B, st));
+                const double inner = std::min(0.1, std::max(1e-5, rtol / ((a1.gmres ? 9.0 : 3.0) * brel)));
+                st1 = run_engine<float2>(c, *E1, a1, inner, a1.gmres ? c->max_cycles : std::min(c->max_cycles, kFomCap),
+                                         &r1);
+                if (debug_log())
+                    fprintf(stderr,
+                            "[sgn mixed]   batch at %zu (%d systems, %s): inner tol %.1e status %d cycles %d "
+                            "resmax %.3e\n",
+                            t0, nb, a1.gmres ? "GMRES" : "FOM", inner, st1, r1.cycles, r1.resmax);
+                ref_cycles += r1.cycles;
+                const bool fom_failed = !a1.gmres && (st1 == SGN_ERR_NONFINITE || st1 == SGN_ERR_BREAKDOWN ||
+                                                      (st1 == SGN_OK && !r1.converged));
+                if (!fom_failed) break;
+                SGN_CUDA(cudaMemsetAsync(E1->S.err, 0, sizeof(int), st));
+            }
             if (st1 != SGN_OK) return st1;
-            ref_cycles += r1.cycles;
             // r_i -= (A^2 - sigma_i) d_i:  A^2 d in FP32 on the engine's scratch fields
             {
                 float2* w32 = reinterpret_cast<float2*>(E1->w);
@@ -972,7 +1007,7 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
                                nullptr, st));
     if (x_shift) SGN_CUDA(cudaMemcpyAsync(x_shift, xs, field * ncol * s, cudaMemcpyDeviceToDevice, st));
     SGN_CUDA(cudaStreamSynchronize(st));
-    if (worst > c->tol) {
+    if (worst > rtol) {
         status = SGN_ERR_NOT_CONVERGED;
         set_error("mixed form: refinement did not bring every true residual below the tolerance");
     }

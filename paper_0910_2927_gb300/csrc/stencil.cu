@@ -463,15 +463,11 @@ __device__ __forceinline__ void both_hops_x2(float2 (&ar)[12], float2 (&ai)[12],
     hop_x2<LinkT, NU, +1>(ar, ai, in, P.stride_rhs, act, U, bw, bw, cb, P.vol);
 }
 
-// Grid and thread layout as k_hw with NR = 2.
+// One site, fields rhs0 and rhs0 + 1.
 template <class LinkT, bool CS>
-__device__ __forceinline__ void hw_x2_body(float2* __restrict__ out, const float2* __restrict__ in,
-                                           const LinkT* __restrict__ U, int nrhs, const StencilParams& P,
-                                           const int* __restrict__ skip, int ngrp) {
-    const int64_t tile = blockIdx.x / (unsigned)ngrp;
-    const int grp = (int)(blockIdx.x - tile * ngrp);
-    const int64_t site = tile * blockDim.x + threadIdx.x;
-    const int rhs0 = (grp * blockDim.y + threadIdx.y) * 2;
+__device__ __forceinline__ void x2_site(float2* __restrict__ out, const float2* __restrict__ in,
+                                        const LinkT* __restrict__ U, int nrhs, const StencilParams& P,
+                                        const int* __restrict__ skip, int64_t site, int rhs0) {
     if (site >= P.vol || rhs0 >= nrhs) return;
     bool act[2];
 #pragma unroll
@@ -526,6 +522,17 @@ __device__ __forceinline__ void hw_x2_body(float2* __restrict__ out, const float
         }
         Field<float>::template store<CS>(out + (rhs0 + i) * P.stride_rhs, site, 2 * P.vol, o);
     }
+}
+
+// Grid and thread layout as k_hw with NR = 2.
+template <class LinkT, bool CS>
+__device__ __forceinline__ void hw_x2_body(float2* __restrict__ out, const float2* __restrict__ in,
+                                           const LinkT* __restrict__ U, int nrhs, const StencilParams& P,
+                                           const int* __restrict__ skip, int ngrp) {
+    const int64_t tile = blockIdx.x / (unsigned)ngrp;
+    const int grp = (int)(blockIdx.x - tile * ngrp);
+    x2_site<LinkT, CS>(out, in, U, nrhs, P, skip, tile * blockDim.x + threadIdx.x,
+                       (grp * blockDim.y + threadIdx.y) * 2);
 }
 
 // The kernel as the compiler sizes it (144 registers: 12 warps per SM), and capped at 128
@@ -727,6 +734,177 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// ---- colour-split FP32 form ---------------------------------------------------
+// Three lanes per site and field, one per colour a = 0, 1, 2 (lanes 3 j + a of a warp
+// for its 10 sites j; lanes 30 and 31 carry no site).  Lane a loads the four spin
+// components of colour a of each neighbour (entries 3 s + a of the packed field),
+// projects them to its colour of the half-spinor (1 -/+ gamma) psi, receives the other
+// two colours from the lanes beside it (shuffles), multiplies them by row a of the
+// link, U_ab h_b (forward) or conj(U_ba) h_b (backward), and accumulates the four spins
+// of colour a.  A lane holds a quarter of the state of a one-field thread, so the
+// kernel runs at about 50 registers and 40+ resident warps per SM, which keep far more
+// loads in flight than the 12-16 warps of the two-field kernels.
+// Grid: CTA b covers site tile b / ngrp and field group b % ngrp; warp w of the CTA
+// takes site group tile * (warps / fw) + w / fw (10 sites) and field group * fw + w % fw.
+constexpr int kCsSites = 10;  // sites per warp
+
+__device__ __forceinline__ Cx<float> ldc(const float2* __restrict__ p) {
+    const float2 v = __ldg(p);
+    return {v.x, v.y};
+}
+__device__ __forceinline__ Cx<float> shfl_cx(Cx<float> v, int src) {
+    return {__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src)};
+}
+// acc += u * v (CONJ: conj(u) * v)
+template <bool CONJ>
+__device__ __forceinline__ void cmac_cs(Cx<float>& acc, Cx<float> u, Cx<float> v) {
+    if constexpr (CONJ) cmac_conj(acc, u, v); else cmac(acc, u, v);
+}
+
+template <class LinkT, int NU, int S>
+__device__ __forceinline__ void hop_cs(Cx<float> (&acc)[4], const float2* __restrict__ fin, int64_t vol2,
+                                       bool act, const LinkT* __restrict__ U, int64_t link_site, int64_t nb,
+                                       float coef, int64_t vol, int a, int a1, int a2, int src1, int src2) {
+    // spins 0..3 of colour a at the neighbour: entry k = 3 s + a at (k/2) vol2 + 2 nb + k % 2
+    Cx<float> p[4];
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp) {
+        const int k = 3 * sp + a;
+        p[sp] = act ? ldc(fin + (int64_t)(k >> 1) * vol2 + 2 * nb + (k & 1)) : Cx<float>{0.f, 0.f};
+    }
+    // this colour of the projected half-spinor h = psi_up + S B psi_dn
+    const float sg = float(S);
+    Cx<float> h0, h1;
+    if constexpr (NU == 0) {  // B psi_dn = (-i p3, -i p2)
+        h0 = p[0] + scale(mul_mi(p[3]), sg);
+        h1 = p[1] + scale(mul_mi(p[2]), sg);
+    } else if constexpr (NU == 1) {  // (-p3, p2)
+        h0 = p[0] - scale(p[3], sg);
+        h1 = p[1] + scale(p[2], sg);
+    } else if constexpr (NU == 2) {  // (-i p2, i p3)
+        h0 = p[0] + scale(mul_mi(p[2]), sg);
+        h1 = p[1] + scale(mul_i(p[3]), sg);
+    } else {  // (p2, p3)
+        h0 = p[0] + scale(p[2], sg);
+        h1 = p[1] + scale(p[3], sg);
+    }
+    // the two other colours from the lanes of the same site
+    const Cx<float> h0b = shfl_cx(h0, src1), h1b = shfl_cx(h1, src1);
+    const Cx<float> h0c = shfl_cx(h0, src2), h1c = shfl_cx(h1, src2);
+    // row a of U(site) (forward) or of U(nb)^dag, i.e. column a of U(nb) conjugated (backward)
+    const LinkT* lb = U + (int64_t)NU * 9 * vol + link_site;
+    constexpr bool CJ = S > 0;
+    auto uidx = [&](int b) -> int64_t { return (int64_t)(CJ ? 3 * b + a : 3 * a + b) * vol; };
+    const Cx<float> ua = Link<float, LinkT>::ld(lb, uidx(a));
+    const Cx<float> ub = Link<float, LinkT>::ld(lb, uidx(a1));
+    const Cx<float> uc = Link<float, LinkT>::ld(lb, uidx(a2));
+    Cx<float> g0 = {0.f, 0.f}, g1 = {0.f, 0.f};
+    cmac_cs<CJ>(g0, ua, h0);
+    cmac_cs<CJ>(g1, ua, h1);
+    cmac_cs<CJ>(g0, ub, h0b);
+    cmac_cs<CJ>(g1, ub, h1b);
+    cmac_cs<CJ>(g0, uc, h0c);
+    cmac_cs<CJ>(g1, uc, h1c);
+    // reconstruction: upper spins coef g, lower spins coef S B^dag g
+    const float cs = coef * sg;
+    acc[0] = acc[0] + scale(g0, coef);
+    acc[1] = acc[1] + scale(g1, coef);
+    if constexpr (NU == 0) {  // B^dag g = (i g1, i g0)
+        acc[2] = acc[2] + scale(mul_i(g1), cs);
+        acc[3] = acc[3] + scale(mul_i(g0), cs);
+    } else if constexpr (NU == 1) {  // (g1, -g0)
+        acc[2] = acc[2] + scale(g1, cs);
+        acc[3] = acc[3] - scale(g0, cs);
+    } else if constexpr (NU == 2) {  // (i g0, -i g1)
+        acc[2] = acc[2] + scale(mul_i(g0), cs);
+        acc[3] = acc[3] + scale(mul_mi(g1), cs);
+    } else {  // (g0, g1)
+        acc[2] = acc[2] + scale(g0, cs);
+        acc[3] = acc[3] + scale(g1, cs);
+    }
+}
+
+template <class LinkT, int NU>
+__device__ __forceinline__ void both_hops_cs(Cx<float> (&acc)[4], const float2* __restrict__ fin, bool act,
+                                             const LinkT* __restrict__ U, int64_t site, const int co[4],
+                                             const StencilParams& P, int a, int a1, int a2, int src1, int src2) {
+    int64_t stride = 1;
+#pragma unroll
+    for (int d = 0; d < NU; ++d) stride *= P.L[d];
+    const int L = P.L[NU];
+    int64_t fw = site + stride;
+    float cf = P.cf32[NU];
+    if (co[NU] == L - 1) {
+        fw = site - (int64_t)(L - 1) * stride;
+        if (P.ap[NU]) cf = -cf;
+    }
+    int64_t bw = site - stride;
+    float cb = P.cb32[NU];
+    if (co[NU] == 0) {
+        bw = site + (int64_t)(L - 1) * stride;
+        if (P.ap[NU]) cb = -cb;
+    }
+    hop_cs<LinkT, NU, -1>(acc, fin, 2 * P.vol, act, U, site, fw, cf, P.vol, a, a1, a2, src1, src2);
+    hop_cs<LinkT, NU, +1>(acc, fin, 2 * P.vol, act, U, bw, bw, cb, P.vol, a, a1, a2, src1, src2);
+}
+
+template <class LinkT, bool CS>
+__global__ void __launch_bounds__(256, 4)
+    k_hw_cs(float2* __restrict__ out, const float2* __restrict__ in, const LinkT* __restrict__ U, int nrhs,
+            StencilParams P, const int* __restrict__ skip, int ngrp, int fw) {
+    const int warp = threadIdx.y, lane = threadIdx.x;
+    const int64_t tile = blockIdx.x / (unsigned)ngrp;
+    const int grp = (int)(blockIdx.x - tile * ngrp);
+    const int sgpc = blockDim.y / fw;  // site groups per CTA
+    const int64_t sgroup = tile * sgpc + warp / fw;
+    const int field = grp * fw + warp % fw;
+    // warp-uniform exits only (every lane of a warp takes part in the shuffles)
+    if (field >= nrhs || (skip && skip[field])) return;
+    if (sgroup * kCsSites >= P.vol) return;
+    const int j = lane / 3;
+    const int a = lane - 3 * j;           // colour of this lane (lanes 30, 31: j = 10, a = 0, 1)
+    const int a1 = a == 2 ? 0 : a + 1, a2 = a == 0 ? 2 : a - 1;
+    const int jj = j < kCsSites ? j : kCsSites - 1;
+    const int src1 = 3 * jj + a1, src2 = 3 * jj + a2;
+    const int64_t site0 = sgroup * kCsSites + jj;
+    const bool act = j < kCsSites && site0 < P.vol;
+    const int64_t site = act ? site0 : sgroup * kCsSites;  // idle lanes: a valid site, nothing stored
+    int co[4];
+    {
+        const uint32_t s0 = (uint32_t)site;
+        const uint32_t q0 = P.div[0].div(s0);
+        co[0] = (int)(s0 - q0 * (uint32_t)P.L[0]);
+        const uint32_t q1 = P.div[1].div(q0);
+        co[1] = (int)(q0 - q1 * (uint32_t)P.L[1]);
+        const uint32_t q2 = P.div[2].div(q1);
+        co[2] = (int)(q1 - q2 * (uint32_t)P.L[2]);
+        co[3] = (int)q2;
+    }
+    const float2* fin = in + (int64_t)field * P.stride_rhs;
+    const int64_t vol2 = 2 * P.vol;
+    Cx<float> acc[4];
+    const float d = P.diag32;
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp) {
+        const int k = 3 * sp + a;
+        acc[sp] = act ? scale(ldc(fin + (int64_t)(k >> 1) * vol2 + 2 * site + (k & 1)), d) : Cx<float>{0.f, 0.f};
+    }
+    both_hops_cs<LinkT, 0>(acc, fin, act, U, site, co, P, a, a1, a2, src1, src2);
+    both_hops_cs<LinkT, 1>(acc, fin, act, U, site, co, P, a, a1, a2, src1, src2);
+    both_hops_cs<LinkT, 2>(acc, fin, act, U, site, co, P, a, a1, a2, src1, src2);
+    both_hops_cs<LinkT, 3>(acc, fin, act, U, site, co, P, a, a1, a2, src1, src2);
+    if (!act) return;
+    float2* fo = out + (int64_t)field * P.stride_rhs;
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp) {
+        const int k = 3 * sp + a;
+        const float g5 = sp < 2 ? 1.f : -1.f;  // gamma5 = diag(1, 1, -1, -1)
+        const float2 v = make_float2(g5 * acc[sp].x, g5 * acc[sp].y);
+        float2* dst = fo + (int64_t)(k >> 1) * vol2 + 2 * site + (k & 1);
+        if constexpr (CS) __stcs(dst, v); else *dst = v;
+    }
+}
+
 // ---- layout conversions (one thread per site of one field) --------------------
 template <class T>
 __global__ void k_pack(const T* __restrict__ in, T* __restrict__ out, int64_t vol) {
@@ -809,6 +987,26 @@ cudaError_t launch_pipe(float2* out, const float2* in, const LinkT* U, int nrhs,
     return cudaGetLastError();
 }
 
+// Colour-split kernel: CTA = 32 lanes x (sg site groups x fw fields) warps.
+template <class LinkT>
+cudaError_t launch_cs(float2* out, const float2* in, const LinkT* U, int nrhs, const StencilParams& p, const int* skip,
+                      cudaStream_t st, int sg, int fw) {
+    if (sg < 1 || fw < 1 || sg * fw > 8) return cudaErrorInvalidValue;
+    const int ngrp = (nrhs + fw - 1) / fw;
+    const int64_t groups = (p.vol + kCsSites - 1) / kCsSites;
+    const int64_t tiles = (groups + sg - 1) / sg;
+    if (tiles * ngrp > 0x7fffffffLL) return cudaErrorInvalidValue;
+    dim3 block(32, sg * fw);
+    const bool cs = (double)nrhs * (double)p.vol * 12.0 * sizeof(float2) > 256.0 * (1 << 20);
+    const unsigned grid = (unsigned)(tiles * ngrp);
+    if (cs)
+        k_hw_cs<LinkT, true><<<grid, block, 0, st>>>(out, in, U, nrhs, p, skip, ngrp, fw);
+    else
+        k_hw_cs<LinkT, false><<<grid, block, 0, st>>>(out, in, U, nrhs, p, skip, ngrp, fw);
+    count_launch();
+    return cudaGetLastError();
+}
+
 template <class LinkT, int MINB>
 cudaError_t launch_x2(float2* out, const float2* in, const LinkT* U, int nrhs, const StencilParams& p,
                       const int* skip, cudaStream_t st, int sx, int rb) {
@@ -837,6 +1035,14 @@ template <class R, class LinkT>
 cudaError_t launch(typename Field<R>::T* out, const typename Field<R>::T* in, const LinkT* U, int nrhs,
                    const StencilParams& p, const int* skip, cudaStream_t st, StencilShape sh) {
     if (nrhs <= 0 || p.vol <= 0) return cudaSuccess;
+    if (sh.pipe == 4) {  // the colour-split FP32 kernel: sx site groups of 10 sites, rb fields per CTA
+        if constexpr (sizeof(R) == 4) {
+            if (sh.nr != 1) return cudaErrorInvalidValue;
+            return launch_cs<LinkT>(out, in, U, nrhs, p, skip, st, sh.sx, sh.rb);
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
     if (sh.pipe == 2 || sh.pipe == 3) {  // the paired FP32 kernel (3: capped at 128 registers)
         if constexpr (sizeof(R) == 4) {
             if (sh.sx % 32 != 0 || sh.rb < 1 || sh.sx * sh.rb > 256 || sh.nr != 2) return cudaErrorInvalidValue;

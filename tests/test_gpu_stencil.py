@@ -106,7 +106,8 @@ def test_packed_layout_roundtrip_and_stencil():
 @pytest.mark.parametrize("shape", ["32,4,3", "64,2,2", "32,2,3", "64,3,1", "128,1,2",
                                    "32,4,1,1", "64,2,2,1", "128,1,2,1", "256,1,1,1",
                                    "32,4,2,2", "64,2,2,2", "128,1,2,2", "256,1,2,2",
-                                   "64,2,2,3", "128,1,2,3"])
+                                   "64,2,2,3", "128,1,2,3",
+                                   "1,2,1,4", "2,4,1,4", "4,2,1,4", "8,1,1,4", "1,8,1,4"])
 def test_fp32_stencil_launch_shapes(shape, monkeypatch):
     """Every launch shape (sites per CTA, thread rows, fields per thread, the kernel
     that stages neighbours through shared memory with cp.async, and the kernel with
@@ -129,7 +130,7 @@ def test_fp32_stencil_launch_shapes(shape, monkeypatch):
         assert np.linalg.norm(outa[r] - refa) / np.linalg.norm(refa) < 2e-6
 
 
-@pytest.mark.parametrize("shape", ["32,12,3", "64,2,1,2", "128,4,2,2", "64,2,3,3"])
+@pytest.mark.parametrize("shape", ["32,12,3", "64,2,1,2", "128,4,2,2", "64,2,3,3", "3,3,1,4", "2,2,2,4"])
 def test_invalid_launch_shape_is_an_error(shape, monkeypatch):
     """A shape outside the kernel's limits (384 threads with 3 fields each; the paired
     kernel with one field per thread, or with 512 threads) is refused with an error."""
@@ -144,7 +145,7 @@ def test_invalid_launch_shape_is_an_error(shape, monkeypatch):
             ctx.hw(torch.from_numpy(b).cuda(), precision=pkg.PREC_MIXED)
 
 
-@pytest.mark.parametrize("shape", ["64,2,2,1", "32,4,1,1", "64,2,2,2", "128,1,2,3"])
+@pytest.mark.parametrize("shape", ["64,2,2,1", "32,4,1,1", "64,2,2,2", "128,1,2,3", "2,4,1,4", "1,6,1,4"])
 def test_pipelined_stencil_bf16_links_and_many_fields(shape, monkeypatch):
     """The shared-memory staged kernel with BF16 links and 13 fields (several CTAs
     per site tile) matches the oracle within the BF16 rounding of the links."""
@@ -159,3 +160,23 @@ def test_pipelined_stencil_bf16_links_and_many_fields(shape, monkeypatch):
     for r in (0, 6, 12):
         ref = O.hw(dims, U, b[r], mu)
         assert np.linalg.norm(out[r] - ref) / np.linalg.norm(ref) < 2e-2
+
+
+@pytest.mark.parametrize("shape", ["1,4,1,4", "4,1,1,4"])
+def test_colour_split_stencil_ragged_tail(shape, monkeypatch):
+    """The colour-split kernel (10 sites per warp, three lanes per site) on a volume that
+    leaves the last warp's group of sites ragged (135 sites), both hop directions."""
+    import paper_0910_2927_gb300 as pkg
+    monkeypatch.setenv("SGN_STENCIL_SHAPE", shape)
+    dims, mu = (3, 3, 3, 5), 0.6
+    U = si.random_su3_links(dims, 0.7, 37)
+    b = si.gaussian_block(dims, 3, 38)
+    with _ctx(dims, U, mu) as ctx:
+        ctx.set_precision(pkg.PREC_MIXED, 1e-8, pkg.LINKS_FP32)
+        out = ctx.hw(torch.from_numpy(b).cuda(), precision=pkg.PREC_MIXED).cpu().numpy()
+        outa = ctx.hw(torch.from_numpy(b).cuda(), precision=pkg.PREC_MIXED, adjoint=True).cpu().numpy()
+    for r in range(3):
+        ref = O.hw(dims, U, b[r], mu)
+        assert np.linalg.norm(out[r] - ref) / np.linalg.norm(ref) < 2e-6
+        refa = O.hw(dims, U, b[r], -mu)
+        assert np.linalg.norm(outa[r] - refa) / np.linalg.norm(refa) < 2e-6
