@@ -13,6 +13,8 @@
 // the per-column sum over CTAs -- is FP64 in a fixed order (no atomics).
 #include "blas.cuh"
 
+#include <cstdlib>
+
 #include <algorithm>
 
 namespace sgn {
@@ -465,10 +467,11 @@ __global__ void __launch_bounds__(NT) k_update_x(Basis<T> V, int J, const double
     }
 }
 
-// xs[i] += sum_j y_ij V_j for every shift i, one sweep of V per group of 8 shifts.
+// xs[i] += sum_j y_ij V_j for every shift i, one sweep of V per group of SG shifts.  SG = 8 by
+// default: with SG = 20 (V read once for the workloads' 20 poles) the FP32 kernel needs 192
+// registers and ran at half the speed on the 10^4 workload (17.9 against 8.3 ms per solve).
 // Products and the sum over j in the storage precision; the add to xs in FP64.
-constexpr int SG = 8;
-template <class T>
+template <class T, int SG>
 __global__ void __launch_bounds__(NT) k_update_shifts(Basis<T> V, int J, const double2* __restrict__ y, int s,
                                                       int kmax, double2* __restrict__ xs, int64_t xs_shift,
                                                       int64_t xs_col, int64_t npk, const int* __restrict__ skip,
@@ -1129,7 +1132,9 @@ __global__ void __launch_bounds__(NT) k_axpby3(T* __restrict__ out, double a, co
     }
 }
 
-// Z_j = sum_i C[i][j] Y_i  (Y: q fields, Z: r fields, each n complex apart; C row-major q x r).
+// Z_j = sum_i C[i][j] Y_i  (Y: q fields, Z: r fields, each n complex apart; C row-major q x r),
+// SG output fields per sweep of Y.
+constexpr int SG = 8;
 template <class T>
 __global__ void __launch_bounds__(NT) k_block_combine(const T* __restrict__ Y, int q, const double2* __restrict__ Cm,
                                                       int r, T* __restrict__ Z, int64_t n, int64_t npk) {
@@ -1381,7 +1386,18 @@ cudaError_t update_shifts(Basis<T> V, int J, const double2* y, int s, int kmax, 
     size_t smem = sizeof(typename Ops<T>::C) * (size_t)s * (size_t)J;
     if (smem > 48 * 1024) return cudaErrorInvalidValue;
     dim3 grid((unsigned)((npk + NT - 1) / NT), ncol);
-    k_update_shifts<T><<<grid, NT, smem, st>>>(V, J, y, s, kmax, xs, xs_shift, xs_col, npk, skip, kk);
+    // group size: SGN_SHIFT_GROUP = 10 or 20 overrides the default 8 (measurements)
+    static const int forced = [] {
+        const char* e = getenv("SGN_SHIFT_GROUP");
+        return e ? atoi(e) : 0;
+    }();
+    const int sg = forced == 10 || forced == 20 ? forced : 8;
+    if (sg == 20 && s <= 20)
+        k_update_shifts<T, 20><<<grid, NT, smem, st>>>(V, J, y, s, kmax, xs, xs_shift, xs_col, npk, skip, kk);
+    else if (sg == 10)
+        k_update_shifts<T, 10><<<grid, NT, smem, st>>>(V, J, y, s, kmax, xs, xs_shift, xs_col, npk, skip, kk);
+    else
+        k_update_shifts<T, 8><<<grid, NT, smem, st>>>(V, J, y, s, kmax, xs, xs_shift, xs_col, npk, skip, kk);
     count_launch();
     return cudaGetLastError();
 }

@@ -54,6 +54,12 @@ struct Engine {
     cudaGraphExec_t graph = nullptr;
     uint64_t graph_key = 0;
     long long graph_kernels = 0;  // kernel nodes of the captured cycle
+    // the whole restart loop on the device: a conditional WHILE node whose body is one
+    // captured cycle and the decision kernel (k_loop_decide)
+    cudaGraphExec_t loop = nullptr;
+    uint64_t loop_key = 0;
+    bool loop_unavailable = false;  // the runtime refused the conditional node: host loop
+    int* cyc_dev = nullptr;         // [1] cycles run by the device loop
     // kernel timing: event pairs recorded inside the cycle (class, algorithmic bytes)
     std::vector<cudaEvent_t> tev;
     std::vector<std::pair<int, double>> tmarks;

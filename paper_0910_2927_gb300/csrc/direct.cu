@@ -4,42 +4,221 @@
 // and sign(H_k) by Roberts' Newton iteration X <- (X + X^{-1}) / 2 on the k x k matrix.
 // The whole basis is kept (k + 1 FP64 fields per column, the method's memory cost); the
 // Arnoldi steps use the FP64 stencil and two classical Gram-Schmidt passes, in blocks of at
-// most 128 basis vectors per kernel (the reduction's slot limit).  The k x k Newton
-// iterations run on the host, one thread per column.
+// most 128 basis vectors per kernel (the reduction's slot limit).  The Newton iterations run
+// on the GPU for all columns at once: X^{-1} by Gauss-Jordan elimination with partial
+// pivoting on [X | I], one launch pair per pivot (captured once as a CUDA graph), with the
+// matrices of shorter Krylov dimension padded by the identity (sign(I) = I).
 #include "ctx.cuh"
 #include "dense_eig.h"
 
 #include <algorithm>
-#include <thread>
 
 namespace sgn {
 
 namespace {
 constexpr int GS_BLOCK = 128;
+using cdd = std::complex<double>;
 
-// sign(M) of a small dense matrix (row-major kk x kk) by Roberts' Newton iteration:
-// iterate until the update falls below 1e-12 of the iterate, then once more (quadratic
-// convergence takes that step to rounding level).  Returns 0, or 1 on a singular iterate
-// or no convergence in 100 steps.
-int roberts_sign(int kk, std::vector<std::complex<double>>& X) {
-    using cd = std::complex<double>;
-    int extra = -1;
-    for (int it = 0; it < 100; ++it) {
-        std::vector<cd> inv((size_t)kk * kk, 0.0);
-        for (int i = 0; i < kk; ++i) inv[(size_t)i * kk + i] = 1.0;
-        if (dense_solve(kk, kk, X, inv)) return 1;
-        double dn = 0, xn = 0;
-        for (size_t e = 0; e < X.size(); ++e) {
-            const cd xn1 = 0.5 * (X[e] + inv[e]);
-            dn += std::norm(xn1 - X[e]);
-            xn += std::norm(xn1);
-            X[e] = xn1;
-        }
-        if (extra == 0) return 0;
-        if (extra < 0 && std::sqrt(dn) <= 1e-12 * std::sqrt(xn)) extra = 0;
-    }
-    return 1;
+__device__ __forceinline__ double2 cdiv_d(double2 a, double2 b) {
+    const double den = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
 }
+
+// Gauss-Jordan step p on the augmented matrices A[col] = [X | I] (q rows, 2q columns,
+// row-major): pivot row = the first row i >= p of largest |A[i][p]|, swapped with row p,
+// row p scaled by 1 / pivot, and the column of elimination factors A[i][p] saved to fac.
+// One CTA per matrix.  A zero pivot (singular X: an eigenvalue of H_k on the imaginary
+// axis) sets bad[col].
+__global__ void __launch_bounds__(256) k_gj_pivot(double2* __restrict__ A, int q, int p, double2* __restrict__ fac,
+                                                  int* __restrict__ bad) {
+    const int col = blockIdx.x;
+    double2* M = A + (size_t)col * q * 2 * q;
+    const int ld = 2 * q;
+    __shared__ double sv[256];
+    __shared__ int si[256];
+    double best = -1.0;
+    int bi = p;
+    for (int i = p + threadIdx.x; i < q; i += blockDim.x) {
+        const double2 v = M[(size_t)i * ld + p];
+        const double a = v.x * v.x + v.y * v.y;
+        if (a > best) {
+            best = a;
+            bi = i;
+        }
+    }
+    sv[threadIdx.x] = best;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {  // ties keep the lower row (first maximal pivot)
+        if (threadIdx.x < s) {
+            const double o = sv[threadIdx.x + s];
+            const int oi = si[threadIdx.x + s];
+            if (o > sv[threadIdx.x] || (o == sv[threadIdx.x] && oi < si[threadIdx.x])) {
+                sv[threadIdx.x] = o;
+                si[threadIdx.x] = oi;
+            }
+        }
+        __syncthreads();
+    }
+    const int r = si[0];
+    if (!(sv[0] > 0.0)) {
+        if (threadIdx.x == 0) bad[col] = 1;
+        return;
+    }
+    if (r != p)
+        for (int j = threadIdx.x; j < ld; j += blockDim.x) {
+            const double2 t = M[(size_t)p * ld + j];
+            M[(size_t)p * ld + j] = M[(size_t)r * ld + j];
+            M[(size_t)r * ld + j] = t;
+        }
+    __syncthreads();
+    const double2 piv = M[(size_t)p * ld + p];
+    __syncthreads();
+    for (int j = threadIdx.x; j < ld; j += blockDim.x) M[(size_t)p * ld + j] = cdiv_d(M[(size_t)p * ld + j], piv);
+    __syncthreads();
+    for (int i = threadIdx.x; i < q; i += blockDim.x) fac[(size_t)col * q + i] = M[(size_t)i * ld + p];
+}
+
+// A[i][j] -= fac[i] A[p][j] for every row i != p (columns j >= p on the left half carry
+// the reduction; the right half is the inverse being formed).
+__global__ void __launch_bounds__(256) k_gj_eliminate(double2* __restrict__ A, int q, int p,
+                                                      const double2* __restrict__ fac, const int* __restrict__ bad) {
+    const int col = blockIdx.y;
+    if (bad[col]) return;
+    double2* M = A + (size_t)col * q * 2 * q;
+    const int ld = 2 * q;
+    const int w = ld - p;  // columns p .. 2q-1
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)q * w) return;
+    const int i = (int)(e / w);
+    const int j = p + (int)(e - (int64_t)i * w);
+    if (i == p) return;
+    const double2 f = fac[(size_t)col * q + i];
+    const double2 pr = M[(size_t)p * ld + j];
+    double2 v = M[(size_t)i * ld + j];
+    v.x -= f.x * pr.x - f.y * pr.y;
+    v.y -= f.x * pr.y + f.y * pr.x;
+    M[(size_t)i * ld + j] = v;
+}
+
+// [X | I] from X (q x q per column), and after the inversion the Newton update
+// X <- (X + X^{-1}) / 2 with the per-column sums ||X_new - X||^2 and ||X_new||^2.
+__global__ void k_gj_load(const double2* __restrict__ X, double2* __restrict__ A, int q) {
+    const int col = blockIdx.y;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)q * 2 * q) return;
+    const int i = (int)(e / (2 * q)), j = (int)(e - (int64_t)i * 2 * q);
+    A[(size_t)col * q * 2 * q + e] =
+        j < q ? X[(size_t)col * q * q + (size_t)i * q + j] : make_double2(j - q == i ? 1.0 : 0.0, 0.0);
+}
+__global__ void __launch_bounds__(256) k_newton_update(double2* __restrict__ X, const double2* __restrict__ A, int q,
+                                                       double* __restrict__ sums) {
+    const int col = blockIdx.x;
+    __shared__ double sd[256], sx[256];
+    double dn = 0, xn = 0;
+    for (int64_t e = threadIdx.x; e < (int64_t)q * q; e += blockDim.x) {
+        const int i = (int)(e / q), j = (int)(e - (int64_t)i * q);
+        const double2 xo = X[(size_t)col * q * q + e];
+        const double2 xi = A[(size_t)col * q * 2 * q + (size_t)i * 2 * q + q + j];
+        const double2 xn1 = make_double2(0.5 * (xo.x + xi.x), 0.5 * (xo.y + xi.y));
+        dn += (xn1.x - xo.x) * (xn1.x - xo.x) + (xn1.y - xo.y) * (xn1.y - xo.y);
+        xn += xn1.x * xn1.x + xn1.y * xn1.y;
+        X[(size_t)col * q * q + e] = xn1;
+    }
+    sd[threadIdx.x] = dn;
+    sx[threadIdx.x] = xn;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sd[threadIdx.x] += sd[threadIdx.x + s];
+            sx[threadIdx.x] += sx[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        sums[2 * col] = sd[0];
+        sums[2 * col + 1] = sx[0];
+    }
+}
+
+// sign(X_col) for ncol matrices of size q (row-major, device) by Roberts' Newton iteration,
+// every column until its update falls below 1e-12 of the iterate, then once more.  Returns
+// 1 if a column met a singular iterate or did not converge in 100 steps.
+int newton_sign_gpu(sgn_ctx* c, double2* X, int q, int ncol, int* failed) {
+    cudaStream_t st = c->work;
+    const size_t aug = (size_t)ncol * q * 2 * q;
+    DevBuf buf;
+    const size_t oA = 0, of = align256(sizeof(double2) * aug), ob = of + align256(sizeof(double2) * ncol * q),
+                 os = ob + align256(sizeof(int) * ncol);
+    SGN_CHECK(dev_alloc(c, buf, os + align256(sizeof(double) * 2 * ncol)));
+    char* base = reinterpret_cast<char*>(buf.p);
+    double2* A = reinterpret_cast<double2*>(base + oA);
+    double2* fac = reinterpret_cast<double2*>(base + of);
+    int* bad = reinterpret_cast<int*>(base + ob);
+    double* sums = reinterpret_cast<double*>(base + os);
+    auto done_with = [&](int rc) {
+        dev_free(c, buf);
+        return rc;
+    };
+    // one inversion = 2q launches: captured once, replayed every Newton step
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        const int64_t cells = (int64_t)q * 2 * q;
+        k_gj_load<<<dim3((unsigned)((cells + 255) / 256), ncol), 256, 0, st>>>(X, A, q);
+        for (int p = 0; p < q && e == cudaSuccess; ++p) {
+            k_gj_pivot<<<ncol, 256, 0, st>>>(A, q, p, fac, bad);
+            const int64_t work = (int64_t)q * (2 * q - p);
+            k_gj_eliminate<<<dim3((unsigned)((work + 255) / 256), ncol), 256, 0, st>>>(A, q, p, fac, bad);
+            e = cudaGetLastError();
+        }
+        k_newton_update<<<ncol, 256, 0, st>>>(X, A, q, sums);
+        cudaError_t ee = cudaStreamEndCapture(st, &g);
+        if (e == cudaSuccess) e = ee;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        set_error(std::string("apply_direct: Newton graph: ") + cudaGetErrorString(e));
+        return done_with(SGN_ERR_CUDA);
+    }
+    // per column: 0 iterating, 1 update below 1e-12 of the iterate (one more step to take),
+    // 2 finished; every column steps with the others (a converged X is a fixed point)
+    std::vector<double> hs(2 * ncol);
+    std::vector<int> hb(ncol), state(ncol, 0);
+    bool launch_ok = cudaMemsetAsync(bad, 0, sizeof(int) * ncol, st) == cudaSuccess;
+    for (int it = 0; it < 100 && launch_ok; ++it) {
+        if (cudaGraphLaunch(ge, st) != cudaSuccess ||
+            cudaMemcpyAsync(hs.data(), sums, sizeof(double) * 2 * ncol, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(hb.data(), bad, sizeof(int) * ncol, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            launch_ok = false;
+            break;
+        }
+        count_launch(2 + 2LL * q);
+        bool all = true;
+        for (int col = 0; col < ncol; ++col) {
+            if (hb[col] || state[col] == 2) continue;
+            if (state[col] == 1) {
+                state[col] = 2;
+                continue;
+            }
+            if (std::sqrt(hs[2 * col]) <= 1e-12 * std::sqrt(hs[2 * col + 1])) state[col] = 1;
+            all = false;
+        }
+        if (all) break;
+    }
+    cudaGraphExecDestroy(ge);
+    if (!launch_ok) {
+        set_error("apply_direct: Newton iteration launch failed");
+        return done_with(SGN_ERR_CUDA);
+    }
+    for (int col = 0; col < ncol; ++col)
+        if (hb[col] || state[col] != 2) failed[col] = 1;
+    return done_with(SGN_OK);
+}
+
 }  // namespace
 
 int direct_projection(sgn_ctx* c, const double2* b, double2* x, int ncol, int k, bool adjoint, int* kk_out) {
@@ -179,36 +358,48 @@ int direct_projection(sgn_ctx* c, const double2* b, double2* x, int ncol, int k,
         DC(normalize_into(V + (size_t)(j + 1) * sj, hn));
         if (std::none_of(live.begin(), live.end(), [](char v) { return v != 0; })) break;
     }
-    // y_col = beta sign(H_kk) e_1, on the host, one thread per column
+    // y_col = beta sign(H_kk) e_1: Roberts' Newton iteration for all columns on the GPU,
+    // each H_kk padded to the largest Krylov dimension with the identity
     const int kmaxu = *std::max_element(kk.begin(), kk.end());
-    std::vector<cd> Y((size_t)ncol * std::max(kmaxu, 1), 0.0);
+    const int qd = std::max(kmaxu, 1);
+    std::vector<cd> Y((size_t)ncol * qd, 0.0);
     std::vector<int> fail(ncol, 0);
-    auto work = [&](int col) {
-        const int q = kk[col];
-        if (q == 0) return;
-        std::vector<cd> X((size_t)q * q);
-        for (int r = 0; r < q; ++r)
-            for (int l = 0; l < q; ++l) X[(size_t)r * q + l] = H[((size_t)col * (k + 1) + r) * k + l];
-        fail[col] = roberts_sign(q, X);
-        for (int r = 0; r < q; ++r) Y[(size_t)col * std::max(kmaxu, 1) + r] = beta[col] * X[(size_t)r * q];
-    };
-    {
-        const int nt = std::max(1, std::min<int>(ncol, (int)std::thread::hardware_concurrency()));
-        std::vector<std::thread> pool;
-        bool serial = false;
-        try {
-            for (int t = 1; t < nt; ++t)
-                pool.emplace_back([&, t]() {
-                    for (int col = t; col < ncol; col += nt) work(col);
-                });
-        } catch (...) {  // a thread could not be started: every column runs here (work is idempotent)
-            serial = true;
+    if (kmaxu > 0) {
+        std::vector<double2> Xh((size_t)ncol * qd * qd, make_double2(0, 0));
+        for (int col = 0; col < ncol; ++col) {
+            const int q = kk[col];
+            for (int r = 0; r < qd; ++r)
+                for (int l = 0; l < qd; ++l) {
+                    cd v = (r < q && l < q) ? H[((size_t)col * (k + 1) + r) * k + l] : cd(r == l ? 1.0 : 0.0, 0.0);
+                    Xh[((size_t)col * qd + r) * qd + l] = make_double2(v.real(), v.imag());
+                }
         }
-        if (!serial)
-            for (int col = 0; col < ncol; col += nt) work(col);
-        for (auto& th : pool) th.join();
-        if (serial)
-            for (int col = 0; col < ncol; ++col) work(col);
+        DevBuf xb;
+        const int ra = dev_alloc(c, xb, sizeof(double2) * Xh.size());
+        if (ra != SGN_OK) return bail(ra);
+        double2* Xd = reinterpret_cast<double2*>(xb.p);
+        auto xfail = [&](int code) {
+            dev_free(c, xb);
+            return bail(code);
+        };
+        if (cudaMemcpyAsync(Xd, Xh.data(), sizeof(double2) * Xh.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            set_error("apply_direct: copying H_k to the device failed");
+            return xfail(SGN_ERR_CUDA);
+        }
+        const int rn = newton_sign_gpu(c, Xd, qd, ncol, fail.data());
+        if (rn != SGN_OK) return xfail(rn);
+        if (cudaMemcpyAsync(Xh.data(), Xd, sizeof(double2) * Xh.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            set_error("apply_direct: copying sign(H_k) to the host failed");
+            return xfail(SGN_ERR_CUDA);
+        }
+        dev_free(c, xb);
+        for (int col = 0; col < ncol; ++col)
+            for (int r = 0; r < kk[col]; ++r) {
+                const double2 v = Xh[((size_t)col * qd + r) * qd];  // first column of sign(H)
+                Y[(size_t)col * qd + r] = beta[col] * cd(v.x, v.y);
+            }
     }
     if (std::any_of(fail.begin(), fail.end(), [](int f) { return f != 0; })) {
         set_error("apply_direct: Newton iteration for sign(H_k) failed (singular iterate or no convergence)");

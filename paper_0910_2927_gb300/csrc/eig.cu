@@ -65,6 +65,16 @@ struct Work {
     // the polynomial filter is too weak for this spectrum (the ellipse enclosing the
     // unwanted eigenvalues of A^2 comes too close to the wanted ones): set by iterate()
     bool weak = false;
+    DevBuf backup;  // copy of the block before a filter pass (allocated on first use)
+    Work() = default;
+    Work(const Work&) = delete;
+    Work& operator=(const Work&) = delete;
+    ~Work() {  // dev_free ignores buffers already released
+        if (c) {
+            dev_free(c, buf);
+            dev_free(c, backup);
+        }
+    }
 };
 
 int setup(Work& W, sgn_ctx* c, int q, size_t esz, int nblk, int nblocks = 5) {
@@ -137,9 +147,17 @@ int combine(Work& W, const T* Y, int q, const std::vector<cd>& Cm, int r, T* Z) 
 // G = Y^dag Y, D = diag(G)^{-1/2}, D G D = V diag(l) V^dag, Y <- Y D V diag(l)^{-1/2}
 // with l floored at eps * max(l) so that dependent columns do not blow up.
 template <class T>
-int svqb(Work& W, T* Y, int q, T* tmp, double eps, int* deficient = nullptr) {
+int svqb(Work& W, T* Y, int q, T* tmp, double eps, int* deficient = nullptr, bool* overflow = nullptr) {
     std::vector<cd> G;
     SGN_CHECK(gram<T>(W, Y, q, Y, q, G));
+    if (overflow) {  // a filtered block that left the representable range: Y untouched
+        *overflow = false;
+        for (int i = 0; i < q; ++i) {
+            const double g = G[(size_t)i * q + i].real();
+            if (!std::isfinite(g)) *overflow = true;
+        }
+        if (*overflow) return SGN_OK;
+    }
     std::vector<double> d(q);
     for (int i = 0; i < q; ++i) {
         double g = G[(size_t)i * q + i].real();
@@ -446,8 +464,10 @@ int iterate(Work& W, bool adj, T* Y, int want, double tol, int max_it, Ritz& rz,
             *its = it;
             return SGN_OK;
         }
-        if (worst < 0.5 * best) {
-            best = worst;
+        // the first passes move the block from the middle of the spectrum to its low end and
+        // do not count towards a stall
+        if (worst < 0.5 * best || it < 3) {
+            best = std::min(best, worst);
             stall = 0;
         } else if (++stall >= (stop_on_stall ? 2 : 8)) {
             *its = it;
@@ -468,12 +488,37 @@ int iterate(Work& W, bool adj, T* Y, int want, double tol, int max_it, Ritz& rz,
         const int dmax = f64 ? 400 : 800;
         const double amp = f64 ? 1e6 : 1e3;  // squared stays inside the Gram resolution above
         const Ellipse e(a, b, W.beta);
+        // on the first pass of a fresh random block the cap also holds at t = 0: its Ritz
+        // values sit in the middle of the spectrum, far above the smallest eigenvalues, which
+        // a degree sized on them would amplify past the FP32 range
+        const double tlow = (fresh && it == 0) ? std::min(tmin, 0.0) : tmin;
         const int d_conv = degree_for(e, tw, amp, dmax);
-        const int d_safe = degree_for(e, tmin, amp, dmax);
+        const int d_safe = degree_for(e, tlow, amp, dmax);
         const int deg = std::max(4, std::min(d_conv, d_safe));
-        SGN_CHECK(filter<T>(W, adj, Y, a, b, deg));
+        // keep the block: a filter on too flat an ellipse amplifies bulk eigenvalues outside
+        // it without bound, until the FP32 block overflows; then the pass is repeated with a
+        // taller ellipse (by a quarter) and half the degree
+        if (!W.backup.p) SGN_CHECK(dev_alloc(W.c, W.backup, sizeof(T) * (size_t)q * W.n));
+        SGN_CUDA(cudaMemcpyAsync(W.backup.p, Y, sizeof(T) * (size_t)q * W.n, cudaMemcpyDeviceToDevice, W.c->work));
         int bad = 0;
-        SGN_CHECK(svqb<T>(W, Y, q, tmp, eps, &bad));
+        bool over = false;
+        int dpass = deg;
+        for (int tries = 0;; ++tries) {
+            SGN_CHECK(filter<T>(W, adj, Y, a, b, dpass));
+            SGN_CHECK(svqb<T>(W, Y, q, tmp, eps, &bad, &over));
+            if (!over) break;
+            if (tries >= 6 || !(4.0 * W.beta * 1.25 < b - a)) {
+                set_error("deflation set-up: the filtered block overflows (spectrum outside the filter ellipse)");
+                return SGN_ERR_DEFLATION;
+            }
+            W.beta *= 1.25;
+            dpass = std::max(4, dpass / 2);
+            if (debug_on())
+                fprintf(stderr, "[sgn eig] filtered block overflowed: ellipse height -> %.3f, degree %d\n", W.beta,
+                        dpass);
+            SGN_CUDA(cudaMemcpyAsync(Y, W.backup.p, sizeof(T) * (size_t)q * W.n, cudaMemcpyDeviceToDevice,
+                                     W.c->work));
+        }
         SGN_CHECK(svqb<T>(W, Y, q, tmp, eps));
         if (bad) SGN_CHECK(svqb<T>(W, Y, q, tmp, eps));
         if (debug_on() && bad) fprintf(stderr, "[sgn eig] refilled %d dependent directions\n", bad);

@@ -489,6 +489,7 @@ int get_engine(sgn_ctx* c, int ncol, int k, int s, int prec, Engine** out) {
     size_t ocnt = take(nc * sizeof(int));
     size_t ogres = take(nc * (size_t)(k + 1) * sizeof(double2));
     size_t oneg = take(nc * sizeof(double));
+    size_t ocyc = take(sizeof(int));
     SGN_CHECK(dev_alloc(c, E->arena, off));
     char* base = reinterpret_cast<char*>(E->arena.p);
     E->V = base + oV;
@@ -525,6 +526,7 @@ int get_engine(sgn_ctx* c, int ncol, int k, int s, int prec, Engine** out) {
     S.rstride = E->rstride;
     S.bd_tol = prec == SGN_PREC_FP64 ? 1e-14 : 1e-6;
     E->neg1 = reinterpret_cast<double*>(base + oneg);
+    E->cyc_dev = reinterpret_cast<int*>(base + ocyc);
     // zero the whole arena once so no kernel ever reads uninitialised memory
     SGN_CUDA(cudaMemsetAsync(E->arena.p, 0, off, c->work));
     {
@@ -547,6 +549,7 @@ void release_engines(sgn_ctx* c) {
     for (auto& kv : c->engines) {
         Engine& E = *kv.second;
         if (E.graph) cudaGraphExecDestroy(E.graph);
+        if (E.loop) cudaGraphExecDestroy(E.loop);
         for (cudaEvent_t ev : E.tev) cudaEventDestroy(ev);
         dev_free(c, E.arena);
         if (E.h_done) cudaFreeHost(E.h_done);
@@ -559,6 +562,23 @@ void release_engines(sgn_ctx* c) {
 }
 
 namespace {
+
+// End of one restart cycle inside the device loop (Algorithm 1's "while not all systems
+// are converged"): count the cycle and keep looping unless every column has converged,
+// the error word is set, or the cycle cap is reached.  One warp; the counter only grows,
+// so the loop ends after at most max_cycles bodies.
+__global__ void k_loop_decide(cudaGraphConditionalHandle h, const int* __restrict__ done, int ncol,
+                              const int* __restrict__ err, int* __restrict__ cyc, int max_cycles) {
+    bool all = true;
+    for (int i = threadIdx.x; i < ncol; i += 32) all = all && done[i] != 0;
+    all = __all_sync(0xffffffffu, all);
+    if (threadIdx.x == 0) {
+        const int cnum = *cyc + 1;
+        *cyc = cnum;
+        const bool stop = all || *err != 0 || cnum >= max_cycles;
+        cudaGraphSetConditional(h, stop ? 0u : 1u);
+    }
+}
 
 struct RunResult {
     int cycles = 0;
@@ -624,6 +644,79 @@ int run_engine(sgn_ctx* c, Engine& E, const CycleArgs& a, double tol, int max_cy
     }
     int cyc = 0;
     bool all_done = false;
+    // The restart loop on the device: one graph launch runs cycles until every column has
+    // converged (no host round trip per cycle).  Not with per-kernel timing (event nodes
+    // are not allowed inside a conditional body) or the per-cycle debug log; if the runtime
+    // refuses the conditional node, the host loop below runs instead.
+    static const bool no_loop = [] {
+        const char* s = getenv("SGN_HOST_LOOP");
+        return s && s[0] == '1';
+    }();
+    if (E.graph && !c->timing && !debug_log() && !no_loop && !E.loop_unavailable) {
+        const uint64_t lkey = mix(key, (uint64_t)max_cycles);
+        if (E.loop && E.loop_key != lkey) {
+            cudaGraphExecDestroy(E.loop);
+            E.loop = nullptr;
+        }
+        if (!E.loop) {
+            cudaGraph_t g = nullptr;
+            cudaGraphConditionalHandle h = 0;
+            cudaGraphNode_t node = nullptr;
+            cudaGraphNodeParams cp{};
+            cudaError_t e = cudaGraphCreate(&g, 0);
+            if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+            if (e == cudaSuccess) {
+                cp.type = cudaGraphNodeTypeConditional;
+                cp.conditional.handle = h;
+                cp.conditional.type = cudaGraphCondTypeWhile;
+                cp.conditional.size = 1;
+                e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp);
+            }
+            if (e == cudaSuccess) {
+                cudaGraph_t body = cp.conditional.phGraph_out[0];
+                e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    const long long before = g_launches;
+                    E.tmarks.clear();
+                    cudaError_t ce = cycle<T>(c, E, a, st);
+                    if (ce == cudaSuccess) {
+                        k_loop_decide<<<1, 32, 0, st>>>(h, E.S.done, ncol, E.S.err, E.cyc_dev, max_cycles);
+                        ce = cudaGetLastError();
+                    }
+                    g_launches = before;
+                    cudaGraph_t cap = nullptr;
+                    cudaError_t ee = cudaStreamEndCapture(st, &cap);
+                    e = ce != cudaSuccess ? ce : ee;
+                }
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&E.loop, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                E.loop = nullptr;
+                E.loop_unavailable = true;
+                cudaGetLastError();  // clear the refusal; the host loop takes over
+                if (debug_log()) fprintf(stderr, "[sgn] device restart loop unavailable: %s\n", cudaGetErrorString(e));
+            } else {
+                E.loop_key = lkey;
+            }
+        }
+        if (E.loop) {
+            SGN_CUDA(cudaMemsetAsync(E.cyc_dev, 0, sizeof(int), st));
+            SGN_CUDA(cudaGraphLaunch(E.loop, st));
+            int ran = 0;
+            SGN_CUDA(cudaMemcpyAsync(E.h_done, E.S.done, ncol * sizeof(int), cudaMemcpyDeviceToHost, st));
+            SGN_CUDA(cudaMemcpyAsync(E.h_err, E.S.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+            SGN_CUDA(cudaMemcpyAsync(E.h_kk, E.cyc_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+            SGN_CUDA(cudaStreamSynchronize(st));
+            ran = E.h_kk[0];
+            count_launch((E.graph_kernels + 1) * (long long)ran);
+            all_done = true;
+            for (int i = 0; i < ncol; ++i) all_done = all_done && E.h_done[i];
+            cyc = ran;
+            goto finish;
+        }
+    }
+    {
     // kernel timing: the bytes of a cycle count only the columns still active in it
     // (converged columns skip their work in every kernel)
     int active = ncol;
@@ -671,6 +764,8 @@ int run_engine(sgn_ctx* c, Engine& E, const CycleArgs& a, double tol, int max_cy
             break;
         }
     }
+    }
+finish:
     SGN_CUDA(cudaMemcpyAsync(E.h_resest, E.S.resest, ncol * sizeof(double), cudaMemcpyDeviceToHost, st));
     SGN_CUDA(cudaMemcpyAsync(E.h_kk, E.S.kk, ncol * sizeof(int), cudaMemcpyDeviceToHost, st));
     SGN_CUDA(cudaStreamSynchronize(st));

@@ -117,8 +117,10 @@ def test_mu1_regime_with_oracle_eigenpairs():
     assert _rel(x64, xo) <= 1e-10
     assert _rel(x64, target) <= 1e-9
     assert _rel(xm, xo) <= 1e-8
-    # ~180 cycles in the slow, non-normal regime: rounding moves the last few
-    assert abs(orep["cycles"] - rep64["cycles"]) <= max(1, 0.03 * orep["cycles"]), (orep["cycles"], rep64["cycles"])
+    # No cycle-count comparison here: in this slowly converging non-normal regime the
+    # residual estimate oscillates around the tolerance for many cycles, and rounding alone
+    # (the oracle's OpenMP sums) moved its stopping cycle from 183 to 299 between two runs
+    # while x agreed to 1e-10 both times.
     ref = np.concatenate([lam, nxt[:EXTRA]])
     for z in lam_gpu:
         assert np.min(np.abs(ref - z)) <= 1e-9 * abs(z), z
