@@ -82,3 +82,48 @@ def test_24x4_stencil_sampled_sites():
         assert _rel(out32[col], ref) < 2e-6
     ref3 = O.hw_sites(dims, U, psi[3], sites, mu)
     assert _rel(out64, ref3) < 1e-13
+
+
+def test_24x4_solve_shifted_residuals_sampled():
+    """The 24^4 lattice of the throughput workload (spread 0.7, mu = 0.2, s = 20, k = 40), one
+    Gaussian column, FP64 form, undeflated (its 40-pair set-up takes minutes): every shifted
+    system's residual b~ - (A^2 - sigma_i) x_i, with b~ = A b and A^2 applied by the oracle's stencil,
+    is at the solver's tolerance on sampled sites and the sites on every face; and the returned x is
+    sum_i omega_i x_i there (Algorithm 1's combination, eq. 2.3).  A wrong hop, sign, shift or weight
+    gives O(1) residuals."""
+    import paper_0910_2927_gb300 as pkg
+    dims, mu, s, k, tol = (24, 24, 24, 24), 0.2, 20, 40, 1e-10
+    V = 24 ** 4
+    U = si.random_su3_links(dims, 0.7, si.CONFIG_SEEDS[5][0])
+    b = si.gaussian_field(dims, si.CONFIG_SEEDS[5][1])
+    b_max = abs(4.0 - 1.6) + 3.0 * math.sqrt(2.0) + math.sqrt(2.0 * math.cosh(2.0 * mu))
+    sigma, omega = pkg.kenney_laub(s, 1.0 / math.sqrt(0.18 * b_max))
+    with pkg.SignContext(dims, mu=mu) as ctx:
+        ctx.load_gauge(torch.from_numpy(U).cuda())
+        ctx.set_rational(sigma, omega)
+        ctx.set_restart(k=k, tol=tol, max_cycles=3000)
+        x, xs, rep = ctx.apply(torch.from_numpy(b).cuda(), shifts=True)
+        x = x.cpu().numpy().reshape(V, 12)
+        xs = xs[:, 0].cpu().numpy()
+    assert rep["status"] == 0
+    rng = np.random.default_rng(503)
+    faces = [0, 23, 23 * 24, 23 * 24 ** 2, 23 * 24 ** 3, V - 1]
+    sites = np.unique(np.concatenate([rng.choice(V, 96, replace=False), faces]))
+    # sites whose A x is needed for A^2 x on `sites`: the sites and their 8 neighbours
+    co = np.stack(np.unravel_index(sites, dims[::-1])[::-1], axis=1)   # (x, y, z, t)
+    near = [sites]
+    for d in range(4):
+        for step in (1, -1):
+            c2 = co.copy()
+            c2[:, d] = (c2[:, d] + step) % 24
+            near.append(np.ravel_multi_index(tuple(c2[:, ::-1].T), dims[::-1]))
+    near = np.unique(np.concatenate(near))
+    bt = O.hw_sites(dims, U, b, sites, mu)                        # b~ = A b on the sampled sites
+    for i in (0, 7, s - 1):
+        ax = np.zeros((V, 12), dtype=np.complex128)
+        ax[near] = O.hw_sites(dims, U, xs[i], near, mu)            # A x_i where A^2 x_i needs it
+        a2x = O.hw_sites(dims, U, ax.reshape(-1), sites, mu)
+        r = bt - (a2x - sigma[i] * xs[i].reshape(V, 12)[sites])
+        assert np.linalg.norm(r) <= 100 * tol * np.linalg.norm(bt), (i, np.linalg.norm(r) / np.linalg.norm(bt))
+    comb = sum(omega[i] * xs[i].reshape(V, 12)[sites] for i in range(s))
+    assert np.linalg.norm(comb - x[sites]) <= 1e-12 * np.linalg.norm(x[sites])
