@@ -65,7 +65,7 @@ typedef enum {
 typedef enum { SGN_PREC_FP64 = 0, SGN_PREC_MIXED = 1 } sgn_precision;
 
 /* Storage of the FP32 stencil's links (mixed form only). */
-typedef enum { SGN_LINKS_FP32 = 0, SGN_LINKS_BF16 = 1 } sgn_link_storage;
+typedef enum { SGN_LINKS_FP32 = 0, SGN_LINKS_BF16 = 1, SGN_LINKS_FP16 = 2 } sgn_link_storage;
 
 /* Which Krylov space carries the partial fractions (Sec. 2 with eq. (6.2)):
  *  SGN_FORM_A2:  the s systems (A^2 - sigma_i) x_i = A (I - P) b in K(A^2) (default);
@@ -168,8 +168,10 @@ SGN_API int sgn_set_rational(sgn_ctx* ctx, int s, const double* sigma, const dou
 SGN_API int sgn_set_restart(sgn_ctx* ctx, int k, double tol, int max_cycles, int project_each_cycle);
 
 /* Arithmetic form (sgn_precision) and, for the mixed form, the relative error
- * of x that refinement aims at (e.g. 1e-8).  link_storage selects FP32 or BF16
- * links for the FP32 stencil. */
+ * of x that refinement aims at (e.g. 1e-8).  link_storage (sgn_link_storage)
+ * selects the links the FP32 stencil reads: FP32, BF16 or FP16 (all three are
+ * rounded from the FP64 field at sgn_load_gauge; the true residuals of the
+ * refinement always use the FP32 links).  Errors: SGN_ERR_ARG. */
 SGN_API int sgn_set_precision(sgn_ctx* ctx, int precision, double target_rel_err, int link_storage);
 
 /* Krylov space of the partial fractions (sgn_formulation).  SGN_FORM_A needs
@@ -184,7 +186,7 @@ SGN_API int sgn_set_method(sgn_ctx* ctx, int method);
 /* Mixed form only (no counterpart in the paper, which works in FP64): the
  * restart length of the FP32 correction solves that bring each shifted
  * system's true FP64 residual below the tolerance (0: min(k, 16)), and how many
- * shifted systems one correction batch solves side by side (0: up to 4 nrhs,
+ * shifted systems one correction batch solves side by side (0: up to 10 nrhs,
  * bounded by memory).  Errors: SGN_ERR_ARG (k_refine > 64, max_batch > 4096). */
 SGN_API int sgn_set_refinement(sgn_ctx* ctx, int k_refine, int max_batch);
 

@@ -12,10 +12,11 @@ import numpy as np
 
 from . import _abi
 from ._abi import (APPLY_ADJOINT, APPLY_HOST_BUFFERS, FORM_A, FORM_A2, HW_ADJOINT, HW_PACKED, LINKS_BF16,
-                   LINKS_FP32, METHOD_FOM, METHOD_GMRES, PREC_FP64, PREC_MIXED, Report, SignError, check, lib)
+                   LINKS_FP16, LINKS_FP32, METHOD_FOM, METHOD_GMRES, PREC_FP64, PREC_MIXED, Report, SignError, check, lib)
 
 __all__ = ["SignContext", "kenney_laub", "SignError", "PREC_FP64", "PREC_MIXED", "LINKS_FP32", "LINKS_BF16",
-           "HW_ADJOINT", "HW_PACKED", "FORM_A2", "FORM_A", "METHOD_FOM", "METHOD_GMRES", "sign_apply", "SignApply"]
+           "LINKS_FP16", "HW_ADJOINT", "HW_PACKED", "FORM_A2", "FORM_A", "METHOD_FOM", "METHOD_GMRES", "sign_apply",
+           "SignApply"]
 
 
 def kenney_laub(s: int, c: float = 1.0):

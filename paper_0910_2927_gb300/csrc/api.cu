@@ -148,6 +148,7 @@ SGN_API int sgn_destroy(sgn_ctx* c) {
     dev_free(c, c->U64);
     dev_free(c, c->U32);
     dev_free(c, c->U16);
+    dev_free(c, c->UH);
     dev_free(c, c->R64);
     dev_free(c, c->L64);
     dev_free(c, c->R32);
@@ -187,6 +188,7 @@ SGN_API int sgn_load_gauge(sgn_ctx* c, const double* links, int on_device) {
     SGN_CHECK(dev_alloc(c, c->U64, count * sizeof(double2)));
     SGN_CHECK(dev_alloc(c, c->U32, count * sizeof(float2)));
     SGN_CHECK(dev_alloc(c, c->U16, count * sizeof(__nv_bfloat162)));
+    SGN_CHECK(dev_alloc(c, c->UH, count * sizeof(__half2)));
     const double2* nat = reinterpret_cast<const double2*>(links);
     if (!on_device) {
         SGN_CHECK(dev_alloc(c, c->stage, count * sizeof(double2)));
@@ -196,6 +198,7 @@ SGN_API int sgn_load_gauge(sgn_ctx* c, const double* links, int on_device) {
     SGN_CUDA(pack_links(nat, as<double2>(c->U64), c->vol, c->work));
     SGN_CUDA(convert_f64_to_f32(as<double2>(c->U64), as<float2>(c->U32), (int64_t)count, c->work));
     SGN_CUDA(links_f64_to_bf16(as<double2>(c->U64), as<__nv_bfloat162>(c->U16), (int64_t)count, c->work));
+    SGN_CUDA(links_f64_to_f16(as<double2>(c->U64), as<__half2>(c->UH), (int64_t)count, c->work));
     SGN_CUDA(cudaStreamSynchronize(c->work));
     SGN_CHECK(ses.close());
     c->have_gauge = true;
@@ -263,7 +266,7 @@ SGN_API int sgn_set_restart(sgn_ctx* c, int k, double tol, int max_cycles, int p
 
 SGN_API int sgn_set_precision(sgn_ctx* c, int precision, double target_rel_err, int link_storage) {
     if (!c || (precision != SGN_PREC_FP64 && precision != SGN_PREC_MIXED) || !(target_rel_err > 0) ||
-        (link_storage != SGN_LINKS_FP32 && link_storage != SGN_LINKS_BF16))
+        (link_storage != SGN_LINKS_FP32 && link_storage != SGN_LINKS_BF16 && link_storage != SGN_LINKS_FP16))
         return fail(SGN_ERR_ARG, "sgn_set_precision: bad argument");
     c->precision = precision;
     c->target = target_rel_err;
@@ -512,7 +515,7 @@ SGN_API int sgn_hw_apply(sgn_ctx* c, const void* in, void* out, int nrhs, int pr
             pi = t;
             po = t + nn;
         }
-        SGN_CHECK(tune_stencil(c, c->link_storage == SGN_LINKS_BF16 ? 2 : 1, nrhs, const_cast<float2*>(pi), po));
+        SGN_CHECK(tune_stencil(c, stencil_prec32(c), nrhs, const_cast<float2*>(pi), po));
         SGN_CUDA(apply_hw32(c, po, pi, nrhs, adjoint, nullptr, c->work));
         if (!packed)
             SGN_CUDA(unpack_fields<float2>(po, reinterpret_cast<float2*>(out), c->vol, nrhs, c->work));

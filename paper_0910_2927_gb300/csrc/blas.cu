@@ -467,10 +467,13 @@ __global__ void __launch_bounds__(NT) k_update_x(Basis<T> V, int J, const double
     }
 }
 
-// xs[i] += sum_j y_ij V_j for every shift i, one sweep of V per group of SG shifts.  SG = 8 by
-// default: with SG = 20 (V read once for the workloads' 20 poles) the FP32 kernel needs 192
-// registers and ran at half the speed on the 10^4 workload (17.9 against 8.3 ms per solve).
-// Products and the sum over j in the storage precision; the add to xs in FP64.
+// xs[i] += sum_j y_ij V_j for every shift i.  Each CTA takes one group of SG shifts for one
+// tile of elements; the groups of a tile are consecutive CTAs (blockIdx.x = tile * ngrp + group),
+// so they run together and the tile of V comes from HBM once, the other groups reading it from L2.
+// SG = 2 by default (on the 10^4 workload 176 us per launch, against 193 us with SG = 4 and 253 us
+// with SG = 8); with SG = 20 (all of the workloads' 20 poles in one CTA) the FP32 kernel needs 192
+// registers and ran at half the speed.  Products and the sum over j in the
+// storage precision; the add to xs in FP64.
 template <class T, int SG>
 __global__ void __launch_bounds__(NT) k_update_shifts(Basis<T> V, int J, const double2* __restrict__ y, int s,
                                                       int kmax, double2* __restrict__ xs, int64_t xs_shift,
@@ -480,18 +483,21 @@ __global__ void __launch_bounds__(NT) k_update_shifts(Basis<T> V, int J, const d
     const int col = blockIdx.y;
     if (skip && skip[col]) return;
     if (kk && kk[col] < J) J = kk[col];
+    const int ngrp = (s + SG - 1) / SG;
+    const int64_t tile = blockIdx.x / (unsigned)ngrp;
+    const int g0 = (int)(blockIdx.x - tile * ngrp) * SG;
+    const int ng = (s - g0) < SG ? (s - g0) : SG;
     extern __shared__ unsigned char smraw[];
-    typename O::C* ys = reinterpret_cast<typename O::C*>(smraw);  // [s][J]
-    for (int t = threadIdx.x; t < s * J; t += NT) {
+    typename O::C* ys = reinterpret_cast<typename O::C*>(smraw);  // [ng][J]: this CTA's shifts
+    for (int t = threadIdx.x; t < ng * J; t += NT) {
         int i = t / J, j = t % J;
-        ys[t] = O::coef(y[((int64_t)col * s + i) * kmax + j]);
+        ys[t] = O::coef(y[((int64_t)col * s + g0 + i) * kmax + j]);
     }
     __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
+    const int64_t i = tile * NT + threadIdx.x;
     if (i >= npk) return;
     const T* vb = V.base + col * V.sr;
-    for (int g0 = 0; g0 < s; g0 += SG) {
-        const int ng = (s - g0) < SG ? (s - g0) : SG;
+    {
         typename O::P acc[SG];
 #pragma unroll
         for (int g = 0; g < SG; ++g) acc[g] = O::zero();
@@ -505,7 +511,7 @@ __global__ void __launch_bounds__(NT) k_update_shifts(Basis<T> V, int J, const d
                 if (j0 + u < J)
 #pragma unroll
                     for (int g = 0; g < SG; ++g)
-                        if (g < ng) O::add_cv(acc[g], ys[(g0 + g) * J + j0 + u], v[u]);
+                        if (g < ng) O::add_cv(acc[g], ys[g * J + j0 + u], v[u]);
         }
 #pragma unroll
         for (int g = 0; g < SG; ++g)
@@ -1206,6 +1212,15 @@ __global__ void k_f64_to_bf16(const double2* __restrict__ in, __nv_bfloat162* __
         out[i] = __floats2bfloat162_rn((float)v.x, (float)v.y);
     }
 }
+// FP16 links: SU(3) entries have modulus <= 1, inside FP16's normal range (one rounding
+// from FP32; entries below 6e-5 in modulus lose relative precision as subnormals, which
+// costs at most 6e-8 absolute per entry)
+__global__ void k_f64_to_f16(const double2* __restrict__ in, __half2* __restrict__ out, int64_t count) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 v = in[i];
+        out[i] = __floats2half2_rn((float)v.x, (float)v.y);
+    }
+}
 
 // r_j += sigma_j d_j - w_j for nb systems: r_j at r + roff[j] (complex128), w_j = A^2 d_j
 // in FP32 and d_j in FP64, both at j * n.
@@ -1383,21 +1398,31 @@ template <class T>
 cudaError_t update_shifts(Basis<T> V, int J, const double2* y, int s, int kmax, double2* xs, int64_t xs_shift,
                           int64_t xs_col, int64_t n, int ncol, const int* skip, const int* kk, cudaStream_t st) {
     int64_t npk = n / Ops<T>::CPX;
-    size_t smem = sizeof(typename Ops<T>::C) * (size_t)s * (size_t)J;
-    if (smem > 48 * 1024) return cudaErrorInvalidValue;
-    dim3 grid((unsigned)((npk + NT - 1) / NT), ncol);
-    // group size: SGN_SHIFT_GROUP = 10 or 20 overrides the default 8 (measurements)
+    if (s <= 0 || npk <= 0) return cudaSuccess;
+    // group size: SGN_SHIFT_GROUP = 1, 4, 8, 10 or 20 overrides the default 2 (measurements)
     static const int forced = [] {
         const char* e = getenv("SGN_SHIFT_GROUP");
         return e ? atoi(e) : 0;
     }();
-    const int sg = forced == 10 || forced == 20 ? forced : 8;
-    if (sg == 20 && s <= 20)
+    const int sg = (forced == 20 && s <= 20) || forced == 10 || forced == 8 || forced == 4 || forced == 1 ? forced : 2;
+    size_t smem = sizeof(typename Ops<T>::C) * (size_t)(s < sg ? s : sg) * (size_t)J;
+    if (smem > 48 * 1024) return cudaErrorInvalidValue;
+    const int64_t tiles = (npk + NT - 1) / NT;
+    const int64_t nblk = tiles * ((s + sg - 1) / sg);
+    if (nblk > 0x7fffffff) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)nblk, ncol);
+    if (sg == 20)
         k_update_shifts<T, 20><<<grid, NT, smem, st>>>(V, J, y, s, kmax, xs, xs_shift, xs_col, npk, skip, kk);
     else if (sg == 10)
         k_update_shifts<T, 10><<<grid, NT, smem, st>>>(V, J, y, s, kmax, xs, xs_shift, xs_col, npk, skip, kk);
-    else
+    else if (sg == 8)
         k_update_shifts<T, 8><<<grid, NT, smem, st>>>(V, J, y, s, kmax, xs, xs_shift, xs_col, npk, skip, kk);
+    else if (sg == 4)
+        k_update_shifts<T, 4><<<grid, NT, smem, st>>>(V, J, y, s, kmax, xs, xs_shift, xs_col, npk, skip, kk);
+    else if (sg == 1)
+        k_update_shifts<T, 1><<<grid, NT, smem, st>>>(V, J, y, s, kmax, xs, xs_shift, xs_col, npk, skip, kk);
+    else
+        k_update_shifts<T, 2><<<grid, NT, smem, st>>>(V, J, y, s, kmax, xs, xs_shift, xs_col, npk, skip, kk);
     count_launch();
     return cudaGetLastError();
 }
@@ -1501,6 +1526,11 @@ cudaError_t convert_f32_to_f64(const float2* in, double2* out, int64_t count, cu
 }
 cudaError_t links_f64_to_bf16(const double2* in, __nv_bfloat162* out, int64_t count, cudaStream_t st) {
     k_f64_to_bf16<<<grid_for(count), 256, 0, st>>>(in, out, count);
+    count_launch();
+    return cudaGetLastError();
+}
+cudaError_t links_f64_to_f16(const double2* in, __half2* out, int64_t count, cudaStream_t st) {
+    k_f64_to_f16<<<grid_for(count), 256, 0, st>>>(in, out, count);
     count_launch();
     return cudaGetLastError();
 }

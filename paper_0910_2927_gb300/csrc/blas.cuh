@@ -92,6 +92,7 @@ cudaError_t random_fill(T* out, int64_t count, uint64_t seed, cudaStream_t st);
 cudaError_t convert_f64_to_f32(const double2* in, float2* out, int64_t count, cudaStream_t st);
 cudaError_t convert_f32_to_f64(const float2* in, double2* out, int64_t count, cudaStream_t st);
 cudaError_t links_f64_to_bf16(const double2* in, __nv_bfloat162* out, int64_t count, cudaStream_t st);
+cudaError_t links_f64_to_f16(const double2* in, __half2* out, int64_t count, cudaStream_t st);
 
 // Small dense steps (hess.cu).  prepare_small_kernels sets launch attributes once
 // per device (before any stream capture).

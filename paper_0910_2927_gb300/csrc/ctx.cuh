@@ -82,7 +82,7 @@ struct sgn_ctx {
     int device = 0;
 
     // gauge field: FP64 master copy, FP32 and BF16 copies for the FP32 stencil
-    sgn::DevBuf U64, U32, U16;
+    sgn::DevBuf U64, U32, U16, UH;  // links: FP64, FP32, BF16, FP16
     bool have_gauge = false;
 
     // rational function
@@ -150,6 +150,11 @@ cudaError_t apply_hw32(const sgn_ctx* c, float2* out, const float2* in, int ncol
 int solve(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int ncol, bool adjoint, bool no_a,
           sgn_report* rep,
           const std::vector<std::complex<double>>* cshift = nullptr);
+// Tuning key of the FP32 stencil for the context's link storage: 1 FP32, 2 BF16, 3 FP16 links
+// (0 is the FP64 stencil).
+inline int stencil_prec32(const sgn_ctx* c) {
+    return c->link_storage == SGN_LINKS_BF16 ? 2 : c->link_storage == SGN_LINKS_FP16 ? 3 : 1;
+}
 // Pick the fastest stencil launch shape for (precision, ncol) by timing candidates
 // on the given buffers (ncol fields each); cached in the context.  Not during capture.
 int tune_stencil(sgn_ctx* c, int prec, int ncol, void* in, void* out);

@@ -43,9 +43,11 @@ template <>
 cudaError_t hw<double2>(const sgn_ctx* c, double2* out, const double2* in, int ncol, bool adj, cudaStream_t st) {
     return apply_hw64(c, out, in, ncol, adj, nullptr, st);
 }
+// The FP32 phase always reads the FP32 links: with BF16 or FP16 ones (a choice for the solves)
+// its residuals would stall at the links' rounding instead of near the FP32 floor.
 template <>
 cudaError_t hw<float2>(const sgn_ctx* c, float2* out, const float2* in, int ncol, bool adj, cudaStream_t st) {
-    return apply_hw32(c, out, in, ncol, adj, nullptr, st);
+    return apply_hw32(c, out, in, ncol, adj, nullptr, st, true);
 }
 
 struct Work {

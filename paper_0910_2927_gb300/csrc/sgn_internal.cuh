@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include <string>
@@ -113,6 +114,8 @@ cudaError_t launch_hw_f32(float2* out, const float2* in, const float2* U, int nr
 cudaError_t launch_hw_f32_bf16links(float2* out, const float2* in, const __nv_bfloat162* U, int nrhs,
                                     const StencilParams& p, const int* skip, cudaStream_t st,
                                     StencilShape sh = {});
+cudaError_t launch_hw_f32_f16links(float2* out, const float2* in, const __half2* U, int nrhs,
+                                   const StencilParams& p, const int* skip, cudaStream_t st, StencilShape sh = {});
 
 // ------------------------------------------------------------ vector ops --
 // A "basis" is J fields per column: element e of vector j of column r lives at

@@ -98,11 +98,13 @@ cudaError_t apply_hw64(const sgn_ctx* c, double2* out, const double2* in, int nc
 cudaError_t apply_hw32(const sgn_ctx* c, float2* out, const float2* in, int ncol, bool adjoint, const int* skip,
                        cudaStream_t st, bool fp32_links) {
     StencilParams p = stencil_params(c, adjoint);
-    const bool bf16 = c->link_storage == SGN_LINKS_BF16 && !fp32_links;
-    const int prec = bf16 ? 2 : 1;
-    if (bf16)
+    const int prec = fp32_links ? 1 : stencil_prec32(c);
+    if (prec == 2)
         return launch_hw_f32_bf16links(out, in, reinterpret_cast<const __nv_bfloat162*>(c->U16.p), ncol, p, skip, st,
                                        shape_for(c, prec, ncol));
+    if (prec == 3)
+        return launch_hw_f32_f16links(out, in, reinterpret_cast<const __half2*>(c->UH.p), ncol, p, skip, st,
+                                      shape_for(c, prec, ncol));
     return launch_hw_f32(out, in, reinterpret_cast<const float2*>(c->U32.p), ncol, p, skip, st,
                          shape_for(c, prec, ncol));
 }
@@ -154,6 +156,9 @@ int tune_stencil(sgn_ctx* c, int prec, int ncol, void* in, void* out) {
             return launch_hw_f32_bf16links(reinterpret_cast<float2*>(out), reinterpret_cast<const float2*>(in),
                                            reinterpret_cast<const __nv_bfloat162*>(c->U16.p), ncol, p, nullptr, st,
                                            sh);
+        if (prec == 3)
+            return launch_hw_f32_f16links(reinterpret_cast<float2*>(out), reinterpret_cast<const float2*>(in),
+                                          reinterpret_cast<const __half2*>(c->UH.p), ncol, p, nullptr, st, sh);
         return launch_hw_f32(reinterpret_cast<float2*>(out), reinterpret_cast<const float2*>(in),
                              reinterpret_cast<const float2*>(c->U32.p), ncol, p, nullptr, st, sh);
     };
@@ -249,6 +254,7 @@ uint64_t cycle_key(const sgn_ctx* c, const Engine& E, const CycleArgs& a) {
     h = mix(h, (uint64_t)(uintptr_t)c->U64.p);
     h = mix(h, (uint64_t)(uintptr_t)c->U32.p);
     h = mix(h, (uint64_t)(uintptr_t)c->U16.p);
+    h = mix(h, (uint64_t)(uintptr_t)c->UH.p);
     h = mix(h, c->link_storage);
     mixd(c->mu);
     mixd(c->mass);
@@ -359,8 +365,9 @@ cudaError_t cycle_dcgs(const sgn_ctx* c, Engine& E, const CycleArgs& a, cudaStre
     CU(combine_shifts(S, ncol, st));
     if (a.xacc) CU(update_x<T>(VB, k, S.coef, S.rstride, a.xacc, a.xsr, n, ncol, S.done, S.kk, st));
     if (a.xs) {
-        // the basis once per group of 8 shifts, every per-shift iterate read and written (FP64)
-        CU(tm.begin(4, (double)((E.s + 7) / 8) * k * fb + 2.0 * E.s * ncol * n * sizeof(double2)));
+        // the basis once (the shift groups of a tile share it through L2), every per-shift
+        // iterate read and written (FP64)
+        CU(tm.begin(4, (double)k * fb + 2.0 * E.s * ncol * n * sizeof(double2)));
         CU(update_shifts<T>(VB, k, S.y, E.s, k, a.xs, a.xs_shift, a.xs_col, n, ncol, S.done, S.kk, st));
         CU(tm.end());
     }
@@ -833,7 +840,7 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
     // phase: a cycle of the engine always runs all its k_refine steps.
     const int k1 = c->k_refine > 0 ? c->k_refine : std::min(k, 16);
     const size_t per_col = (size_t)(k1 + 4) * n * sizeof(float2) + (size_t)n * sizeof(double2);
-    size_t bmax = c->refine_batch > 0 ? (size_t)c->refine_batch : (size_t)4 * ncol;
+    size_t bmax = c->refine_batch > 0 ? (size_t)c->refine_batch : (size_t)10 * ncol;
     int B = (int)std::min<size_t>({(size_t)s * ncol, bmax, std::max<size_t>(1, kRefineBudgetBytes / per_col)});
     Engine* E1 = nullptr;
     SGN_CHECK(get_engine(c, B, k1, 1, SGN_PREC_MIXED, &E1));
@@ -915,7 +922,7 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
     else
         SGN_CUDA(apply_hw64(c, bt, rstart, ncol, adjoint, nullptr, st));  // b~ in FP64
     SGN_CUDA(convert_f64_to_f32(bt, reinterpret_cast<float2*>(E->V), (int64_t)ncol * n, st));
-    const int p32 = c->link_storage == SGN_LINKS_BF16 ? 2 : 1;
+    const int p32 = stencil_prec32(c);
     SGN_CHECK(tune_stencil(c, p32, ncol, E->V, E->t));
     SGN_CHECK(tune_stencil(c, p32, B, E1->V, E1->t));
     SGN_CHECK(tune_stencil(c, 0, ncol, bt, t64));

@@ -133,6 +133,13 @@ struct Link<float, __nv_bfloat162> {
         return {v.x, v.y};
     }
 };
+template <>
+struct Link<float, __half2> {
+    static __device__ __forceinline__ Cx<float> ld(const __half2* __restrict__ U, int64_t i) {
+        float2 v = __half22float2(__ldg(U + i));
+        return {v.x, v.y};
+    }
+};
 
 // One hop for NR fields: acc[i] += coef * (1 + S gamma_NU) W psi_i(nb), W =
 // U_NU(site) (forward, S = -1) or U_NU(nb)^dag (backward, S = +1).  Spin
@@ -384,31 +391,39 @@ __device__ __forceinline__ void hop_x2(float2 (&ar)[12], float2 (&ai)[12], const
     }
     const LinkT* lb = U + (int64_t)NU * 9 * vol + link_site;
     const float2 cc = f2s(coef), cs = f2s(coef * float(S)), ncs = f2s(-coef * float(S));
+    // the sign of the Im u terms goes on the three projected pairs it multiplies (six negated
+    // pairs per hop) instead of on a third broadcast pair per link entry (nine per hop)
+    float2 n0[3], n1[3];  // -hi (g += u h) or -hr (g += conj(u) h)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        n0[b] = S < 0 ? f2(-hi0[b].x, -hi0[b].y) : f2(-hr0[b].x, -hr0[b].y);
+        n1[b] = S < 0 ? f2(-hi1[b].x, -hi1[b].y) : f2(-hr1[b].x, -hr1[b].y);
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         float2 g0r = f2s(0.f), g0i = f2s(0.f), g1r = f2s(0.f), g1i = f2s(0.f);
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
             const Cx<float> u = Link<float, LinkT>::ld(lb, (S < 0 ? a * 3 + b : b * 3 + a) * vol);
-            const float2 ux = f2s(u.x), uy = f2s(u.y), nuy = f2s(-u.y);
+            const float2 ux = f2s(u.x), uy = f2s(u.y);
             if constexpr (S < 0) {  // g += u h
                 g0r = pfma(ux, hr0[b], g0r);
-                g0r = pfma(nuy, hi0[b], g0r);
+                g0r = pfma(uy, n0[b], g0r);
                 g0i = pfma(ux, hi0[b], g0i);
                 g0i = pfma(uy, hr0[b], g0i);
                 g1r = pfma(ux, hr1[b], g1r);
-                g1r = pfma(nuy, hi1[b], g1r);
+                g1r = pfma(uy, n1[b], g1r);
                 g1i = pfma(ux, hi1[b], g1i);
                 g1i = pfma(uy, hr1[b], g1i);
             } else {  // g += conj(u) h
                 g0r = pfma(ux, hr0[b], g0r);
                 g0r = pfma(uy, hi0[b], g0r);
                 g0i = pfma(ux, hi0[b], g0i);
-                g0i = pfma(nuy, hr0[b], g0i);
+                g0i = pfma(uy, n0[b], g0i);
                 g1r = pfma(ux, hr1[b], g1r);
                 g1r = pfma(uy, hi1[b], g1r);
                 g1i = pfma(ux, hi1[b], g1i);
-                g1i = pfma(nuy, hr1[b], g1i);
+                g1i = pfma(uy, n1[b], g1i);
             }
         }
         ar[a] = pfma(cc, g0r, ar[a]);
@@ -1122,6 +1137,10 @@ cudaError_t launch_hw_f32(float2* out, const float2* in, const float2* U, int nr
 cudaError_t launch_hw_f32_bf16links(float2* out, const float2* in, const __nv_bfloat162* U, int nrhs,
                                     const StencilParams& p, const int* skip, cudaStream_t st, StencilShape sh) {
     return launch<float, __nv_bfloat162>(out, in, U, nrhs, p, skip, st, sh);
+}
+cudaError_t launch_hw_f32_f16links(float2* out, const float2* in, const __half2* U, int nrhs,
+                                   const StencilParams& p, const int* skip, cudaStream_t st, StencilShape sh) {
+    return launch<float, __half2>(out, in, U, nrhs, p, skip, st, sh);
 }
 
 }  // namespace sgn

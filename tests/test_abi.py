@@ -61,3 +61,12 @@ def test_kenney_laub_rejects_bad_arguments():
 def test_version_string():
     import paper_0910_2927_gb300 as pkg
     assert b"sm_103a" in pkg.lib().sgn_version()
+
+
+def test_enum_constants_match_header():
+    """The binding's enum values are the ones include/sgn.h declares."""
+    from paper_0910_2927_gb300 import _abi
+    txt = open(os.path.join(ROOT, "include", "sgn.h")).read()
+    vals = dict((k, int(v)) for k, v in re.findall(r"\b(SGN_LINKS_\w+|SGN_PREC_\w+)\s*=\s*(\d+)", txt))
+    for name in ("LINKS_FP32", "LINKS_BF16", "LINKS_FP16", "PREC_FP64", "PREC_MIXED"):
+        assert vals["SGN_" + name] == getattr(_abi, name), name

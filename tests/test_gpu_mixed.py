@@ -27,7 +27,7 @@ def small():
     return dict(dims=dims, mu=mu, U=U, A=A, R=R, L=L, lam=lam, nxt=nxt)
 
 
-@pytest.mark.parametrize("links", ["fp32", "bf16"])
+@pytest.mark.parametrize("links", ["fp32", "bf16", "fp16"])
 def test_mixed_matches_oracle(small, links):
     import paper_0910_2927_gb300 as pkg
     d = small
@@ -39,7 +39,8 @@ def test_mixed_matches_oracle(small, links):
         ctx.set_rational(sigma, omega)
         ctx.set_restart(k=16, tol=1e-10, max_cycles=2000)
         ctx.set_deflation(d["R"], d["L"], d["lam"])
-        ctx.set_precision(pkg.PREC_MIXED, 1e-8, pkg.LINKS_BF16 if links == "bf16" else pkg.LINKS_FP32)
+        ctx.set_precision(pkg.PREC_MIXED, 1e-8, {"fp32": pkg.LINKS_FP32, "bf16": pkg.LINKS_BF16,
+                                                 "fp16": pkg.LINKS_FP16}[links])
         x, rep = ctx.apply(torch.from_numpy(b).cuda())
         x = x.cpu().numpy()
     assert rep["status"] == 0 and rep["err_est"] <= 1e-10, rep
