@@ -137,6 +137,22 @@ def test_roofline_entry_arithmetic():
     assert r["kernel"] == "k_hw<float,float2>" and r["traffic"] is None
 
 
+def test_solve_roofline_arithmetic():
+    """The whole-solve entry: the counted bytes of every timed class per step over the headline
+    step time, against the HBM peak; no entry without steps or time."""
+    sys.path.insert(0, ROOT)
+    import bench
+    kt = {"k_reduce": {"ms": 1.0, "launches": 10, "bytes": 2e6},
+          "k_dcgs_update<float2>": {"ms": 20.0, "launches": 10, "bytes": 6e9},
+          "k_hw<float,float2>": {"ms": 15.0, "launches": 30, "bytes": 2e9}}
+    r = bench.solve_roofline(kt, 2, 0.001, 6800.0, "measured")
+    assert r["bytes_per_step"] == pytest.approx((2e6 + 6e9 + 2e9) / 2)
+    assert r["achieved"] == pytest.approx((2e6 + 6e9 + 2e9) / 2 / 0.001 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6800.0) and r["unit"] == "GB/s"
+    assert bench.solve_roofline(kt, 0, 0.001, 6800.0, "measured") is None
+    assert bench.solve_roofline(kt, 2, 0.0, 6800.0, "measured") is None
+
+
 def test_clock_summary_parses_samples():
     """Median SM clock under load, the maximum, and the throttle reasons seen in any sample."""
     sys.path.insert(0, ROOT)
