@@ -538,11 +538,13 @@ def run_ours(args, w, name):
     ctx.close()
 
     # ---- stencil alone at 24^4 (HBM-bound): FP32 links and spinors, 12 columns
-    st = st1 = st64 = None
+    st = st1 = st64 = stff = None
     if not args.no_stencil_24:
         st = stencil_hbm(pkg, torch, args)
         st1 = stencil_hbm(pkg, torch, args, nrhs=1)
         st64 = stencil_hbm(pkg, torch, args, precision="fp64")
+        stff = stencil_hbm(pkg, torch, args, precision="float_float")
+        stff["speedup_vs_fp64"] = st64["us_per_launch"] / stff["us_per_launch"]
     # ---- the 24^4 throughput workload, measured beside the headline
     c5 = None
     if args.with_24 and name != "24^4":
@@ -596,6 +598,7 @@ def run_ours(args, w, name):
             "stencil_24^4": st,
             "stencil_24^4_1rhs": st1,
             "stencil_24^4_fp64": st64,
+            "stencil_24^4_float_float": stff,
             "kernel_times": kt,
             "roofline": roofline(kt, hbm, peak_src, t_instrumented),
             "solve_roofline": solve_roofline(kt, args.steps, t_max / args.steps, hbm, peak_src),
@@ -723,13 +726,17 @@ FP64_TFLOPS_NOMINAL = 1.25
 
 def stencil_hbm(pkg, torch, args, precision="fp32", nrhs=12):
     """The stencil alone at 24^4 (spread 0.7, mu 0.2) on nrhs packed fields: GB/s from
-    algorithmic bytes (links read once, every field read once and written once) and GFLOP/s."""
+    algorithmic bytes (links read once, every field read once and written once) and GFLOP/s.
+    precision "fp32", "fp64", or "float_float" (complex128 fields through the float-float
+    stencil; the call includes the split into (hi, lo) pairs and the join back to FP64)."""
     import ctypes as C
     dims = (24, 24, 24, 24)
     U = si.random_su3_links(dims, 0.7, si.CONFIG_SEEDS[5][0])
     vol = int(np.prod(dims))
-    p64 = precision == "fp64"
+    ffl = precision == "float_float"
+    p64 = precision == "fp64" or ffl
     prec = pkg.PREC_FP64 if p64 else pkg.PREC_MIXED
+    flags = pkg.HW_PACKED | (pkg.HW_FLOAT_FLOAT if ffl else 0)
     with pkg.SignContext(dims, mu=0.2) as sc:
         sc.load_gauge(torch.from_numpy(U).cuda())
         del U
@@ -743,15 +750,14 @@ def stencil_hbm(pkg, torch, args, precision="fp32", nrhs=12):
         stream = torch.cuda.current_stream()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         for _ in range(3):
-            lib.sgn_hw_apply(sc._h, C.c_void_p(b.data_ptr()), C.c_void_p(out.data_ptr()), nrhs, prec,
-                             pkg.HW_PACKED)
+            pkg.check(lib.sgn_hw_apply(sc._h, C.c_void_p(b.data_ptr()), C.c_void_p(out.data_ptr()), nrhs, prec,
+                                       flags))
         torch.cuda.synchronize()
         reps = 20 if not p64 else 5
         torch.cuda.nvtx.range_push("stencil")
         ev[0].record(stream)
         for _ in range(reps):
-            lib.sgn_hw_apply(sc._h, C.c_void_p(b.data_ptr()), C.c_void_p(out.data_ptr()), nrhs, prec,
-                             pkg.HW_PACKED)
+            lib.sgn_hw_apply(sc._h, C.c_void_p(b.data_ptr()), C.c_void_p(out.data_ptr()), nrhs, prec, flags)
         ev[1].record(stream)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
@@ -761,7 +767,7 @@ def stencil_hbm(pkg, torch, args, precision="fp32", nrhs=12):
     flops = STENCIL_FLOPS * vol * nrhs
     r = {"precision": precision, "nrhs": nrhs, "lattice": "24^4", "us_per_launch": t * 1e6,
          "bytes_per_launch": byts, "gbs": byts / t / 1e9, "gflops": flops / t / 1e9}
-    if p64:
+    if p64 and not ffl:
         r["roofline"] = {"bound": "alu", "achieved": flops / t / 1e12, "peak": FP64_TFLOPS_NOMINAL,
                          "unit": "TFLOP/s", "frac": flops / t / 1e12 / FP64_TFLOPS_NOMINAL,
                          "peak_source": "nominal FP64 rate of the GB300"}

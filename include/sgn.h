@@ -244,6 +244,7 @@ SGN_API int sgn_apply_shifts(sgn_ctx* ctx, const double* b, double* x, double* x
 /* Flags of sgn_hw_apply. */
 #define SGN_HW_ADJOINT 1 /* apply H_W(mu)^dag = H_W(-mu) */
 #define SGN_HW_PACKED 2  /* in and out are in the packed layout (sgn_pack_fields) */
+#define SGN_HW_FLOAT_FLOAT 4 /* with SGN_PREC_FP64: float-float arithmetic on the FP32 units */
 
 /* The Wilson kernel alone (Sec. 1): out = H_W(mu) in (or H_W(-mu) with
  * SGN_HW_ADJOINT) for nrhs fields.  precision SGN_PREC_FP64: complex128 fields;
@@ -252,7 +253,12 @@ SGN_API int sgn_apply_shifts(sgn_ctx* ctx, const double* b, double* x, double* x
  * Natural-order fields are packed into a staging buffer, the stencil runs on
  * the packed copy and the result is unpacked; with SGN_HW_PACKED the stencil
  * runs on the caller's packed fields directly (no staging, one kernel).
- * Errors: SGN_ERR_ARG (unknown precision or flag), SGN_ERR_STATE (no gauge). */
+ * SGN_HW_FLOAT_FLOAT (SGN_PREC_FP64 only): complex128 in and out, the stencil in
+ * float-float arithmetic (each real a sum of two floats, error-free transforms)
+ * on the FP32 units, within about 1e-13 of the FP64 stencil; the mixed form
+ * forms its true residuals this way.
+ * Errors: SGN_ERR_ARG (unknown precision or flag, SGN_HW_FLOAT_FLOAT with the
+ * mixed precision), SGN_ERR_STATE (no gauge). */
 SGN_API int sgn_hw_apply(sgn_ctx* ctx, const void* in, void* out, int nrhs, int precision, int flags);
 
 /* The overlap operator built on the sign function (Sec. 1):

@@ -11,12 +11,13 @@ import ctypes as C
 import numpy as np
 
 from . import _abi
-from ._abi import (APPLY_ADJOINT, APPLY_HOST_BUFFERS, FORM_A, FORM_A2, HW_ADJOINT, HW_PACKED, LINKS_BF16,
-                   LINKS_FP16, LINKS_FP32, METHOD_FOM, METHOD_GMRES, PREC_FP64, PREC_MIXED, Report, SignError, check, lib)
+from ._abi import (APPLY_ADJOINT, APPLY_HOST_BUFFERS, FORM_A, FORM_A2, HW_ADJOINT, HW_FLOAT_FLOAT, HW_PACKED,
+                   LINKS_BF16, LINKS_FP16, LINKS_FP32, METHOD_FOM, METHOD_GMRES, PREC_FP64, PREC_MIXED, Report,
+                   SignError, check, lib)
 
 __all__ = ["SignContext", "kenney_laub", "SignError", "PREC_FP64", "PREC_MIXED", "LINKS_FP32", "LINKS_BF16",
-           "LINKS_FP16", "HW_ADJOINT", "HW_PACKED", "FORM_A2", "FORM_A", "METHOD_FOM", "METHOD_GMRES", "sign_apply",
-           "SignApply"]
+           "LINKS_FP16", "HW_ADJOINT", "HW_PACKED", "HW_FLOAT_FLOAT", "FORM_A2", "FORM_A", "METHOD_FOM",
+           "METHOD_GMRES", "sign_apply", "SignApply"]
 
 
 def kenney_laub(s: int, c: float = 1.0):
@@ -284,15 +285,17 @@ class SignContext:
                                        wc.shape[0], out.ctypes.data))
         return out
 
-    def hw(self, psi, precision=PREC_FP64, adjoint=False, packed=False):
+    def hw(self, psi, precision=PREC_FP64, adjoint=False, packed=False, float_float=False):
         """H_W(mu) psi (or H_W(-mu) psi) for CUDA fields of shape (nrhs, n) or (n,);
-        packed=True: psi is (and the result stays) in the packed layout of `pack`."""
+        packed=True: psi is (and the result stays) in the packed layout of `pack`;
+        float_float=True (FP64 only): float-float arithmetic on the FP32 units."""
         torch = _torch()
         dt = torch.complex128 if precision == PREC_FP64 else torch.complex64
         x = psi.to(dt).contiguous()
         out = torch.empty_like(x)
         nrhs = x.numel() // self.n
-        flags = (HW_ADJOINT if adjoint else 0) | (HW_PACKED if packed else 0)
+        flags = ((HW_ADJOINT if adjoint else 0) | (HW_PACKED if packed else 0) |
+                 (HW_FLOAT_FLOAT if float_float else 0))
         check(lib().sgn_hw_apply(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()), nrhs,
                                  int(precision), flags))
         return out

@@ -14,7 +14,7 @@ STATUS = {0: "SGN_OK", 1: "SGN_ERR_ARG", 2: "SGN_ERR_CUDA", 3: "SGN_ERR_NOT_CONV
 PREC_FP64, PREC_MIXED = 0, 1
 LINKS_FP32, LINKS_BF16, LINKS_FP16 = 0, 1, 2
 APPLY_HOST_BUFFERS, APPLY_ADJOINT, APPLY_NO_A = 1, 2, 4
-HW_ADJOINT, HW_PACKED = 1, 2
+HW_ADJOINT, HW_PACKED, HW_FLOAT_FLOAT = 1, 2, 4
 FORM_A2, FORM_A = 0, 1
 METHOD_FOM, METHOD_GMRES = 0, 1
 

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libsgn.so")
-SOURCES = ["api.cu", "solver.cu", "stencil.cu", "blas.cu", "tsmm.cu", "hess.cu", "eig.cu", "dense_eig.cu", "grad.cu", "overlap.cu", "direct.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "solver.cu", "stencil.cu", "blas.cu", "tsmm.cu", "hess.cu", "eig.cu", "dense_eig.cu", "grad.cu", "overlap.cu", "direct.cu", "noalloc.cu", "stencil_ff.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
          "-I" + os.path.join(ROOT, "include")]

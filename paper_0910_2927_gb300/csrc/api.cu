@@ -149,6 +149,7 @@ SGN_API int sgn_destroy(sgn_ctx* c) {
     dev_free(c, c->U32);
     dev_free(c, c->U16);
     dev_free(c, c->UH);
+    dev_free(c, c->U32lo);
     dev_free(c, c->R64);
     dev_free(c, c->L64);
     dev_free(c, c->R32);
@@ -189,6 +190,7 @@ SGN_API int sgn_load_gauge(sgn_ctx* c, const double* links, int on_device) {
     SGN_CHECK(dev_alloc(c, c->U32, count * sizeof(float2)));
     SGN_CHECK(dev_alloc(c, c->U16, count * sizeof(__nv_bfloat162)));
     SGN_CHECK(dev_alloc(c, c->UH, count * sizeof(__half2)));
+    SGN_CHECK(dev_alloc(c, c->U32lo, count * sizeof(float2)));
     const double2* nat = reinterpret_cast<const double2*>(links);
     if (!on_device) {
         SGN_CHECK(dev_alloc(c, c->stage, count * sizeof(double2)));
@@ -199,6 +201,7 @@ SGN_API int sgn_load_gauge(sgn_ctx* c, const double* links, int on_device) {
     SGN_CUDA(convert_f64_to_f32(as<double2>(c->U64), as<float2>(c->U32), (int64_t)count, c->work));
     SGN_CUDA(links_f64_to_bf16(as<double2>(c->U64), as<__nv_bfloat162>(c->U16), (int64_t)count, c->work));
     SGN_CUDA(links_f64_to_f16(as<double2>(c->U64), as<__half2>(c->UH), (int64_t)count, c->work));
+    SGN_CUDA(links_lo(as<double2>(c->U64), as<float2>(c->U32), as<float2>(c->U32lo), (int64_t)count, c->work));
     SGN_CUDA(cudaStreamSynchronize(c->work));
     SGN_CHECK(ses.close());
     c->have_gauge = true;
@@ -485,24 +488,43 @@ SGN_API int sgn_hw_apply(sgn_ctx* c, const void* in, void* out, int nrhs, int pr
     if (!c->have_gauge) return fail(SGN_ERR_STATE, "sgn_hw_apply: load the gauge field first");
     if (precision != SGN_PREC_FP64 && precision != SGN_PREC_MIXED)
         return fail(SGN_ERR_ARG, "sgn_hw_apply: unknown precision");
-    if (flags & ~(SGN_HW_ADJOINT | SGN_HW_PACKED)) return fail(SGN_ERR_ARG, "sgn_hw_apply: unknown flag");
+    if (flags & ~(SGN_HW_ADJOINT | SGN_HW_PACKED | SGN_HW_FLOAT_FLOAT))
+        return fail(SGN_ERR_ARG, "sgn_hw_apply: unknown flag");
     const bool adjoint = flags & SGN_HW_ADJOINT;
     const bool packed = flags & SGN_HW_PACKED;
+    const bool ffa = flags & SGN_HW_FLOAT_FLOAT;
+    if (ffa && precision != SGN_PREC_FP64)
+        return fail(SGN_ERR_ARG, "sgn_hw_apply: SGN_HW_FLOAT_FLOAT takes complex128 fields (SGN_PREC_FP64)");
     SGN_CHECK(enter(c));
     Session ses(c);
     const size_t nn = (size_t)c->n * nrhs;
     if (precision == SGN_PREC_FP64) {
         const double2* pi = reinterpret_cast<const double2*>(in);
         double2* po = reinterpret_cast<double2*>(out);
+        // staging (complex128 units): the packed copies of in and out, then the float-float
+        // (hi, lo) pairs of in and out (4 nn complex64 = 2 nn complex128)
+        const size_t need = (packed ? 0 : 2 * nn) + (ffa ? 2 * nn : 0);
+        double2* t = nullptr;
+        if (need) {
+            SGN_CHECK(dev_alloc(c, c->stage, need * sizeof(double2)));
+            t = as<double2>(c->stage);
+        }
         if (!packed) {
-            SGN_CHECK(dev_alloc(c, c->stage, 2 * nn * sizeof(double2)));
-            double2* t = as<double2>(c->stage);
             SGN_CUDA(pack_fields<double2>(pi, t, c->vol, nrhs, c->work));
             pi = t;
             po = t + nn;
         }
-        SGN_CHECK(tune_stencil(c, 0, nrhs, const_cast<double2*>(pi), po));
-        SGN_CUDA(apply_hw64(c, po, pi, nrhs, adjoint, nullptr, c->work));
+        if (ffa) {
+            float2* f = reinterpret_cast<float2*>(t + (packed ? 0 : 2 * nn));
+            float2 *ih = f, *il = f + nn, *oh = f + 2 * nn, *ol = f + 3 * nn;
+            SGN_CUDA(split_ff(pi, ih, il, (int64_t)nn, c->work));
+            SGN_CUDA(launch_hw_ff(oh, ol, ih, il, as<float2>(c->U32), as<float2>(c->U32lo), nrhs,
+                                  stencil_params(c, adjoint), c->work));
+            SGN_CUDA(join_ff(oh, ol, po, (int64_t)nn, c->work));
+        } else {
+            SGN_CHECK(tune_stencil(c, 0, nrhs, const_cast<double2*>(pi), po));
+            SGN_CUDA(apply_hw64(c, po, pi, nrhs, adjoint, nullptr, c->work));
+        }
         if (!packed)
             SGN_CUDA(unpack_fields<double2>(po, reinterpret_cast<double2*>(out), c->vol, nrhs, c->work));
     } else {

@@ -58,9 +58,12 @@ void dev_free(sgn_ctx* c, DevBuf& b) {
 void fill_fp32_coefficients(StencilParams& p) {
     for (int d = 0; d < 3; ++d) p.div[d] = FastDiv((uint32_t)p.L[d]);
     p.diag32 = (float)p.diag;
+    p.diag_lo = (float)(p.diag - (double)p.diag32);
     for (int d = 0; d < 4; ++d) {
         p.cf32[d] = (float)p.cf[d];
         p.cb32[d] = (float)p.cb[d];
+        p.cf_lo[d] = (float)(p.cf[d] - (double)p.cf32[d]);
+        p.cb_lo[d] = (float)(p.cb[d] - (double)p.cb32[d]);
     }
 }
 
@@ -988,14 +991,26 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
         // scratch in FP64 in round 0; later rounds carry them along with the corrections
         // (r_i -= R c_i with x_i += R (Lambda^2 - sigma_i)^{-1} c_i, r_i -= (A^2 - sigma_i) d_i
         // with x_i += d_i), where FP32 products of the small d_i are exact to ~1e-7 ||r_i||
-        if (round == 0)
+        // A^2 x_i in float-float arithmetic on the FP32 units (stencil_ff.cu; ~1e-13 of the FP64
+        // stencil, which GB300 runs at 1/64 of the FP32 rate); the (hi, lo) pairs of x_i and A x_i
+        // live in the space of t64 and u64 (4 ncol complex64 fields = 2 ncol complex128 fields)
+        if (round == 0) {
+            const size_t nf = (size_t)ncol * n;
+            float2* xh = reinterpret_cast<float2*>(t64);
+            float2* xl = xh + nf;
+            float2* th = reinterpret_cast<float2*>(u64);
+            float2* tl = th + nf;
+            const StencilParams pf = stencil_params(c, adjoint);
+            const float2* Uh = reinterpret_cast<const float2*>(c->U32.p);
+            const float2* Ul = reinterpret_cast<const float2*>(c->U32lo.p);
             for (int i = 0; i < s; ++i) {
-                double2* xi = xs + (size_t)i * ncol * n;
-                SGN_CUDA(apply_hw64(c, t64, xi, ncol, adjoint, nullptr, st));
-                SGN_CUDA(apply_hw64(c, u64, t64, ncol, adjoint, nullptr, st));
-                SGN_CUDA(axpby3<double2>(rsd + (size_t)i * ncol * n, 1.0, bt, -1.0, u64, c->sigma[i], xi,
-                                         (int64_t)ncol * n, st));
+                double2* xi = xs + (size_t)i * nf;
+                SGN_CUDA(split_ff(xi, xh, xl, (int64_t)nf, st));
+                SGN_CUDA(launch_hw_ff(th, tl, xh, xl, Uh, Ul, ncol, pf, st));
+                SGN_CUDA(launch_hw_ff(xh, xl, th, tl, Uh, Ul, ncol, pf, st));
+                SGN_CUDA(residual_ff(rsd + (size_t)i * nf, bt, xh, xl, c->sigma[i], xi, (int64_t)nf, st));
             }
+        }
         SGN_CUDA(mdot<double2>(Basis<double2>{rsd, 0, n}, 0, rsd, n, n, nall, rd64, 1, nullptr, st));
         SGN_CUDA(reduce(rd64, 1, nall, RM_STORE, 0, S64, nullptr, st));
         SGN_CUDA(cudaMemcpyAsync(hall.data(), S64.red, sizeof(double2) * hall.size(), cudaMemcpyDeviceToHost, st));

@@ -68,5 +68,7 @@ def test_enum_constants_match_header():
     from paper_0910_2927_gb300 import _abi
     txt = open(os.path.join(ROOT, "include", "sgn.h")).read()
     vals = dict((k, int(v)) for k, v in re.findall(r"\b(SGN_LINKS_\w+|SGN_PREC_\w+)\s*=\s*(\d+)", txt))
-    for name in ("LINKS_FP32", "LINKS_BF16", "LINKS_FP16", "PREC_FP64", "PREC_MIXED"):
+    vals.update((k, int(v)) for k, v in re.findall(r"#define\s+(SGN_HW_\w+)\s+(\d+)", txt))
+    for name in ("LINKS_FP32", "LINKS_BF16", "LINKS_FP16", "PREC_FP64", "PREC_MIXED", "HW_ADJOINT", "HW_PACKED",
+                 "HW_FLOAT_FLOAT"):
         assert vals["SGN_" + name] == getattr(_abi, name), name

@@ -187,3 +187,40 @@ def test_colour_split_stencil_ragged_tail(shape, monkeypatch):
         assert np.linalg.norm(out[r] - ref) / np.linalg.norm(ref) < 2e-6
         refa = O.hw(dims, U, b[r], -mu)
         assert np.linalg.norm(outa[r] - refa) / np.linalg.norm(refa) < 2e-6
+
+
+@pytest.mark.parametrize("dims,ap", [((3, 4, 5, 6), (0, 0, 0, 1)), ((5, 2, 3, 7), (1, 1, 0, 1)),
+                                     ((2, 2, 2, 2), (0, 0, 0, 0))])
+@pytest.mark.parametrize("mu", [0.0, 0.3, 1.0])
+def test_float_float_stencil_matches_oracle(dims, ap, mu):
+    """The float-float stencil (the mixed form's true residuals) against the oracle's FP64 stencil:
+    within 1e-13 of the largest entry, like the FP64 stencil, on ragged lattices, both boundary
+    conditions, both hop directions (adjoint), 3 fields (the last CTA's field pair ragged)."""
+    U = si.random_su3_links(dims, 0.7, 11)
+    b = si.gaussian_block(dims, 3, 12)
+    with _ctx(dims, U, mu, ap) as ctx:
+        out = ctx.hw(torch.from_numpy(b).cuda(), float_float=True).cpu().numpy()
+        outa = ctx.hw(torch.from_numpy(b).cuda(), adjoint=True, float_float=True).cpu().numpy()
+    for r in range(3):
+        ref = O.hw(dims, U, b[r], mu, -1.6, ap)
+        np.testing.assert_allclose(out[r], ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+        refa = O.hw(dims, U, b[r], -mu, -1.6, ap)
+        np.testing.assert_allclose(outa[r], refa, rtol=0, atol=1e-13 * np.abs(refa).max())
+
+
+def test_float_float_stencil_is_more_than_fp32():
+    """Float-float is not FP32 in disguise: on inputs with low-order bits (x = 1 + 2^-30 u) the
+    result keeps them (error 1e-13 against the FP32 stencil's 1e-7), and the flag is refused for
+    complex64 fields."""
+    import paper_0910_2927_gb300 as pkg
+    dims, mu = (4, 3, 4, 5), 0.4
+    U = si.random_su3_links(dims, 0.7, 51)
+    b = si.gaussian_block(dims, 2, 52)
+    x = 1.0 + 2.0 ** -30 * b
+    with _ctx(dims, U, mu) as ctx:
+        out = ctx.hw(torch.from_numpy(x).cuda(), float_float=True).cpu().numpy()
+        with pytest.raises(pkg.SignError):
+            ctx.hw(torch.from_numpy(x).cuda(), precision=pkg.PREC_MIXED, float_float=True)
+    for r in range(2):
+        ref = O.hw(dims, U, x[r], mu)
+        assert np.linalg.norm(out[r] - ref) / np.linalg.norm(ref) < 1e-13
