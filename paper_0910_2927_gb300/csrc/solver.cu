@@ -988,12 +988,14 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
     std::vector<double> rsig(B);
     for (int round = 0; round <= max_rounds; ++round) {
         // true residuals r_i = b~ - (A^2 - sigma_i) x_i of every shifted system: from
-        // scratch in FP64 in round 0; later rounds carry them along with the corrections
-        // (r_i -= R c_i with x_i += R (Lambda^2 - sigma_i)^{-1} c_i, r_i -= (A^2 - sigma_i) d_i
-        // with x_i += d_i), where FP32 products of the small d_i are exact to ~1e-7 ||r_i||
-        // A^2 x_i in float-float arithmetic on the FP32 units (stencil_ff.cu; ~1e-13 of the FP64
-        // stencil, which GB300 runs at 1/64 of the FP32 rate); the (hi, lo) pairs of x_i and A x_i
-        // live in the space of t64 and u64 (4 ncol complex64 fields = 2 ncol complex128 fields)
+        // scratch in refinement round 0, assembled in FP64; later rounds carry them along with
+        // the corrections (r_i -= R c_i with x_i += R (Lambda^2 - sigma_i)^{-1} c_i,
+        // r_i -= (A^2 - sigma_i) d_i with x_i += d_i), where FP32 products of the small d_i are
+        // exact to ~1e-7 ||r_i||.
+        // Round 0 forms A^2 x_i in float-float arithmetic on the FP32 units (stencil_ff.cu; ~1e-13
+        // of the FP64 stencil, which GB300 runs at 1/64 of the FP32 rate); the (hi, lo) pairs of
+        // x_i and A x_i live in the space of t64 and u64 (4 ncol complex64 fields = 2 ncol
+        // complex128 fields).
         if (round == 0) {
             const size_t nf = (size_t)ncol * n;
             float2* xh = reinterpret_cast<float2*>(t64);

@@ -33,12 +33,16 @@ __device__ __forceinline__ ff fast_two_sum(float a, float b) {
     const float s = __fadd_rn(a, b);
     return {s, __fsub_rn(b, __fsub_rn(s, a))};
 }
-__device__ __forceinline__ ff ff_add(ff a, ff b) {
-    const ff s = two_sum(a.hi, b.hi);
-    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
-}
 __device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
-__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+// Sum of two float-float numbers, left unnormalised: hi is the rounded sum of the high parts, lo
+// collects its error and the low parts (|lo| stays within a few units of 2^-24 |hi| unless the sum
+// cancels, and hi + lo is the sum to about 2^-46 of the operands either way).  The stencil's
+// intermediate sums and its accumulators use this form; the accumulators are normalised once,
+// before the store.
+__device__ __forceinline__ ff ff_add_u(ff a, ff b) {
+    const ff s = two_sum(a.hi, b.hi);
+    return {s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo))};
+}
 // a * b: TwoProd of the high parts by FMA, the cross terms in FP32 (their rounding is of
 // order 2^-48 of the product), the small lo * lo term dropped.
 __device__ __forceinline__ ff ff_mul(ff a, ff b) {
@@ -64,14 +68,14 @@ struct Dot {
         s = t.hi;
         c = __fadd_rn(c, __fadd_rn(t.lo, e));
     }
-    __device__ __forceinline__ ff value() const { return two_sum(s, c); }
+    __device__ __forceinline__ ff value() const { return {s, c}; }  // unnormalised (see ff_add_u)
 };
 
 struct ffc {
     ff re, im;
 };
-__device__ __forceinline__ ffc cadd(ffc a, ffc b) { return {ff_add(a.re, b.re), ff_add(a.im, b.im)}; }
-__device__ __forceinline__ ffc csub(ffc a, ffc b) { return {ff_sub(a.re, b.re), ff_sub(a.im, b.im)}; }
+__device__ __forceinline__ ffc cadd(ffc a, ffc b) { return {ff_add_u(a.re, b.re), ff_add_u(a.im, b.im)}; }
+__device__ __forceinline__ ffc csub(ffc a, ffc b) { return {ff_add_u(a.re, ff_neg(b.re)), ff_add_u(a.im, ff_neg(b.im))}; }
 __device__ __forceinline__ ffc mul_i(ffc a) { return {ff_neg(a.im), a.re}; }   // i a
 __device__ __forceinline__ ffc mul_mi(ffc a) { return {a.im, ff_neg(a.re)}; }  // -i a
 
@@ -197,9 +201,10 @@ __device__ __forceinline__ void both_hops(ffc (&acc)[12], const float2* __restri
     hop<NU, +1>(acc, fh, fl, Uh, Ul, bw, bw, coef_ff(P.cb32[NU], P.cb_lo[NU], bfl), P.vol);
 }
 
-// Thread (x, y) of CTA b: site (b / ngrp) * SX + x, field (b % ngrp) * RB + y.  144 registers:
-// CTAs of 128 threads, three per SM.
-__global__ void __launch_bounds__(128)
+// Thread (x, y) of CTA b: site (b / ngrp) * SX + x, field (b % ngrp) * RB + y.  Capped at 128
+// registers (four CTAs of 128 threads per SM; as the compiler sizes it, 144 registers and three
+// CTAs ran 20 % slower at 10^4 despite a few spilled values).
+__global__ void __launch_bounds__(128, 4)
     k_hw_ff(float2* __restrict__ oh, float2* __restrict__ ol, const float2* __restrict__ ih,
             const float2* __restrict__ il, const float2* __restrict__ Uh, const float2* __restrict__ Ul, int nrhs,
             StencilParams P, int ngrp) {
@@ -237,7 +242,10 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
         const float g = k < 3 ? 1.f : -1.f;  // gamma5 = diag(1, 1, -1, -1): planes 3..5 hold spins 2, 3
-        const ffc a = acc[2 * k], b = acc[2 * k + 1];
+        const ff ar = two_sum(acc[2 * k].re.hi, acc[2 * k].re.lo), ai = two_sum(acc[2 * k].im.hi, acc[2 * k].im.lo);
+        const ff br = two_sum(acc[2 * k + 1].re.hi, acc[2 * k + 1].re.lo),
+                 bi = two_sum(acc[2 * k + 1].im.hi, acc[2 * k + 1].im.lo);
+        const ffc a = {ar, ai}, b = {br, bi};
         *reinterpret_cast<float4*>(gh + k * 2 * P.vol + 2 * site) =
             make_float4(g * a.re.hi, g * a.im.hi, g * b.re.hi, g * b.im.hi);
         *reinterpret_cast<float4*>(gl + k * 2 * P.vol + 2 * site) =
