@@ -774,6 +774,39 @@ def stencil_hbm(pkg, torch, args, precision="fp32", nrhs=12):
     return r
 
 
+def stencil_compare(pkg, torch):
+    """The FP64 stencil against the float-float one on 12 packed point-source fields at 10^4 and
+    24^4 (spread 0.7, mu 0.2): ms per sgn_hw_apply call (warm, CUDA events over 10 calls; the
+    float-float call includes the split into (hi, lo) pairs and the join back to FP64)."""
+    import ctypes as C
+    lib = pkg.lib()
+    out = []
+    for L in (10, 24):
+        dims = (L,) * 4
+        U = si.random_su3_links(dims, 0.7, si.CONFIG_SEEDS[5][0])
+        with pkg.SignContext(dims, mu=0.2) as sc:
+            sc.load_gauge(torch.from_numpy(U).cuda())
+            del U
+            b = sc.pack(torch.from_numpy(si.point_sources(dims, 12)).cuda(), pkg.PREC_FP64)
+            o = torch.empty_like(b)
+            r = {"lattice": f"{L}^4", "nrhs": 12}
+            for name, fl in (("fp64_ms", pkg.HW_PACKED), ("float_float_ms", pkg.HW_PACKED | pkg.HW_FLOAT_FLOAT)):
+                for _ in range(3):
+                    pkg.check(lib.sgn_hw_apply(sc._h, C.c_void_p(b.data_ptr()), C.c_void_p(o.data_ptr()), 12,
+                                               pkg.PREC_FP64, fl))
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(10):
+                    lib.sgn_hw_apply(sc._h, C.c_void_p(b.data_ptr()), C.c_void_p(o.data_ptr()), 12, pkg.PREC_FP64, fl)
+                e1.record()
+                torch.cuda.synchronize()
+                r[name] = e0.elapsed_time(e1) / 10
+            r["speedup"] = r["fp64_ms"] / r["float_float_ms"]
+            out.append(r)
+    return out
+
+
 def main():
     global TOL
     ap = argparse.ArgumentParser()
@@ -793,6 +826,8 @@ def main():
     ap.add_argument("--direct-k", default="", help="comma-separated Krylov dimensions for the direct projection")
     ap.add_argument("--stencil-only", action="store_true",
                     help="time only the 12-column FP32 stencil at 24^4 and print its numbers")
+    ap.add_argument("--stencil-compare", action="store_true",
+                    help="time the FP64 and the float-float stencil at 10^4 and 24^4 and print their numbers")
     args = ap.parse_args()
     TOL = args.tol
     w = WORKLOADS[args.workload]
@@ -800,6 +835,11 @@ def main():
         import torch
         import paper_0910_2927_gb300 as pkg
         print(json.dumps({"stencil_24^4": stencil_hbm(pkg, torch, args)}))
+        return
+    if args.stencil_compare:
+        import torch
+        import paper_0910_2927_gb300 as pkg
+        print(json.dumps({"stencil_fp64_vs_float_float": stencil_compare(pkg, torch)}))
         return
     if args.impl == "reference":
         reference_arm(args, w, args.workload)
