@@ -52,7 +52,8 @@ __device__ __forceinline__ ff ff_mul(ff a, ff b) {
     e = __fmaf_rn(a.lo, b.hi, e);
     return fast_two_sum(p, e);
 }
-// exact scaling by a power of two (the hop coefficient -1/2 of the space directions)
+// scaling by a float whose product is exact (a power of two: the hop coefficient -1/2 of the
+// space directions)
 __device__ __forceinline__ ff ff_scale2(ff a, float s) { return {a.hi * s, a.lo * s}; }
 
 // Compensated dot-product accumulator: value s + c.  add(a, b) adds a * b: the product's
@@ -149,7 +150,7 @@ __device__ __forceinline__ void hop(ffc (&acc)[12], const float2* __restrict__ f
             g1i.add(ui, h1[b].re);
         }
         ffc g0 = {g0r.value(), g0i.value()}, g1 = {g1r.value(), g1i.value()};
-        if constexpr (NU == 3) {
+        if (NU == 3 || coef.lo != 0.f) {  // the space directions' -1/2 is exact: lo = 0
             g0 = {ff_mul(g0.re, coef), ff_mul(g0.im, coef)};
             g1 = {ff_mul(g1.re, coef), ff_mul(g1.im, coef)};
         } else {
