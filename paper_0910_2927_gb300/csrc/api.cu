@@ -149,7 +149,7 @@ SGN_API int sgn_destroy(sgn_ctx* c) {
     dev_free(c, c->U32);
     dev_free(c, c->U16);
     dev_free(c, c->UH);
-    dev_free(c, c->U32lo);
+    dev_free(c, c->Uff);
     dev_free(c, c->R64);
     dev_free(c, c->L64);
     dev_free(c, c->R32);
@@ -190,7 +190,7 @@ SGN_API int sgn_load_gauge(sgn_ctx* c, const double* links, int on_device) {
     SGN_CHECK(dev_alloc(c, c->U32, count * sizeof(float2)));
     SGN_CHECK(dev_alloc(c, c->U16, count * sizeof(__nv_bfloat162)));
     SGN_CHECK(dev_alloc(c, c->UH, count * sizeof(__half2)));
-    SGN_CHECK(dev_alloc(c, c->U32lo, count * sizeof(float2)));
+    SGN_CHECK(dev_alloc(c, c->Uff, count * sizeof(float4)));
     const double2* nat = reinterpret_cast<const double2*>(links);
     if (!on_device) {
         SGN_CHECK(dev_alloc(c, c->stage, count * sizeof(double2)));
@@ -201,7 +201,7 @@ SGN_API int sgn_load_gauge(sgn_ctx* c, const double* links, int on_device) {
     SGN_CUDA(convert_f64_to_f32(as<double2>(c->U64), as<float2>(c->U32), (int64_t)count, c->work));
     SGN_CUDA(links_f64_to_bf16(as<double2>(c->U64), as<__nv_bfloat162>(c->U16), (int64_t)count, c->work));
     SGN_CUDA(links_f64_to_f16(as<double2>(c->U64), as<__half2>(c->UH), (int64_t)count, c->work));
-    SGN_CUDA(links_lo(as<double2>(c->U64), as<float2>(c->U32), as<float2>(c->U32lo), (int64_t)count, c->work));
+    SGN_CUDA(links_ff(as<double2>(c->U64), as<float2>(c->U32), as<float4>(c->Uff), (int64_t)count, c->work));
     SGN_CUDA(cudaStreamSynchronize(c->work));
     SGN_CHECK(ses.close());
     c->have_gauge = true;
@@ -518,8 +518,7 @@ SGN_API int sgn_hw_apply(sgn_ctx* c, const void* in, void* out, int nrhs, int pr
             float2* f = reinterpret_cast<float2*>(t + (packed ? 0 : 2 * nn));
             float2 *ih = f, *il = f + nn, *oh = f + 2 * nn, *ol = f + 3 * nn;
             SGN_CUDA(split_ff(pi, ih, il, (int64_t)nn, c->work));
-            SGN_CUDA(launch_hw_ff(oh, ol, ih, il, as<float2>(c->U32), as<float2>(c->U32lo), nrhs,
-                                  stencil_params(c, adjoint), c->work));
+            SGN_CUDA(launch_hw_ff(oh, ol, ih, il, as<float4>(c->Uff), nrhs, stencil_params(c, adjoint), c->work));
             SGN_CUDA(join_ff(oh, ol, po, (int64_t)nn, c->work));
         } else {
             SGN_CHECK(tune_stencil(c, 0, nrhs, const_cast<double2*>(pi), po));

@@ -82,7 +82,7 @@ struct sgn_ctx {
     int device = 0;
 
     // gauge field: FP64 master copy, FP32 and BF16 copies for the FP32 stencil
-    sgn::DevBuf U64, U32, U16, UH, U32lo;  // links: FP64, FP32, BF16, FP16, fl(U64 - U32)
+    sgn::DevBuf U64, U32, U16, UH, Uff;  // links: FP64, FP32, BF16, FP16, float-float (float4)
     bool have_gauge = false;
 
     // rational function

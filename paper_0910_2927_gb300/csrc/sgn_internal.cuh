@@ -121,16 +121,16 @@ cudaError_t launch_hw_f32_bf16links(float2* out, const float2* in, const __nv_bf
 cudaError_t launch_hw_f32_f16links(float2* out, const float2* in, const __half2* U, int nrhs,
                                    const StencilParams& p, const int* skip, cudaStream_t st, StencilShape sh = {});
 // Float-float stencil (stencil_ff.cu): fields as (hi, lo) pairs of packed FP32 fields, links as
-// the FP32 copy Uh and the FP32 rounding Ul of U - Uh; about 1e-13 of the FP64 result.
-cudaError_t launch_hw_ff(float2* oh, float2* ol, const float2* ih, const float2* il, const float2* Uh,
-                         const float2* Ul, int nrhs, const StencilParams& p, cudaStream_t st);
+// one float4 (U32, fl(U - U32)) per packed entry; about 1e-13 of the FP64 result.
+cudaError_t launch_hw_ff(float2* oh, float2* ol, const float2* ih, const float2* il, const float4* Uf, int nrhs,
+                         const StencilParams& p, cudaStream_t st);
 // FP64 <-> (hi, lo) conversions of count complex entries, the FP64 true residual
-// r = b - (yh + yl) + sigma x, and the links' remainder lo = fl(U - U32).
+// r = b - (yh + yl) + sigma x, and the float-float links (U32, fl(U - U32)).
 cudaError_t split_ff(const double2* in, float2* hi, float2* lo, int64_t count, cudaStream_t st);
 cudaError_t join_ff(const float2* hi, const float2* lo, double2* out, int64_t count, cudaStream_t st);
 cudaError_t residual_ff(double2* r, const double2* b, const float2* yh, const float2* yl, double sigma,
                         const double2* x, int64_t count, cudaStream_t st);
-cudaError_t links_lo(const double2* U, const float2* U32, float2* lo, int64_t count, cudaStream_t st);
+cudaError_t links_ff(const double2* U, const float2* U32, float4* out, int64_t count, cudaStream_t st);
 
 // ------------------------------------------------------------ vector ops --
 // A "basis" is J fields per column: element e of vector j of column r lives at

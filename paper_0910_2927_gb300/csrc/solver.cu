@@ -1003,13 +1003,12 @@ int solve_mixed(sgn_ctx* c, const double2* b, double2* x, double2* x_shift, int 
             float2* th = reinterpret_cast<float2*>(u64);
             float2* tl = th + nf;
             const StencilParams pf = stencil_params(c, adjoint);
-            const float2* Uh = reinterpret_cast<const float2*>(c->U32.p);
-            const float2* Ul = reinterpret_cast<const float2*>(c->U32lo.p);
+            const float4* Uf = reinterpret_cast<const float4*>(c->Uff.p);
             for (int i = 0; i < s; ++i) {
                 double2* xi = xs + (size_t)i * nf;
                 SGN_CUDA(split_ff(xi, xh, xl, (int64_t)nf, st));
-                SGN_CUDA(launch_hw_ff(th, tl, xh, xl, Uh, Ul, ncol, pf, st));
-                SGN_CUDA(launch_hw_ff(xh, xl, th, tl, Uh, Ul, ncol, pf, st));
+                SGN_CUDA(launch_hw_ff(th, tl, xh, xl, Uf, ncol, pf, st));
+                SGN_CUDA(launch_hw_ff(xh, xl, th, tl, Uf, ncol, pf, st));
                 SGN_CUDA(residual_ff(rsd + (size_t)i * nf, bt, xh, xl, c->sigma[i], xi, (int64_t)nf, st));
             }
         }

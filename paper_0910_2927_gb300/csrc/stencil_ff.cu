@@ -8,8 +8,7 @@
 // than FP32 (they decide convergence at 1e-8 ||b~||), and GB300 executes FP64 at 1/64 of its FP32
 // rate: the FP64 stencil is bound by the FP64 pipe.  The float-float stencil reaches ~1e-13 of the
 // FP64 result with FP32 instructions only.  Fields enter and leave as (hi, lo) pairs of packed FP32
-// fields (the FP32 layout of stencil.cu); the links as the FP32 copy plus the FP32 rounding of the
-// remainder U - U32.  Same hop structure as stencil.cu: rank-2 spin projection, gamma5 folded into
+// fields (the FP32 layout of stencil.cu); the links as float4 (U32, fl(U - U32)) per entry.  Same hop structure as stencil.cu: rank-2 spin projection, gamma5 folded into
 // the store, one thread per site and field, CTA = SX sites x RB fields of one site tile.
 #include "sgn_internal.cuh"
 
@@ -120,7 +119,7 @@ __device__ __forceinline__ void project(const ffc (&p)[12], ffc (&h0)[3], ffc (&
 // exactly; -1/2 e^{+-mu} in time, a float-float product.
 template <int NU, int S>
 __device__ __forceinline__ void hop(ffc (&acc)[12], const float2* __restrict__ fh, const float2* __restrict__ fl,
-                                    const float2* __restrict__ Uh, const float2* __restrict__ Ul, int64_t link_site,
+                                    const float4* __restrict__ Uf, int64_t link_site,
                                     int64_t nb, ff coef, int64_t vol) {
     ffc h0[3], h1[3];
     {
@@ -135,10 +134,10 @@ __device__ __forceinline__ void hop(ffc (&acc)[12], const float2* __restrict__ f
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
             const int64_t e = lb + (int64_t)(S < 0 ? a * 3 + b : b * 3 + a) * vol;
-            const float2 uh = __ldg(Uh + e), ul = __ldg(Ul + e);
-            const ff ur = {uh.x, ul.x};
+            const float4 u = __ldg(Uf + e);  // (Re hi, Im hi, Re lo, Im lo)
+            const ff ur = {u.x, u.z};
             // U h (forward) or conj(U) h (backward, the dagger's transpose is in the index)
-            const ff ui = S < 0 ? ff{uh.y, ul.y} : ff{-uh.y, -ul.y};
+            const ff ui = S < 0 ? ff{u.y, u.w} : ff{-u.y, -u.w};
             const ff nui = ff_neg(ui);
             g0r.add(ur, h0[b].re);
             g0r.add(nui, h0[b].im);
@@ -180,7 +179,7 @@ __device__ __forceinline__ ff coef_ff(float hi, float lo, bool flip) { return fl
 
 template <int NU>
 __device__ __forceinline__ void both_hops(ffc (&acc)[12], const float2* __restrict__ fh, const float2* __restrict__ fl,
-                                          const float2* __restrict__ Uh, const float2* __restrict__ Ul, int64_t site,
+                                          const float4* __restrict__ Uf, int64_t site,
                                           const int co[4], const StencilParams& P) {
     int64_t stride = 1;
 #pragma unroll
@@ -198,8 +197,8 @@ __device__ __forceinline__ void both_hops(ffc (&acc)[12], const float2* __restri
         bw = site + (int64_t)(L - 1) * stride;
         bfl = P.ap[NU];
     }
-    hop<NU, -1>(acc, fh, fl, Uh, Ul, site, fw, coef_ff(P.cf32[NU], P.cf_lo[NU], ffl), P.vol);
-    hop<NU, +1>(acc, fh, fl, Uh, Ul, bw, bw, coef_ff(P.cb32[NU], P.cb_lo[NU], bfl), P.vol);
+    hop<NU, -1>(acc, fh, fl, Uf, site, fw, coef_ff(P.cf32[NU], P.cf_lo[NU], ffl), P.vol);
+    hop<NU, +1>(acc, fh, fl, Uf, bw, bw, coef_ff(P.cb32[NU], P.cb_lo[NU], bfl), P.vol);
 }
 
 // Thread (x, y) of CTA b: site (b / ngrp) * SX + x, field (b % ngrp) * RB + y.  Capped at 128
@@ -207,7 +206,7 @@ __device__ __forceinline__ void both_hops(ffc (&acc)[12], const float2* __restri
 // CTAs ran 20 % slower at 10^4 despite a few spilled values).
 __global__ void __launch_bounds__(128, 4)
     k_hw_ff(float2* __restrict__ oh, float2* __restrict__ ol, const float2* __restrict__ ih,
-            const float2* __restrict__ il, const float2* __restrict__ Uh, const float2* __restrict__ Ul, int nrhs,
+            const float2* __restrict__ il, const float4* __restrict__ Uf, int nrhs,
             StencilParams P, int ngrp) {
     const int64_t tile = blockIdx.x / (unsigned)ngrp;
     const int grp = (int)(blockIdx.x - tile * ngrp);
@@ -234,10 +233,10 @@ __global__ void __launch_bounds__(128, 4)
 #pragma unroll
         for (int k = 0; k < 12; ++k) acc[k] = {ff_mul(acc[k].re, d), ff_mul(acc[k].im, d)};
     }
-    both_hops<0>(acc, fh, fl, Uh, Ul, site, co, P);
-    both_hops<1>(acc, fh, fl, Uh, Ul, site, co, P);
-    both_hops<2>(acc, fh, fl, Uh, Ul, site, co, P);
-    both_hops<3>(acc, fh, fl, Uh, Ul, site, co, P);
+    both_hops<0>(acc, fh, fl, Uf, site, co, P);
+    both_hops<1>(acc, fh, fl, Uf, site, co, P);
+    both_hops<2>(acc, fh, fl, Uf, site, co, P);
+    both_hops<3>(acc, fh, fl, Uf, site, co, P);
     float2* gh = oh + rhs * P.stride_rhs;
     float2* gl = ol + rhs * P.stride_rhs;
 #pragma unroll
@@ -283,13 +282,14 @@ __global__ void k_residual_ff(double2* __restrict__ r, const double2* __restrict
                             bv.y - ((double)h.y + (double)l.y) + sigma * xv.y);
     }
 }
-// links: lo = fl(U - U32)
-__global__ void k_links_lo(const double2* __restrict__ U, const float2* __restrict__ U32, float2* __restrict__ lo,
+// links as float-float pairs, one 16-byte load per entry: (Re hi, Im hi, Re lo, Im lo) with
+// hi = U32 and lo = fl(U - U32)
+__global__ void k_links_ff(const double2* __restrict__ U, const float2* __restrict__ U32, float4* __restrict__ out,
                            int64_t count) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
         const double2 u = U[i];
         const float2 h = U32[i];
-        lo[i] = make_float2((float)(u.x - (double)h.x), (float)(u.y - (double)h.y));
+        out[i] = make_float4(h.x, h.y, (float)(u.x - (double)h.x), (float)(u.y - (double)h.y));
     }
 }
 
@@ -300,8 +300,8 @@ unsigned grid_of(int64_t count) {
 
 }  // namespace
 
-cudaError_t launch_hw_ff(float2* oh, float2* ol, const float2* ih, const float2* il, const float2* Uh,
-                         const float2* Ul, int nrhs, const StencilParams& p, cudaStream_t st) {
+cudaError_t launch_hw_ff(float2* oh, float2* ol, const float2* ih, const float2* il, const float4* Uf, int nrhs,
+                         const StencilParams& p, cudaStream_t st) {
     if (nrhs <= 0 || p.vol <= 0) return cudaSuccess;
     // 64 sites x 2 fields per CTA (128 x 1 for one field); the fields of a site tile in
     // consecutive CTAs share links in L2
@@ -309,7 +309,7 @@ cudaError_t launch_hw_ff(float2* oh, float2* ol, const float2* ih, const float2*
     const int ngrp = (nrhs + rb - 1) / rb;
     const int64_t tiles = (p.vol + sx - 1) / sx;
     if (tiles * ngrp > 0x7fffffffLL) return cudaErrorInvalidValue;
-    k_hw_ff<<<(unsigned)(tiles * ngrp), dim3(sx, rb), 0, st>>>(oh, ol, ih, il, Uh, Ul, nrhs, p, ngrp);
+    k_hw_ff<<<(unsigned)(tiles * ngrp), dim3(sx, rb), 0, st>>>(oh, ol, ih, il, Uf, nrhs, p, ngrp);
     count_launch();
     return cudaGetLastError();
 }
@@ -333,9 +333,9 @@ cudaError_t residual_ff(double2* r, const double2* b, const float2* yh, const fl
     count_launch();
     return cudaGetLastError();
 }
-cudaError_t links_lo(const double2* U, const float2* U32, float2* lo, int64_t count, cudaStream_t st) {
+cudaError_t links_ff(const double2* U, const float2* U32, float4* out, int64_t count, cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
-    k_links_lo<<<grid_of(count), 256, 0, st>>>(U, U32, lo, count);
+    k_links_ff<<<grid_of(count), 256, 0, st>>>(U, U32, out, count);
     count_launch();
     return cudaGetLastError();
 }
